@@ -1,0 +1,393 @@
+/*
+ * hz_oracle.c -- CPU oracle for the complex Helmholtz Krylov path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, single-threaded
+ * statement of what the GPU path computes.  Only the test-suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it; the product
+ * path never does.  It shares no code, header, table or helper with the CUDA
+ * sources.
+ *
+ * Arithmetic is IEEE binary64 (binary32 for the inner solve of the mixed
+ * precision refinement), summed in the order the definitions are written.
+ * Build with -ffp-contract=off so no multiply-add is fused behind our back.
+ *
+ * Complex numbers are two contiguous doubles (real, imaginary), the layout
+ * of the paper's Section 4 (listing "Complex number in memory").  Matrices
+ * are CSR as in Section 3.2 (AA values, JA column indices, IA row pointers),
+ * 0-based.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct { double re, im; } oz;   /* complex double */
+typedef struct { float re, im; } oc;    /* complex float  */
+
+enum { OR_OK = 0, OR_NOT_CONVERGED = 4, OR_BREAKDOWN = 5, OR_NAN = 6 };
+
+static oz z_mul(oz a, oz b) { oz r = {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; return r; }
+static oz z_add(oz a, oz b) { oz r = {a.re + b.re, a.im + b.im}; return r; }
+static oz z_sub(oz a, oz b) { oz r = {a.re - b.re, a.im - b.im}; return r; }
+static oz z_conj(oz a) { oz r = {a.re, -a.im}; return r; }
+static oz z_div(oz a, oz b) {
+    /* textbook quotient a * conj(b) / |b|^2 */
+    double d = b.re * b.re + b.im * b.im;
+    oz r = {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+    return r;
+}
+static int z_isfinite(oz a) { return isfinite(a.re) && isfinite(a.im); }
+
+static oc c_mul(oc a, oc b) { oc r = {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; return r; }
+static oc c_add(oc a, oc b) { oc r = {a.re + b.re, a.im + b.im}; return r; }
+static oc c_sub(oc a, oc b) { oc r = {a.re - b.re, a.im - b.im}; return r; }
+static oc c_conj(oc a) { oc r = {a.re, -a.im}; return r; }
+static oc c_div(oc a, oc b) {
+    float d = b.re * b.re + b.im * b.im;
+    oc r = {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+    return r;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Neumaier-compensated summation, used by every reduction so that the    */
+/* oracle is more accurate than any blocked GPU reduction it is compared   */
+/* against.                                                                */
+typedef struct { double s, c; } ksum;
+static void ks_add(ksum *k, double v) {
+    double t = k->s + v;
+    if (fabs(k->s) >= fabs(v)) k->c += (k->s - t) + v;
+    else k->c += (v - t) + k->s;
+    k->s = t;
+}
+static double ks_val(const ksum *k) { return k->s + k->c; }
+
+/* ---------------------------------------------------------------------- */
+/* Section 6: y = A x with A in CSR, y_i = sum_{k=IA(i)}^{IA(i+1)-1} AA(k) x(JA(k)),
+ * summed in storage order. */
+void or_zspmv(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *val,
+              const oz *x, oz *y)
+{
+    for (int32_t i = 0; i < n; ++i) {
+        oz acc = {0.0, 0.0};
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            acc = z_add(acc, z_mul(val[k], x[col[k]]));
+        y[i] = acc;
+    }
+}
+
+/* complex64 SpMV for the inner solve of the mixed-precision refinement */
+void or_cspmv(int32_t n, const int32_t *rowptr, const int32_t *col, const oc *val,
+              const oc *x, oc *y)
+{
+    for (int32_t i = 0; i < n; ++i) {
+        oc acc = {0.0f, 0.0f};
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            acc = c_add(acc, c_mul(val[k], x[col[k]]));
+        y[i] = acc;
+    }
+}
+
+/* Section 5, dot product: sum_i conj(x_i) y_i (conjugated) */
+void or_zdotc(int64_t n, const oz *x, const oz *y, oz *out)
+{
+    ksum re = {0, 0}, im = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        oz p = z_mul(z_conj(x[i]), y[i]);
+        ks_add(&re, p.re);
+        ks_add(&im, p.im);
+    }
+    out->re = ks_val(&re);
+    out->im = ks_val(&im);
+}
+
+/* Section 5, dot product without conjugation: sum_i x_i y_i */
+void or_zdotu(int64_t n, const oz *x, const oz *y, oz *out)
+{
+    ksum re = {0, 0}, im = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        oz p = z_mul(x[i], y[i]);
+        ks_add(&re, p.re);
+        ks_add(&im, p.im);
+    }
+    out->re = ks_val(&re);
+    out->im = ks_val(&im);
+}
+
+/* Section 5, L2 norm: sqrt(sum_i |x_i|^2) */
+double or_dznrm2(int64_t n, const oz *x)
+{
+    ksum s = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        ks_add(&s, x[i].re * x[i].re);
+        ks_add(&s, x[i].im * x[i].im);
+    }
+    return sqrt(ks_val(&s));
+}
+
+/* Section 5, Zaxpy: y_i = alpha x_i + y_i */
+void or_zaxpy(int64_t n, const oz *alpha, const oz *x, oz *y)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = z_add(z_mul(*alpha, x[i]), y[i]);
+}
+
+/* Section 5, scale: x_i = alpha x_i */
+void or_zscal(int64_t n, const oz *alpha, oz *x)
+{
+    for (int64_t i = 0; i < n; ++i) x[i] = z_mul(*alpha, x[i]);
+}
+
+/* Section 5, assign: y_i = x_i */
+void or_zcopy(int64_t n, const oz *x, oz *y)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = x[i];
+}
+
+/* ---------------------------------------------------------------------- */
+/* Section 7: BiCGStab (van der Vorst's method as given in Saad's "Iterative
+ * Methods for Sparse Linear Systems", which the paper cites), without a
+ * preconditioner, with the Hermitian inner product <u,w> = sum conj(u_i) w_i.
+ *
+ *   r = b - A x;  rh = r;  rho_old = alpha = omega = 1;  v = p = 0
+ *   loop:  rho = <rh, r>;  beta = (rho/rho_old)(alpha/omega)
+ *          p = r + beta (p - omega v);  v = A p;  alpha = rho / <rh, v>
+ *          s = r - alpha v;   stop with x += alpha p if ||s|| <= tol ||b||
+ *          t = A s;  omega = <t, s> / <t, t>
+ *          x += alpha p + omega s;  r = s - omega t;  rho_old = rho
+ *          stop if ||r|| <= tol ||b||
+ *
+ * Stopping test: relative 2-norm residual against ||b||.  Breakdown: rho == 0
+ * or omega == 0 or <rh, v> == 0 (exact zeros).  After the loop the true
+ * residual ||b - A x|| / ||b|| is formed; if it exceeds tol while the
+ * recursive one did not, the iteration restarts once from the current x.
+ *
+ * hist (optional, length maxit+1): hist[0] = ||r0||/||b||, hist[j] = the
+ * recursive residual ratio after iteration j (||s|| for a half-step exit).
+ */
+typedef struct {
+    int32_t iters;
+    int32_t status;
+    int32_t restarts;
+    double relres_rec;
+    double relres_true;
+} or_info;
+
+static double z_norm(int64_t n, const oz *x) { return or_dznrm2(n, x); }
+
+int or_bicgstab(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *val,
+                const oz *b, oz *x, double tol, int32_t maxit, double *hist, or_info *info)
+{
+    oz *r = calloc((size_t)n, sizeof(oz)), *rh = calloc((size_t)n, sizeof(oz));
+    oz *p = calloc((size_t)n, sizeof(oz)), *v = calloc((size_t)n, sizeof(oz));
+    oz *s = calloc((size_t)n, sizeof(oz)), *t = calloc((size_t)n, sizeof(oz));
+    double nb = z_norm(n, b);
+    int32_t it = 0, status = OR_NOT_CONVERGED, restarts = 0;
+    double rel = 0.0;
+
+    if (nb == 0.0) {                     /* b = 0: the solution is x = 0 */
+        memset(x, 0, (size_t)n * sizeof(oz));
+        info->iters = 0; info->status = OR_OK; info->restarts = 0;
+        info->relres_rec = 0.0; info->relres_true = 0.0;
+        if (hist) hist[0] = 0.0;
+        free(r); free(rh); free(p); free(v); free(s); free(t);
+        return OR_OK;
+    }
+
+    for (;;) {                           /* at most one restart */
+        oz rho_old = {1, 0}, alpha = {1, 0}, omega = {1, 0};
+        or_zspmv(n, rowptr, col, val, x, r);
+        for (int32_t i = 0; i < n; ++i) { r[i] = z_sub(b[i], r[i]); rh[i] = r[i]; }
+        memset(p, 0, (size_t)n * sizeof(oz));
+        memset(v, 0, (size_t)n * sizeof(oz));
+        rel = z_norm(n, r) / nb;
+        if (hist && it == 0) hist[0] = rel;
+        if (!isfinite(rel)) { status = OR_NAN; break; }
+        if (rel <= tol) { status = OR_OK; }
+        else {
+            status = OR_NOT_CONVERGED;
+            while (it < maxit) {
+                oz rho, sig, ts, tt, beta;
+                ++it;
+                or_zdotc(n, rh, r, &rho);
+                if (rho.re == 0.0 && rho.im == 0.0) { status = OR_BREAKDOWN; break; }
+                beta = z_mul(z_div(rho, rho_old), z_div(alpha, omega));
+                for (int32_t i = 0; i < n; ++i)
+                    p[i] = z_add(r[i], z_mul(beta, z_sub(p[i], z_mul(omega, v[i]))));
+                or_zspmv(n, rowptr, col, val, p, v);
+                or_zdotc(n, rh, v, &sig);
+                if (sig.re == 0.0 && sig.im == 0.0) { status = OR_BREAKDOWN; break; }
+                alpha = z_div(rho, sig);
+                for (int32_t i = 0; i < n; ++i) s[i] = z_sub(r[i], z_mul(alpha, v[i]));
+                rel = z_norm(n, s) / nb;
+                if (!isfinite(rel)) { status = OR_NAN; break; }
+                if (rel <= tol) {        /* half-step exit */
+                    for (int32_t i = 0; i < n; ++i) x[i] = z_add(x[i], z_mul(alpha, p[i]));
+                    if (hist) hist[it] = rel;
+                    status = OR_OK;
+                    break;
+                }
+                or_zspmv(n, rowptr, col, val, s, t);
+                or_zdotc(n, t, s, &ts);
+                or_zdotc(n, t, t, &tt);
+                if (tt.re == 0.0 && tt.im == 0.0) { status = OR_BREAKDOWN; break; }
+                omega = z_div(ts, tt);
+                for (int32_t i = 0; i < n; ++i) {
+                    x[i] = z_add(x[i], z_add(z_mul(alpha, p[i]), z_mul(omega, s[i])));
+                    r[i] = z_sub(s[i], z_mul(omega, t[i]));
+                }
+                rho_old = rho;
+                rel = z_norm(n, r) / nb;
+                if (hist) hist[it] = rel;
+                if (!isfinite(rel)) { status = OR_NAN; break; }
+                if (rel <= tol) { status = OR_OK; break; }
+                if (omega.re == 0.0 && omega.im == 0.0) { status = OR_BREAKDOWN; break; }
+            }
+        }
+        /* true residual */
+        or_zspmv(n, rowptr, col, val, x, t);
+        for (int32_t i = 0; i < n; ++i) t[i] = z_sub(b[i], t[i]);
+        info->relres_true = z_norm(n, t) / nb;
+        info->relres_rec = rel;
+        if (status == OR_OK && info->relres_true > tol && restarts == 0 && it < maxit) {
+            ++restarts;
+            continue;
+        }
+        if (status == OR_OK && info->relres_true > tol) status = OR_NOT_CONVERGED;
+        break;
+    }
+    info->iters = it;
+    info->status = status;
+    info->restarts = restarts;
+    free(r); free(rh); free(p); free(v); free(s); free(t);
+    return status;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Same iteration in complex64 with binary32 sums: the inner solver of the
+ * mixed-precision refinement.  x0 = 0, stopping on ||r|| <= tol ||b||.
+ * Returns the iteration count; *status gets the exit reason. */
+static float c_norm(int32_t n, const oc *x)
+{
+    float s = 0.0f;
+    for (int32_t i = 0; i < n; ++i) s += x[i].re * x[i].re + x[i].im * x[i].im;
+    return sqrtf(s);
+}
+static oc c_dotc(int32_t n, const oc *x, const oc *y)
+{
+    oc s = {0.0f, 0.0f};
+    for (int32_t i = 0; i < n; ++i) s = c_add(s, c_mul(c_conj(x[i]), y[i]));
+    return s;
+}
+
+int32_t or_cbicgstab(int32_t n, const int32_t *rowptr, const int32_t *col, const oc *val,
+                     const oc *b, oc *x, float tol, int32_t maxit, int32_t *status)
+{
+    oc *r = calloc((size_t)n, sizeof(oc)), *rh = calloc((size_t)n, sizeof(oc));
+    oc *p = calloc((size_t)n, sizeof(oc)), *v = calloc((size_t)n, sizeof(oc));
+    oc *s = calloc((size_t)n, sizeof(oc)), *t = calloc((size_t)n, sizeof(oc));
+    oc rho_old = {1, 0}, alpha = {1, 0}, omega = {1, 0};
+    float nb = c_norm(n, b);
+    int32_t it = 0;
+    *status = OR_NOT_CONVERGED;
+    memset(x, 0, (size_t)n * sizeof(oc));
+    if (nb == 0.0f) { *status = OR_OK; goto done; }
+    for (int32_t i = 0; i < n; ++i) { r[i] = b[i]; rh[i] = b[i]; }
+    while (it < maxit) {
+        oc rho, sig, ts, tt, beta;
+        float rel;
+        ++it;
+        rho = c_dotc(n, rh, r);
+        if (rho.re == 0.0f && rho.im == 0.0f) { *status = OR_BREAKDOWN; break; }
+        beta = c_mul(c_div(rho, rho_old), c_div(alpha, omega));
+        for (int32_t i = 0; i < n; ++i)
+            p[i] = c_add(r[i], c_mul(beta, c_sub(p[i], c_mul(omega, v[i]))));
+        or_cspmv(n, rowptr, col, val, p, v);
+        sig = c_dotc(n, rh, v);
+        if (sig.re == 0.0f && sig.im == 0.0f) { *status = OR_BREAKDOWN; break; }
+        alpha = c_div(rho, sig);
+        for (int32_t i = 0; i < n; ++i) s[i] = c_sub(r[i], c_mul(alpha, v[i]));
+        rel = c_norm(n, s) / nb;
+        if (!isfinite(rel)) { *status = OR_NAN; break; }
+        if (rel <= tol) {
+            for (int32_t i = 0; i < n; ++i) x[i] = c_add(x[i], c_mul(alpha, p[i]));
+            *status = OR_OK;
+            break;
+        }
+        or_cspmv(n, rowptr, col, val, s, t);
+        ts = c_dotc(n, t, s);
+        tt = c_dotc(n, t, t);
+        if (tt.re == 0.0f && tt.im == 0.0f) { *status = OR_BREAKDOWN; break; }
+        omega = c_div(ts, tt);
+        for (int32_t i = 0; i < n; ++i) {
+            x[i] = c_add(x[i], c_add(c_mul(alpha, p[i]), c_mul(omega, s[i])));
+            r[i] = c_sub(s[i], c_mul(omega, t[i]));
+        }
+        rho_old = rho;
+        rel = c_norm(n, r) / nb;
+        if (!isfinite(rel)) { *status = OR_NAN; break; }
+        if (rel <= tol) { *status = OR_OK; break; }
+        if (omega.re == 0.0f && omega.im == 0.0f) { *status = OR_BREAKDOWN; break; }
+    }
+done:
+    free(r); free(rh); free(p); free(v); free(s); free(t);
+    return it;
+}
+
+/* Mixed-precision iterative refinement (classical, Wilkinson/Moler):
+ *   repeat: r = b - A x (binary64);  stop if ||r|| <= tol ||b||
+ *           solve A d = r approximately in complex64 (inner BiCGStab, tol_in)
+ *           x = x + d (binary64)
+ * The complex64 operator is the rounded copy val32 of val. */
+int or_refine_mixed(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *val,
+                    const oc *val32, const oz *b, oz *x, double tol, float tol_in,
+                    int32_t maxit_in, int32_t max_outer, int32_t *outer_out,
+                    int32_t *inner_total, double *relres_out)
+{
+    oz *r = calloc((size_t)n, sizeof(oz));
+    oc *r32 = calloc((size_t)n, sizeof(oc)), *d32 = calloc((size_t)n, sizeof(oc));
+    double nb = z_norm(n, b), rel = 0.0;
+    int32_t outer = 0, inner = 0, status = OR_NOT_CONVERGED;
+    if (nb == 0.0) {
+        memset(x, 0, (size_t)n * sizeof(oz));
+        status = OR_OK;
+    } else {
+        for (;;) {
+            int32_t st, k;
+            or_zspmv(n, rowptr, col, val, x, r);
+            for (int32_t i = 0; i < n; ++i) r[i] = z_sub(b[i], r[i]);
+            rel = z_norm(n, r) / nb;
+            if (!isfinite(rel)) { status = OR_NAN; break; }
+            if (rel <= tol) { status = OR_OK; break; }
+            if (outer >= max_outer) break;
+            ++outer;
+            for (int32_t i = 0; i < n; ++i) { r32[i].re = (float)r[i].re; r32[i].im = (float)r[i].im; }
+            k = or_cbicgstab(n, rowptr, col, val32, r32, d32, tol_in, maxit_in, &st);
+            inner += k;
+            for (int32_t i = 0; i < n; ++i) {
+                x[i].re += (double)d32[i].re;
+                x[i].im += (double)d32[i].im;
+            }
+        }
+    }
+    *outer_out = outer;
+    *inner_total = inner;
+    *relres_out = rel;
+    free(r); free(r32); free(d32);
+    return status;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Adjoint of x = A^{-1} b for a complex-symmetric A (A = A^T): with mu the
+ * solution of A^T mu = conj(g), where g is the conjugate-Wirtinger gradient
+ * of a real loss with respect to x, the gradient with respect to the stored
+ * entry A_ij is -conj(mu_i x_j).  This routine forms that product on A's
+ * sparsity pattern. */
+void or_outer_on_pattern(int32_t n, const int32_t *rowptr, const int32_t *col,
+                         const oz *mu, const oz *x, oz *grad)
+{
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            oz m = z_mul(mu[i], x[col[k]]);
+            grad[k].re = -m.re;
+            grad[k].im = m.im;
+        }
+}

@@ -1,0 +1,240 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle (oracle/hz_oracle.c) against something other
+than itself: the paper's worked CSR example (Section 3.2), brute-force dense
+products, closed-form eigenpairs of the finite-difference Laplacian, exact
+integer arithmetic, dense LU, constructed breakdowns and finite differences.
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from tests import _cases as K
+
+
+# --------------------------------------------------------------------------- SpMV
+def test_worked_example_structure():
+    """The CSR arrays of the paper's 5x5 example match its printed pattern
+    and the 1-based end marker IA(n+1) = nz + 1 (Section 3.2)."""
+    dense, pattern = K.worked_example()
+    A = K.worked_example_csr()
+    assert A.n == 5 and A.nnz == 11 == len(pattern)
+    rows = np.repeat(np.arange(5), np.diff(A.rowptr))
+    assert [(int(r) + 1, int(c) + 1) for r, c in zip(rows, A.col)] == pattern
+    assert int(A.rowptr[-1]) + 1 == 12
+    assert list(A.rowptr) == [0, 2, 4, 6, 9, 11]
+    assert list(A.col) == [0, 1, 1, 2, 0, 2, 1, 3, 4, 2, 4]
+    assert list(A.val.real) == [3, 14, 8, 1, 2, 6, 4, 2, -1, 9, 7]
+
+
+def test_worked_example_products(oracle):
+    dense, _ = K.worked_example()
+    for scale in (1.0, 1 + 2j):
+        A = K.worked_example_csr(scale)
+        y = oracle.zspmv(A, np.ones(5, dtype=np.complex128))
+        assert np.array_equal(y, np.array([17, 9, 8, 5, 16]) * scale)
+        for j in range(5):
+            e = np.zeros(5, dtype=np.complex128)
+            e[j] = 1.0
+            assert np.array_equal(oracle.zspmv(A, e), dense[:, j] * scale)
+
+
+@pytest.mark.parametrize("seed,n", [(1, 1), (2, 17), (3, 300), (4, 999)])
+def test_spmv_brute_force_dense(oracle, seed, n):
+    A = K.random_csr(n, seed, max_row=30, long_rows=(n,) if n > 100 else ())
+    x = K.vectors(n, seed + 10)[0]
+    ref = A.to_scipy().toarray() @ x
+    assert np.all(np.abs(oracle.zspmv(A, x) - ref) <= 1e-13 * K.row_abs_scale(A, x) + 1e-300)
+
+
+def test_spmv_complex_symmetry_invariant(oracle):
+    """Helmholtz matrices are complex symmetric: u^T (A v) = v^T (A u)."""
+    for A in (W.c1_small_fd()[0], K.small_cylinder()[0]):
+        u, v = K.vectors(A.n, 33)
+        lhs = np.sum(u * oracle.zspmv(A, v))
+        rhs = np.sum(v * oracle.zspmv(A, u))
+        assert abs(lhs - rhs) <= 1e-12 * np.sum(np.abs(u) * K.row_abs_scale(A, v))
+        S = A.to_scipy()
+        assert abs(S - S.T).max() <= 1e-14 * abs(S).max()
+
+
+def test_fd_closed_form_eigenpairs(oracle):
+    """-Lap_h v = lambda v for the sine modes; A v = (lambda - k^2(1+0.05i)) v."""
+    A, _, _ = W.c1_small_fd()
+    m, k = 16, 8.5
+    assert abs(A.meta["k"] - k) < 1e-12
+    shift = k * k * (1 + 0.05j)
+    for (a, b, c) in ((1, 1, 1), (3, 5, 7), (16, 16, 16), (2, 9, 1)):
+        lam, v = W.fd_laplacian_eig(m, a, b, c)
+        mu = lam - shift
+        assert np.allclose(oracle.zspmv(A, v), mu * v, rtol=0, atol=1e-10 * abs(lam))
+    lam_min, _ = W.fd_laplacian_eig(m, 1, 1, 1)
+    lam_max, _ = W.fd_laplacian_eig(m, 16, 16, 16)
+    assert abs(lam_min - 29.52) < 0.01 and abs(lam_max - 3438.5) < 0.1   # derived: C1 spectrum
+
+
+def test_fd_closed_form_solve(oracle):
+    A, _, _ = W.c1_small_fd()
+    lam, v = W.fd_laplacian_eig(16, 2, 3, 4)
+    mu = lam - 72.25 * (1 + 0.05j)
+    x, info = oracle.bicgstab(A, v, tol=1e-12, maxit=500)
+    assert info.status == 0
+    assert np.linalg.norm(x - v / mu) <= 1e-10 * np.linalg.norm(v / mu)
+
+
+# --------------------------------------------------------------------------- FEM generator invariants
+def test_cylinder_fem_invariants():
+    nr, nth, nz, R, L = 6, 16, 20, 1.0, 4.0
+    A, b, parts = W.cylinder_helmholtz(nr, nth, nz, kh=0.5, damping=0.05, jitter=0.2, seed=7,
+                                       rcm=False, return_parts=True)
+    Kst, M, B, xyz = parts["K"], parts["M"], parts["B"], parts["xyz"]
+    one = np.ones(Kst.shape[0])
+    assert np.abs(Kst @ one).max() < 1e-10 * abs(Kst).max()                  # K 1 = 0
+    vol = 0.5 * nth * np.sin(2 * np.pi / nth) * R * R * L                     # polygonal cylinder
+    assert abs(one @ (M @ one) - vol) < 1e-10 * vol                           # jitter keeps volume
+    area = 0.5 * nth * np.sin(2 * np.pi / nth) * R * R
+    assert abs(one @ (B @ one) - 2 * area) < 1e-10 * area                      # two end faces
+    assert abs(Kst - Kst.T).max() < 1e-12 * abs(Kst).max()
+    # linear fields are in the P1 space: K u = 0 away from the boundary
+    u = 0.3 * xyz[:, 0] - 1.1 * xyz[:, 1] + 0.7 * xyz[:, 2]
+    r = np.hypot(xyz[:, 0], xyz[:, 1])
+    per = 1 + nr * nth
+    k = np.arange(xyz.shape[0]) // per
+    loc = np.arange(xyz.shape[0]) % per
+    ring = np.where(loc == 0, 0, (loc - 1) // nth + 1)
+    interior = (ring < nr) & (k > 0) & (k < nz)
+    assert np.abs((Kst @ u)[interior]).max() < 1e-10 * abs(Kst).max()
+    assert r.max() <= R + 1e-12
+
+
+# --------------------------------------------------------------------------- BLAS-1
+def test_blas1_closed_forms(oracle):
+    n = 4096
+    phi = np.random.default_rng(5).uniform(0, 2 * np.pi, n)
+    x = np.exp(1j * phi)
+    assert abs(oracle.dznrm2(x) ** 2 - n) < 1e-11 * n
+    d = oracle.zdotc(x, x)
+    assert abs(d - n) < 1e-11 * n and d.imag == 0.0
+    one = np.ones(n, dtype=np.complex128)
+    assert oracle.zdotc((1 + 1j) * one, (2 - 1j) * one) == n * (1 - 3j)
+    assert oracle.zdotu((1 + 1j) * one, (2 - 1j) * one) == n * (3 + 1j)
+    u, v = K.vectors(n, 8)
+    assert abs(oracle.zdotc(u, v) - oracle.zdotu(np.conj(u), v)) <= 1e-13 * np.sum(np.abs(u * v))
+    assert abs(oracle.zdotc(u, v) - np.conj(oracle.zdotc(v, u))) <= 1e-13 * np.sum(np.abs(u * v))
+
+
+def test_blas1_exact_integer_data(oracle):
+    rng = np.random.default_rng(6)
+    x = rng.integers(-50, 50, 1000) + 1j * rng.integers(-50, 50, 1000)
+    y = rng.integers(-50, 50, 1000) + 1j * rng.integers(-50, 50, 1000)
+    a = 3 - 2j
+    assert np.array_equal(oracle.zaxpy(a, x, y), a * x + y)
+    assert np.array_equal(oracle.zscal(a, x), a * x)
+    assert np.array_equal(oracle.zcopy(x), x)
+    assert oracle.zdotc(x, y) == np.vdot(x, y)
+    assert oracle.zdotu(x, y) == np.sum(x * y)
+
+
+# --------------------------------------------------------------------------- BiCGStab
+def test_bicgstab_dense_lu_8cubed(oracle):
+    A = W.fd_helmholtz_box(8, kh=0.5, damping=0.05)
+    b = K.vectors(A.n, 1001)[0]
+    x_lu = np.linalg.solve(A.to_scipy().toarray(), b)
+    x, info = oracle.bicgstab(A, b, tol=1e-10, maxit=2000)
+    assert info.status == 0 and info.relres_true <= 1e-10
+    assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) <= 1e-8
+    assert info.hist[0] == 1.0 and info.hist[-1] <= 1e-10
+
+
+def test_bicgstab_general_nonsymmetric_dense_lu(oracle):
+    """The iteration itself does not rely on symmetry: a random diagonally
+    dominant complex matrix against dense LU."""
+    A = K.random_csr(200, 12, max_row=10)
+    S = A.to_scipy().tolil()
+    S.setdiag(S.diagonal() + 12.0 + 3j)
+    A = W.CSR.from_scipy(S.tocsr())
+    b = K.vectors(200, 13)[0]
+    x, info = oracle.bicgstab(A, b, tol=1e-12, maxit=500)
+    x_lu = np.linalg.solve(A.to_scipy().toarray(), b)
+    assert info.status == 0
+    assert np.linalg.norm(x - x_lu) <= 1e-10 * np.linalg.norm(x_lu)
+
+
+def test_bicgstab_manufactured(oracle):
+    A, _, xs = W.c1_small_fd()
+    b = A.to_scipy() @ xs
+    x, info = oracle.bicgstab(A, b, tol=1e-12, maxit=2000)
+    assert info.status == 0 and np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-8
+
+
+def test_bicgstab_identity_half_step(oracle):
+    """A = I: one step, exact half-step exit with x = b."""
+    A = W.CSR.from_scipy(sp.identity(50, dtype=np.complex128, format="csr"))
+    b = K.vectors(50, 2)[0]
+    x, info = oracle.bicgstab(A, b, tol=1e-10)
+    assert info.status == 0 and info.iters == 1 and np.array_equal(x, b)
+
+
+def test_bicgstab_special_cases(oracle):
+    A, b, _ = W.c1_small_fd()
+    x, info = oracle.bicgstab(A, np.zeros(A.n, np.complex128), x0=np.ones(A.n))
+    assert info.status == 0 and info.iters == 0 and not x.any()
+    x, info = oracle.bicgstab(A, b, maxit=0)
+    assert info.status == 4 and info.iters == 0 and not x.any()
+    x, info = oracle.bicgstab(K.breakdown_2x2(), np.array([1, 0], dtype=np.complex128))
+    assert info.status == 5 and info.iters == 1
+    bn = b.copy()
+    bn[0] = np.nan
+    x, info = oracle.bicgstab(A, bn)
+    assert info.status == 6
+
+
+def test_mixed_refinement(oracle):
+    A, b, _ = W.c1_small_fd()
+    x, d = oracle.refine_mixed(A, b, tol=1e-10)
+    x_lu = np.linalg.solve(A.to_scipy().toarray(), b)
+    assert d["status"] == 0 and d["relres"] <= 1e-10 and d["outer"] >= 2
+    assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) <= 1e-8
+    # the inner solve alone stops near single precision
+    x32, it, st = oracle.cbicgstab(A, b.astype(np.complex64), tol=1e-5)
+    r = np.linalg.norm(b - A.to_scipy() @ x32.astype(np.complex128)) / np.linalg.norm(b)
+    assert 1e-8 < r < 1e-4
+
+
+# --------------------------------------------------------------------------- adjoint
+def test_adjoint_oracle_gradient(oracle):
+    """Oracle chain (solve, adjoint solve, outer product on the pattern) against
+    the dense-LU gradient and central differences of the loss."""
+    m = 6
+    A = W.fd_helmholtz_box(m, kh=0.5, damping=0.05)
+    n = A.n
+    b = K.vectors(n, 50)[0]
+    idx = np.arange(0, n, 7)
+    d = K.vectors(idx.size, 51)[0]
+    S = A.to_scipy().toarray()
+
+    def loss_dense(Sm):
+        x = np.linalg.solve(Sm, b)
+        return float(np.sum(np.abs(x[idx] - d) ** 2)), x
+
+    L0, x_lu = loss_dense(S)
+    x, _ = oracle.bicgstab(A, b, tol=1e-13, maxit=5000)
+    g = np.zeros(n, dtype=np.complex128)
+    g[idx] = 2 * (x[idx] - d)
+    mu, info = oracle.bicgstab(A, np.conj(g), tol=1e-13, maxit=5000)
+    grad_val = oracle.outer_on_pattern(A, mu, x)
+    lam = np.linalg.solve(S.conj().T, g)
+    rows = np.repeat(np.arange(n), np.diff(A.rowptr))
+    grad_lu = -lam[rows] * np.conj(x_lu[A.col])
+    assert np.linalg.norm(grad_val - grad_lu) <= 1e-8 * np.linalg.norm(grad_lu)
+    # central differences along random directions on the stored entries
+    rng = np.random.default_rng(52)
+    eps = 1e-4   # the directional derivatives here are ~1e-5 of the loss: keep FD round-off small
+    for _ in range(3):
+        v = rng.standard_normal(A.nnz) + 1j * rng.standard_normal(A.nnz)
+        dA = sp.csr_matrix((v, A.col, A.rowptr), shape=(n, n)).toarray()
+        fd = (loss_dense(S + eps * dA)[0] - loss_dense(S - eps * dA)[0]) / (2 * eps)
+        an = float(np.real(np.vdot(grad_val, v)))
+        assert abs(fd - an) <= 1e-5 * max(abs(fd), 1e-12)   # FD round-off ~ eps_mach L / eps

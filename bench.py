@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Benchmark of the complex Helmholtz Krylov path on GB300.
+
+One step = one full FP64 BiCGStab solve (Section 7 of the paper: CSR SpMV +
+fused zdot/zaxpy/norm kernels, device-side loop in a CUDA graph) of the C2
+workload: the jittered P1-FEM cylinder (nr=40, ntheta=96, nz=160, k=20,
+impedance ends; 618,401 unknowns, 9.18M nonzeros), from x0 = 0 with
+tol 1e-10 and a fixed iteration cap (the cap is reached: preconditioner-free
+BiCGStab does not converge on this indefinite k=20 operator, so every step
+performs the same work).
+
+value  = algorithmic bytes moved by the solve / device time of the step
+         (40*nnz + 312*n bytes per iteration + setup and exit passes), GB/s.
+e2e    = the same bytes over the wall time of the public-API call sequence
+         with host buffers: pinned H2D of the CSR arrays and b, matrix
+         handle creation, solve, D2H of x.
+roofline = the dominant kernel (the CSR SpMV core) timed alone with CUDA
+         events on its stream, L2 flushed between launches.
+cpu_baseline / --impl reference = the C oracle (single thread) on a bounded
+         number of BiCGStab iterations of the same system.
+
+Multi-GPU (torchrun, N > 1): replicas -- every rank solves its own copy of
+the system on its own GPU (weak scaling, no collective on the data path);
+value sums the ranks' bytes over the slowest rank's time.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "zSpMV GB/s (% HBM peak); BiCGStab s to rel.res 1e-10, mixed/batched vs FP64"
+L2_BYTES = 129 * 1024 * 1024
+FALLBACK_HBM_GBS = 6800.0
+
+
+def spmv_bytes(n, nnz):
+    """Algorithmic bytes of one CSR SpMV: values and columns once, row
+    pointers once, x read once, y written once."""
+    return 20 * nnz + 36 * n + 4
+
+
+def iter_bytes(n, nnz):
+    """Algorithmic bytes of one fused BiCGStab iteration (two SpMVs plus the
+    vector passes F1..F5)."""
+    return 40 * nnz + 312 * n
+
+
+def solve_bytes(n, nnz, iters):
+    # start (x0 copy 32n, r = b - A x: SpMV + b 16n + writes r, rh, p, v 64n)
+    # + iterations + exit (true residual SpMV + b 16n, copy-out 32n)
+    start = 32 * n + spmv_bytes(n, nnz) + 16 * n + 64 * n
+    finish = spmv_bytes(n, nnz) + 16 * n + 32 * n
+    return start + iters * iter_bytes(n, nnz) + finish
+
+
+def job_totals(elapsed, nbytes, world, device):
+    """Whole-job totals over replicas: the slowest rank's time and the sum of
+    every rank's bytes (each rank solves its own system: weak scaling)."""
+    if world <= 1:
+        return elapsed, nbytes
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    b = torch.tensor([float(nbytes)], dtype=torch.float64, device=device)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(b.item())
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("spmv.cuh", "hz_internal.cuh", "spmv.cu"):
+        with open(os.path.join(ROOT, "paper_2112_06465_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per SpMV launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "spmv_csr_c2_traffic.txt")
+    try:
+        kv = {}
+        with open(p) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha") != kernel_source_sha():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        if not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload():
+    import workloads as W
+    A, b = W.c2_cylinder()
+    return A, b
+
+
+def cpu_oracle_rate(A, b, iters):
+    """The oracle's BiCGStab for a fixed number of iterations; returns (GB/s, seconds)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    x, info = oracle.bicgstab(A, b, tol=1e-300, maxit=iters, history=False)
+    dt = time.perf_counter() - t0
+    return solve_bytes(A.n, A.nnz, info.iters) / dt / 1e9, dt, info.iters
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    A, b = build_workload()
+    iters = args.ref_iters
+    for _ in range(args.warmup):
+        cpu_oracle_rate(A, b, 2)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt, it = cpu_oracle_rate(A, b, iters)
+        rates.append(r)
+        times.append(dt)
+    value = statistics.median(rates)
+    sample = f"{iters} BiCGStab iterations of C2 per step (n={A.n}, nnz={A.nnz})"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": workload_config(A, iters),
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+DTYPES = {"fp64": "f64", "ff": "f32x2 (double-float complex128: hi+lo binary32 pairs)"}
+
+
+def workload_config(A, maxit, arith="fp64"):
+    return {"workload": "C2 jittered P1-FEM cylinder nr=40 ntheta=96 nz=160 k=20 impedance ends, "
+                        f"complex128 BiCGStab x0=0 tol=1e-10 maxit={maxit}",
+            "arith": arith, "n": A.n, "nnz": A.nnz, "maxit": maxit,
+            "l2": "inputs larger than L2 (CSR matrix %.0f MB > 129 MB L2); the SpMV roofline "
+                  "launches flush L2 between launches" % (A.nnz * 20 / 1e6)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hz", choices=["hz", "reference"])
+    ap.add_argument("--maxit", type=int, default=1000)
+    ap.add_argument("--arith", default="ff", choices=["ff", "fp64"])
+    ap.add_argument("--ref-iters", type=int, default=60)
+    ap.add_argument("--cpu-iters", type=int, default=150)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2112_06465_gb300 as hz
+    from paper_2112_06465_gb300 import hz as hzmod
+
+    A, b = build_workload()
+    rp = torch.as_tensor(A.rowptr).to(dev)
+    cl = torch.as_tensor(A.col).to(dev)
+    vl = torch.as_tensor(A.val).to(dev)
+    bd = torch.as_tensor(b).to(dev)
+    M = hz.Matrix(rp, cl, vl, ff=args.arith == "ff")
+    xd = torch.zeros_like(bd)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- device-resident solve steps
+    for _ in range(args.warmup):
+        hz.zsolve(M, bd, x=xd, tol=1e-10, maxit=args.maxit)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    infos = []
+    barrier()
+    with ClockSampler(local) as clk:
+        for e0, e1 in ev:
+            e0.record(stream)
+            _, info = hz.zsolve(M, bd, x=xd, tol=1e-10, maxit=args.maxit)
+            e1.record(stream)
+            infos.append(info)
+        barrier()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_ms = sum(step_ms)
+    iters = [i.iters for i in infos]
+    my_bytes = sum(solve_bytes(A.n, A.nnz, it) for it in iters)
+    t_max, all_bytes = job_totals(total_ms, my_bytes, world, dev)
+    value = all_bytes / (t_max / 1e3) / 1e9
+
+    # ---------------- end to end through the public API with host buffers
+    h_rp = torch.as_tensor(A.rowptr).pin_memory()
+    h_cl = torch.as_tensor(A.col).pin_memory()
+    h_vl = torch.as_tensor(A.val).pin_memory()
+    h_b = torch.as_tensor(b).pin_memory()
+    h_x = torch.empty_like(h_b).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in (h_rp, h_cl, h_vl, h_b))
+    d2h = h_x.numel() * h_x.element_size()
+    e2e_times, e2e_bytes = [], 0
+    for k in range(args.warmup + args.steps):
+        barrier()
+        t0 = time.perf_counter()
+        d_rp = h_rp.to(dev, non_blocking=True)
+        d_cl = h_cl.to(dev, non_blocking=True)
+        d_vl = h_vl.to(dev, non_blocking=True)
+        d_b = h_b.to(dev, non_blocking=True)
+        M2 = hz.Matrix(d_rp, d_cl, d_vl, ff=args.arith == "ff")
+        x2, inf2 = hz.zsolve(M2, d_b, tol=1e-10, maxit=args.maxit)
+        h_x.copy_(x2, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        M2.close()
+        if k >= args.warmup:
+            e2e_times.append(dt)
+            e2e_bytes += solve_bytes(A.n, A.nnz, inf2.iters)
+    e2e_t, e2e_bytes = job_totals(sum(e2e_times), e2e_bytes, world, dev)
+    e2e_value = e2e_bytes / e2e_t / 1e9
+
+    # ---------------- roofline of the dominant kernel: the CSR SpMV core
+    # Every launch is preceded by a 1 GiB write (flushes the 129 MB L2 and
+    # keeps the GPU busy while the host enqueues the next launch, so host
+    # launch latency never lands between the events); all launches are
+    # enqueued before the one synchronisation.
+    x_r = torch.randn(A.n, dtype=torch.complex128, device=dev)
+    y_r = torch.empty_like(x_r)
+    flush = torch.empty(8 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        hz.zspmv(M, x_r, y_r)
+    ev_sp = []
+    for k in range(20):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hz.zspmv(M, x_r, y_r)
+        e1.record(stream)
+        ev_sp.append((e0, e1))
+    torch.cuda.synchronize()
+    sp_ms = [e0.elapsed_time(e1) for e0, e1 in ev_sp]
+    sp_avg = sum(sp_ms) / len(sp_ms)
+    del flush
+    peak, peak_src = peaks()
+    achieved = spmv_bytes(A.n, A.nnz) / (sp_avg / 1e3) / 1e9
+    traffic = recorded_traffic()
+
+    props = M.props()
+    launches = sum(4 + 5 * it for it in iters)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.arith], "data": "synthetic",
+        "config": workload_config(A, args.maxit, args.arith),
+        "solve": {"iters_per_step": iters[0], "status": infos[-1].status_name,
+                  "relres_true": infos[-1].relres_true, "s_per_solve": t_max / args.steps / 1e3,
+                  "iter_us": 1e3 * t_max / args.steps / max(iters[0], 1),
+                  "spmv_variant": {"kind": props["spmv_kind"], "group": props["group"]}},
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_spmv (CSR, %d lanes/row) alone, L2 flushed; peak %s" % (props["group"], peak_src),
+                     "algorithmic_bytes_per_launch": spmv_bytes(A.n, A.nnz), "launch_ms": sp_avg},
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, dt, it = cpu_oracle_rate(A, b, args.cpu_iters)
+        line["cpu_baseline"] = {"value": r, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{it} BiCGStab iterations of C2 ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

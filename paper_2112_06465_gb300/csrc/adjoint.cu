@@ -1,0 +1,123 @@
+// adjoint.cu -- kernels of the adjoint (reverse-mode) solve x = A^{-1} b.
+//
+// For a real loss L with conjugate-Wirtinger gradient g = 2 dL/d(conj x),
+// and mu the solution of A^T mu = conj(g) (A complex symmetric, so the same
+// operator as the forward solve), the gradients are
+//     dL/dA_ij (stored entries)  = -conj(mu_i x_j)
+//     dL/db                      =  conj(mu)
+// and for a diagonal parametrised as A_ii = base_i + c * theta_i,
+//     dL/dtheta_i                =  conj(c) * (-conj(mu_i x_i)).
+#include <algorithm>
+#include <vector>
+
+#include "hz_internal.cuh"
+
+namespace hz {
+
+// one warp per row: every stored entry (i, j) gets -conj(mu_i x_j)
+__global__ void __launch_bounds__(256) k_outer_pattern(int n, const int *__restrict__ rowptr,
+                                                       const int *__restrict__ col, const double2 *__restrict__ mu,
+                                                       const double2 *__restrict__ x, double2 *__restrict__ g) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const double2 m = mu[i];
+        const int beg = rowptr[i], end = rowptr[i + 1];
+        for (int k = beg + lane; k < end; k += 32) {
+            const double2 xj = __ldg(x + col[k]);
+            const double2 p = cmul(m, xj);
+            g[k] = make_double2(-p.x, p.y);
+        }
+    }
+}
+
+// position of the diagonal entry of every row (-1 if absent)
+__global__ void k_find_diag(int n, const int *__restrict__ rowptr, const int *__restrict__ col, int *__restrict__ pos) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int f = -1;
+        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            if (col[k] == i) { f = k; break; }
+        pos[i] = f;
+    }
+}
+
+__global__ void k_set_diag(int n, const int *__restrict__ pos, const double2 *__restrict__ base, double2 c,
+                           const double2 *__restrict__ theta, double2 *__restrict__ val) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double2 v = base[i];
+        cmac(v, c, theta[i]);
+        val[pos[i]] = v;
+    }
+}
+
+__global__ void k_diag_grad(int n, const double2 *__restrict__ mu, const double2 *__restrict__ x, double2 c,
+                            double2 *__restrict__ gt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double2 p = cmul(mu[i], x[i]);
+        const double2 ga = make_double2(-p.x, p.y);          // -conj(mu_i x_i)
+        gt[i] = cmul(cconj(c), ga);
+    }
+}
+
+static hz_status ensure_diag(hz_mat *A, cudaStream_t s) {
+    if (A->diag_pos) return HZ_OK;
+    HZ_CUDA(cudaMalloc(&A->diag_pos, sizeof(int) * std::max(A->n, 1)));
+    k_find_diag<<<std::max(1, std::min(4096, (A->n + 255) / 256)), 256, 0, s>>>(A->n, A->rowptr, A->col, A->diag_pos);
+    HZ_CUDA(cudaGetLastError());
+    std::vector<int> pos(A->n);
+    HZ_CUDA(cudaMemcpyAsync(pos.data(), A->diag_pos, sizeof(int) * A->n, cudaMemcpyDeviceToHost, s));
+    HZ_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < A->n; ++i)
+        if (pos[i] < 0) {
+            cudaFree(A->diag_pos);
+            A->diag_pos = nullptr;
+            set_error("hz_mat_set_diag: row " + std::to_string(i) + " stores no diagonal entry");
+            return HZ_ERR_ARG;
+        }
+    return HZ_OK;
+}
+
+static int grid_for(int64_t n) {
+    DevInfo d;
+    if (dev_info(&d) != HZ_OK) return 1;
+    return stream_grid(d, n, 256, 8);
+}
+
+}  // namespace hz
+
+using namespace hz;
+
+extern "C" HZ_API hz_status hz_outer_on_pattern(const hz_mat *A, const hz_z *d_mu, const hz_z *d_x,
+                                                hz_z *d_gradval, void *stream) {
+    HZ_CHECK(A, "hz_outer_on_pattern: null handle");
+    if (A->n == 0 || A->nnz == 0) return HZ_OK;
+    HZ_CHECK(d_mu && d_x && d_gradval, "hz_outer_on_pattern: null vector");
+    k_outer_pattern<<<grid_for((int64_t)A->n * 32), 256, 0, (cudaStream_t)stream>>>(
+        A->n, A->rowptr, A->col, (const double2 *)d_mu, (const double2 *)d_x, (double2 *)d_gradval);
+    HZ_CUDA(cudaGetLastError());
+    return HZ_OK;
+}
+
+extern "C" HZ_API hz_status hz_mat_set_diag(hz_mat *A, const hz_z *d_base, hz_z scale, const hz_z *d_theta,
+                                            void *stream) {
+    HZ_CHECK(A, "hz_mat_set_diag: null handle");
+    if (A->n == 0) return HZ_OK;
+    HZ_CHECK(d_base && d_theta, "hz_mat_set_diag: null vector");
+    cudaStream_t s = (cudaStream_t)stream;
+    HZ_TRY(ensure_diag(A, s));
+    k_set_diag<<<grid_for(A->n), 256, 0, s>>>(A->n, A->diag_pos, (const double2 *)d_base,
+                                               make_double2(scale.re, scale.im), (const double2 *)d_theta, A->val);
+    HZ_CUDA(cudaGetLastError());
+    return hz_mat_refresh_values(A, stream);
+}
+
+extern "C" HZ_API hz_status hz_diag_grad(const hz_mat *A, const hz_z *d_mu, const hz_z *d_x, hz_z scale,
+                                         hz_z *d_grad_theta, void *stream) {
+    HZ_CHECK(A, "hz_diag_grad: null handle");
+    if (A->n == 0) return HZ_OK;
+    HZ_CHECK(d_mu && d_x && d_grad_theta, "hz_diag_grad: null vector");
+    k_diag_grad<<<grid_for(A->n), 256, 0, (cudaStream_t)stream>>>(
+        A->n, (const double2 *)d_mu, (const double2 *)d_x, make_double2(scale.re, scale.im), (double2 *)d_grad_theta);
+    HZ_CUDA(cudaGetLastError());
+    return HZ_OK;
+}

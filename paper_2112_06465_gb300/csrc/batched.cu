@@ -1,0 +1,492 @@
+// batched.cu -- a sweep of independent BiCGStab solves (one per frequency or
+// geometry) in ONE persistent cooperative launch.
+//
+// Every system keeps its own BiCGStab state on the device (the Section 7
+// algorithm, as in bicgstab.cu).  All systems advance together through the
+// phases of an iteration; a phase is a list of work items (row blocks for
+// the SpMV phases, element tiles for the vector phases) over the systems
+// still running, shared out over every CTA of the grid, so a few large
+// systems left at the end still use the whole GPU.  Per-system reductions
+// are deterministic: each item writes its block partial sum, and the CTA
+// that completes a system's last item folds that system's partials in item
+// order and does its scalar update.  Phases are separated by a grid barrier
+// whose wait is bounded in time (it reports HZ_ERR_TIMEOUT instead of
+// hanging if a CTA never arrives).
+#include <algorithm>
+#include <vector>
+
+#include "hz_internal.cuh"
+
+namespace hz {
+
+constexpr int kBBlock = 256;
+constexpr int kBVecItem = kBBlock * 4;     // elements per vector item
+constexpr int kBMaxSys = 1024;             // systems per launch (shared-memory tables)
+
+struct BSys {
+    int n, W, rows_per_item;
+    int sp_item0, sp_items;      // SpMV items [sp_item0, sp_item0 + sp_items)
+    int vc_item0, vc_items;      // vector items
+    const int *rowptr;
+    const int *col;
+    const double2 *val;
+    const double2 *b;
+    double2 *x;
+    double2 *r, *rh, *p, *v, *s, *t;
+};
+
+struct BState {
+    double2 rho, rho_old, alpha, omega, beta;
+    double nb, rel, relres_true;
+    int iter, done, half, status;
+    unsigned int cnt;            // items finished in the current phase
+    int pad;
+};
+
+struct BCtl {
+    double tol;
+    int maxit;
+    int nsys;
+    unsigned int bar_count;
+    volatile unsigned int bar_gen;
+    int err;
+};
+
+enum Phase { P_INIT = 0, P_F1, P_F2, P_F3, P_F4, P_F5, P_TRUE };
+
+// bounded grid barrier: gives up after ~1 s and flags the error
+__device__ bool bgrid_sync(BCtl *c) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int gen = c->bar_gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&c->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            c->bar_count = 0u;
+            __threadfence();
+            atomicAdd((unsigned int *)&c->bar_gen, 1u);
+        } else {
+            uint64_t t0, t1;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            while (c->bar_gen == gen) {
+                __nanosleep(64);
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+                if (t1 - t0 > 1000000000ull) { atomicExch(&c->err, 1); break; }
+                if (*(volatile int *)&c->err) break;
+            }
+        }
+        __threadfence();
+        ok = (*(volatile int *)&c->err) == 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <int NV>
+__device__ __forceinline__ void bsum(double (&v)[NV]) {
+    __shared__ double sh[kBBlock / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) sh[warp][j] = v[j];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            double t = lane < kBBlock / 32 ? sh[lane][j] : 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+            v[j] = t;
+        }
+    }
+    __syncthreads();
+}
+
+// per-system scalar work after a phase's reduction (thread 0)
+__device__ void finalize(int phase, const BCtl *c, BState *S, const double *tot) {
+    const double2 one = make_double2(1.0, 0.0);
+    switch (phase) {
+        case P_INIT: {
+            const double nb = sqrt(tot[1]);
+            S->nb = nb; S->half = 0; S->iter = 0;
+            S->rho = make_double2(tot[0], 0.0);
+            S->rho_old = one; S->alpha = one; S->omega = one; S->beta = make_double2(0.0, 0.0);
+            S->done = 1;
+            if (nb == 0.0) { S->rel = 0.0; S->status = HZ_OK; break; }
+            const double rel = sqrt(tot[0]) / nb;
+            S->rel = rel;
+            if (!isfinite(rel)) S->status = HZ_ERR_NAN;
+            else if (rel <= c->tol) S->status = HZ_OK;
+            else if (c->maxit <= 0) S->status = HZ_NOT_CONVERGED;
+            else { S->status = HZ_NOT_CONVERGED; S->done = 0; S->iter = 1; }
+            break;
+        }
+        case P_F2: {
+            const double2 sig = make_double2(tot[0], tot[1]);
+            if (cis_zero(sig)) { S->status = HZ_BREAKDOWN; S->done = 1; break; }
+            S->alpha = cdiv(S->rho, sig);
+            break;
+        }
+        case P_F3: {
+            const double rel = sqrt(tot[0]) / S->nb;
+            if (!isfinite(rel)) { S->status = HZ_ERR_NAN; S->done = 1; S->rel = rel; break; }
+            if (rel <= c->tol) { S->half = 1; S->rel = rel; }
+            break;
+        }
+        case P_F4: {
+            if (tot[2] == 0.0) { S->status = HZ_BREAKDOWN; S->done = 1; break; }
+            S->omega = make_double2(tot[0] / tot[2], tot[1] / tot[2]);
+            break;
+        }
+        case P_F5: {
+            if (S->half) { S->status = HZ_OK; S->done = 1; break; }
+            const double rel = sqrt(tot[2]) / S->nb;
+            S->rel = rel;
+            if (!isfinite(rel)) { S->status = HZ_ERR_NAN; S->done = 1; }
+            else if (rel <= c->tol) { S->status = HZ_OK; S->done = 1; }
+            else if (cis_zero(S->omega)) { S->status = HZ_BREAKDOWN; S->done = 1; }
+            else if (S->iter >= c->maxit) { S->status = HZ_NOT_CONVERGED; S->done = 1; }
+            else {
+                const double2 rn = make_double2(tot[0], tot[1]);
+                S->beta = cmul(cdiv(rn, S->rho), cdiv(S->alpha, S->omega));
+                S->rho_old = S->rho;
+                S->rho = rn;
+                S->iter += 1;                                  // next iteration starts
+                if (cis_zero(rn)) { S->status = HZ_BREAKDOWN; S->done = 1; }
+            }
+            break;
+        }
+        case P_TRUE:
+            S->relres_true = S->nb == 0.0 ? 0.0 : sqrt(tot[0]) / S->nb;
+            break;
+        default: break;
+    }
+}
+
+template <int NV>
+__device__ void item_done(int phase, const BCtl *c, const BSys &sy, BState *S, double *partials, int item_global,
+                          int item0, int nitems, double (&acc)[NV]) {
+    __shared__ int last;
+    bsum<NV>(acc);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) partials[(size_t)item_global * 4 + j] = acc[j];
+        __threadfence();
+        const unsigned int k = atomicAdd(&S->cnt, 1u);
+        last = (k == (unsigned int)nitems - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double tot[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) tot[j] = 0.0;
+    for (int it = threadIdx.x; it < nitems; it += kBBlock)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) tot[j] += __ldcg(&partials[(size_t)(item0 + it) * 4 + j]);
+    bsum<NV>(tot);
+    if (threadIdx.x == 0) {
+        S->cnt = 0u;
+        finalize(phase, c, S, tot);
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// SpMV rows [r0, r1) of one system with W lanes per row and the phase epilogue
+template <int W>
+__device__ void spmv_item(int phase, const BSys &sy, const BState *S, int r0, int r1, double (&acc)[3]) {
+    const int lane = threadIdx.x & (W - 1);
+    const unsigned gmask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << ((threadIdx.x & 31) & ~(W - 1)));
+    const double2 *x = phase == P_F2 ? sy.p : phase == P_F4 ? sy.s : sy.x;
+    for (int row = r0 + (int)threadIdx.x / W; row < r1; row += kBBlock / W) {
+        const int beg = __ldg(sy.rowptr + row), end = __ldg(sy.rowptr + row + 1);
+        double2 y = make_double2(0.0, 0.0);
+        for (int k = beg + lane; k < end; k += W) cmac(y, ld_stream(sy.val + k), __ldg(x + ld_stream(sy.col + k)));
+#pragma unroll
+        for (int off = W / 2; off > 0; off >>= 1) {
+            y.x += __shfl_xor_sync(gmask, y.x, off, W);
+            y.y += __shfl_xor_sync(gmask, y.y, off, W);
+        }
+        if (lane != 0) continue;
+        if (phase == P_INIT) {
+            const double2 bi = sy.b[row];
+            const double2 ri = make_double2(bi.x - y.x, bi.y - y.y);
+            sy.r[row] = ri; sy.rh[row] = ri;
+            sy.p[row] = make_double2(0.0, 0.0); sy.v[row] = make_double2(0.0, 0.0);
+            acc[0] = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0]));
+            acc[1] = fma(bi.x, bi.x, fma(bi.y, bi.y, acc[1]));
+        } else if (phase == P_F2) {
+            sy.v[row] = y;
+            const double2 h = sy.rh[row];
+            acc[0] = fma(h.x, y.x, fma(h.y, y.y, acc[0]));
+            acc[1] = fma(h.x, y.y, fma(-h.y, y.x, acc[1]));
+        } else if (phase == P_F4) {
+            sy.t[row] = y;
+            const double2 q = sy.s[row];
+            acc[0] = fma(y.x, q.x, fma(y.y, q.y, acc[0]));
+            acc[1] = fma(y.x, q.y, fma(-y.y, q.x, acc[1]));
+            acc[2] = fma(y.x, y.x, fma(y.y, y.y, acc[2]));
+        } else {   // P_TRUE
+            const double2 bi = sy.b[row];
+            const double rx = bi.x - y.x, ry = bi.y - y.y;
+            acc[0] = fma(rx, rx, fma(ry, ry, acc[0]));
+        }
+    }
+}
+
+__device__ void vec_item(int phase, const BSys &sy, const BState *S, int e0, int e1, double (&acc)[3]) {
+    const double2 alpha = S->alpha, omega = S->omega, beta = S->beta;
+    const bool half = S->half;
+    for (int i = e0 + threadIdx.x; i < e1; i += kBBlock) {
+        if (phase == P_F1) {
+            double2 q = sy.p[i];
+            const double2 w = sy.v[i];
+            q.x = fma(-omega.x, w.x, q.x); q.x = fma(omega.y, w.y, q.x);
+            q.y = fma(-omega.x, w.y, q.y); q.y = fma(-omega.y, w.x, q.y);
+            double2 o = sy.r[i];
+            cmac(o, beta, q);
+            sy.p[i] = o;
+        } else if (phase == P_F3) {
+            const double2 w = sy.v[i];
+            double2 o = sy.r[i];
+            o.x = fma(-alpha.x, w.x, o.x); o.x = fma(alpha.y, w.y, o.x);
+            o.y = fma(-alpha.x, w.y, o.y); o.y = fma(-alpha.y, w.x, o.y);
+            sy.s[i] = o;
+            acc[0] = fma(o.x, o.x, fma(o.y, o.y, acc[0]));
+        } else {   // P_F5
+            double2 xi = sy.x[i];
+            cmac(xi, alpha, sy.p[i]);
+            if (half) {
+                sy.x[i] = xi;
+                continue;
+            }
+            const double2 si = sy.s[i], ti = sy.t[i];
+            cmac(xi, omega, si);
+            sy.x[i] = xi;
+            double2 ri = si;
+            ri.x = fma(-omega.x, ti.x, ri.x); ri.x = fma(omega.y, ti.y, ri.x);
+            ri.y = fma(-omega.x, ti.y, ri.y); ri.y = fma(-omega.y, ti.x, ri.y);
+            sy.r[i] = ri;
+            const double2 h = sy.rh[i];
+            acc[0] = fma(h.x, ri.x, fma(h.y, ri.y, acc[0]));
+            acc[1] = fma(h.x, ri.y, fma(-h.y, ri.x, acc[1]));
+            acc[2] = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[2]));
+        }
+    }
+}
+
+// one phase over the systems in the block's active table
+__device__ void run_phase(int phase, const BCtl *c, const BSys *sys, BState *st, double *partials, const int *act,
+                          const int *pref, int nact) {
+    const bool spmv = phase == P_INIT || phase == P_F2 || phase == P_F4 || phase == P_TRUE;
+    const int total = pref[nact];
+    for (int j = blockIdx.x; j < total; j += gridDim.x) {
+        int lo = 0, hi = nact - 1;          // system owning item j
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pref[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        const int s = act[lo];
+        const BSys &sy = sys[s];
+        BState *S = &st[s];
+        const int local = j - pref[lo];
+        __shared__ int skip;
+        if (threadIdx.x == 0) {
+            const int done = *(volatile int *)&S->done, half = *(volatile int *)&S->half;
+            skip = (phase != P_INIT && phase != P_TRUE && done) || (phase == P_F4 && half);
+        }
+        __syncthreads();
+        if (skip) continue;
+        double acc[3] = {0.0, 0.0, 0.0};
+        if (spmv) {
+            const int r0 = local * sy.rows_per_item, r1 = min(sy.n, r0 + sy.rows_per_item);
+            switch (sy.W) {
+                case 2: spmv_item<2>(phase, sy, S, r0, r1, acc); break;
+                case 4: spmv_item<4>(phase, sy, S, r0, r1, acc); break;
+                case 8: spmv_item<8>(phase, sy, S, r0, r1, acc); break;
+                case 16: spmv_item<16>(phase, sy, S, r0, r1, acc); break;
+                default: spmv_item<32>(phase, sy, S, r0, r1, acc); break;
+            }
+            const int nit = sy.sp_items;
+            if (phase == P_F4) item_done<3>(phase, c, sy, S, partials, sy.sp_item0 + local, sy.sp_item0, nit, acc);
+            else if (phase == P_TRUE) {
+                double a1[1] = {acc[0]};
+                item_done<1>(phase, c, sy, S, partials, sy.sp_item0 + local, sy.sp_item0, nit, a1);
+            } else {
+                double a2[2] = {acc[0], acc[1]};
+                item_done<2>(phase, c, sy, S, partials, sy.sp_item0 + local, sy.sp_item0, nit, a2);
+            }
+        } else {
+            const int e0 = local * kBVecItem, e1 = min(sy.n, e0 + kBVecItem);
+            vec_item(phase, sy, S, e0, e1, acc);
+            const int nit = sy.vc_items;
+            const int g = sy.vc_item0 + local;
+            if (phase == P_F3) {
+                double a1[1] = {acc[0]};
+                item_done<1>(phase, c, sy, S, partials, g, sy.vc_item0, nit, a1);
+            } else if (phase == P_F5) {
+                item_done<3>(phase, c, sy, S, partials, g, sy.vc_item0, nit, acc);
+            }
+        }
+        __syncthreads();   // `skip` is rewritten by the next item
+    }
+}
+
+// table of systems still running and their item prefix sums: the flags and
+// item counts are loaded by all threads at once, the prefix is taken in
+// shared memory by one thread
+__device__ int build_active(int spmv_items, const BCtl *c, const BSys *sys, const BState *st, int *act,
+                            int *pref, bool only_running) {
+    __shared__ int nact;
+    __shared__ int cnt[kBMaxSys];
+    const int nsys = c->nsys;
+    for (int s = threadIdx.x; s < nsys; s += kBBlock) {
+        const bool run = !only_running || !*(volatile const int *)&st[s].done;
+        cnt[s] = run ? (spmv_items ? sys[s].sp_items : sys[s].vc_items) : -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int k = 0;
+        pref[0] = 0;
+        for (int s = 0; s < nsys; ++s) {
+            if (cnt[s] < 0) continue;
+            act[k] = s;
+            pref[k + 1] = pref[k] + cnt[s];
+            ++k;
+        }
+        nact = k;
+    }
+    __syncthreads();
+    return nact;
+}
+
+__global__ void __launch_bounds__(kBBlock) k_batched(BCtl *c, const BSys *sys, BState *st, double *partials) {
+    __shared__ int act[kBMaxSys];
+    __shared__ int pref_sp[kBMaxSys + 1];
+    __shared__ int pref_vc[kBMaxSys + 1];
+    int nact = build_active(1, c, sys, st, act, pref_sp, false);
+    run_phase(P_INIT, c, sys, st, partials, act, pref_sp, nact);
+    if (!bgrid_sync(c)) return;
+    for (int guard = 0; guard <= c->maxit + 1; ++guard) {
+        nact = build_active(1, c, sys, st, act, pref_sp, true);
+        if (nact == 0) break;
+        build_active(0, c, sys, st, act, pref_vc, true);
+        run_phase(P_F1, c, sys, st, partials, act, pref_vc, nact);
+        if (!bgrid_sync(c)) return;
+        run_phase(P_F2, c, sys, st, partials, act, pref_sp, nact);
+        if (!bgrid_sync(c)) return;
+        run_phase(P_F3, c, sys, st, partials, act, pref_vc, nact);
+        if (!bgrid_sync(c)) return;
+        run_phase(P_F4, c, sys, st, partials, act, pref_sp, nact);
+        if (!bgrid_sync(c)) return;
+        run_phase(P_F5, c, sys, st, partials, act, pref_vc, nact);
+        if (!bgrid_sync(c)) return;
+    }
+    nact = build_active(1, c, sys, st, act, pref_sp, false);
+    run_phase(P_TRUE, c, sys, st, partials, act, pref_sp, nact);
+}
+
+}  // namespace hz
+
+using namespace hz;
+
+extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, const hz_z *const *d_b,
+                                              hz_z *const *d_x, double tol, int32_t maxit, uint32_t mode,
+                                              hz_info *h_info, void *stream) {
+    HZ_CHECK(nsys >= 0 && nsys <= kBMaxSys, "hz_zsolve_batched: nsys out of range (0..1024)");
+    HZ_CHECK(mode == HZ_MODE_FP64, "hz_zsolve_batched: only HZ_MODE_FP64 is batched");
+    HZ_CHECK(maxit >= 0 && tol >= 0.0, "hz_zsolve_batched: bad tol/maxit");
+    if (nsys == 0) return HZ_OK;
+    HZ_CHECK(A && d_b && d_x && h_info, "hz_zsolve_batched: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<BSys> hs(nsys);
+    int64_t sp = 0, vc = 0, vec_elems = 0;
+    for (int k = 0; k < nsys; ++k) {
+        HZ_CHECK(A[k], "hz_zsolve_batched: null matrix handle");
+        HZ_CHECK(A[k]->n == 0 || (d_b[k] && d_x[k]), "hz_zsolve_batched: null vector");
+        BSys &y = hs[k];
+        y.n = A[k]->n;
+        y.W = A[k]->group;
+        y.rows_per_item = (kBBlock / y.W) * 4;
+        y.sp_item0 = (int)sp;
+        y.sp_items = (y.n + y.rows_per_item - 1) / y.rows_per_item;
+        y.vc_item0 = (int)vc;
+        y.vc_items = (y.n + kBVecItem - 1) / kBVecItem;
+        y.rowptr = A[k]->rowptr; y.col = A[k]->col; y.val = A[k]->val;
+        y.b = (const double2 *)d_b[k]; y.x = (double2 *)d_x[k];
+        sp += y.sp_items;
+        vc += y.vc_items;
+        vec_elems += y.n;
+    }
+    HZ_CHECK(sp < INT32_MAX / 4 && vc < INT32_MAX / 4, "hz_zsolve_batched: batch too large");
+    // workspace: 6 vectors per system, item partials, states, controls
+    double2 *work = nullptr;
+    double *partials = nullptr;
+    BState *st = nullptr;
+    BSys *dsys = nullptr;
+    BCtl *ctl = nullptr;
+    auto cleanup = [&]() { cudaFree(work); cudaFree(partials); cudaFree(st); cudaFree(dsys); cudaFree(ctl); };
+    if (cudaMalloc(&work, sizeof(double2) * std::max<int64_t>(6 * vec_elems, 1)) != cudaSuccess ||
+        cudaMalloc(&partials, sizeof(double) * 4 * std::max<int64_t>(std::max(sp, vc), 1)) != cudaSuccess ||
+        cudaMalloc(&st, sizeof(BState) * nsys) != cudaSuccess || cudaMalloc(&dsys, sizeof(BSys) * nsys) != cudaSuccess ||
+        cudaMalloc(&ctl, sizeof(BCtl)) != cudaSuccess) {
+        cleanup();
+        set_error("hz_zsolve_batched: workspace allocation failed");
+        return HZ_ERR_ALLOC;
+    }
+    int64_t off = 0;
+    for (auto &y : hs) {
+        double2 **vecs[6] = {&y.r, &y.rh, &y.p, &y.v, &y.s, &y.t};
+        for (auto v : vecs) { *v = work + off; off += y.n; }
+    }
+    BCtl hc{};
+    hc.tol = tol; hc.maxit = maxit; hc.nsys = nsys;
+    cudaError_t e = cudaMemcpyAsync(dsys, hs.data(), sizeof(BSys) * nsys, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctl, &hc, sizeof(BCtl), cudaMemcpyHostToDevice, s);
+    std::vector<BState> hst(nsys);
+    for (int k = 0; k < nsys; ++k) {
+        hst[k] = BState{};
+        if (hs[k].n == 0) { hst[k].done = 1; hst[k].status = HZ_OK; }   // nothing to solve
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st, hst.data(), sizeof(BState) * nsys, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    DevInfo d;
+    int occ = 0;
+    if (e == cudaSuccess && dev_info(&d) == HZ_OK)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched, kBBlock, 0);
+    if (e == cudaSuccess && occ < 1) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) {
+        dim3 grid(d.num_sms * std::min(occ, 4)), block(kBBlock);
+        void *args[] = {&ctl, &dsys, &st, &partials};
+        e = cudaLaunchCooperativeKernel((void *)k_batched, grid, block, args, 0, s);
+    }
+    BCtl hc2{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), st, sizeof(BState) * nsys, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc2, ctl, sizeof(BCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "hz_zsolve_batched", __FILE__, __LINE__);
+    if (hc2.err) {
+        set_error("hz_zsolve_batched: a grid barrier wait timed out");
+        return HZ_ERR_TIMEOUT;
+    }
+    hz_status worst = HZ_OK;
+    for (int k = 0; k < nsys; ++k) {
+        hz_info &o = h_info[k];
+        o = hz_info{};
+        o.iters = hst[k].iter;
+        o.status = hst[k].status;
+        o.relres_rec = hst[k].rel;
+        o.relres_true = hst[k].relres_true;
+        if (A[k]->n == 0) { o.status = HZ_OK; o.iters = 0; }
+        if (o.status == HZ_OK && o.relres_true > tol) o.status = HZ_NOT_CONVERGED;
+        if (o.status != HZ_OK && worst == HZ_OK) worst = (hz_status)o.status;
+    }
+    return worst;
+}

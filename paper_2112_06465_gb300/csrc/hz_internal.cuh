@@ -1,0 +1,284 @@
+// hz_internal.cuh -- shared device helpers and internal structures of libhz.
+//
+// Complex values are double2 / float2 (real in .x, imaginary in .y), the
+// two-contiguous-reals layout of the paper's Section 4.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/hz.h"
+
+namespace hz {
+
+// ---------------------------------------------------------------------------
+// error plumbing
+void set_error(const std::string &msg);
+hz_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define HZ_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t _e = (call);                                                   \
+        if (_e != cudaSuccess) return ::hz::cuda_fail(_e, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define HZ_CHECK(cond, msg)                                                        \
+    do {                                                                           \
+        if (!(cond)) { ::hz::set_error(msg); return HZ_ERR_ARG; }                   \
+    } while (0)
+
+#define HZ_TRY(call)                                                               \
+    do {                                                                           \
+        hz_status _s = (call);                                                     \
+        if (_s != HZ_OK) return _s;                                                \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device properties (cached per device)
+struct DevInfo {
+    int device = -1;
+    int num_sms = 0;
+    int max_threads_per_sm = 0;
+};
+hz_status dev_info(DevInfo *out);
+
+// ---------------------------------------------------------------------------
+// complex arithmetic (4 fused multiply-adds per complex multiply-accumulate)
+template <class T> struct Cplx;
+template <> struct Cplx<double2> { using R = double; };
+template <> struct Cplx<float2> { using R = float; };
+
+__device__ __forceinline__ double2 cmk(double r, double i) { return make_double2(r, i); }
+__device__ __forceinline__ float2 cmk(float r, float i) { return make_float2(r, i); }
+
+template <class T> __device__ __forceinline__ T czero() { T z; z.x = 0; z.y = 0; return z; }
+
+template <class T> __device__ __forceinline__ T cadd(T a, T b) { T r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <class T> __device__ __forceinline__ T csub(T a, T b) { T r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <class T> __device__ __forceinline__ T cconj(T a) { T r; r.x = a.x; r.y = -a.y; return r; }
+template <class T> __device__ __forceinline__ T cmul(T a, T b) {
+    T r;
+    r.x = fma(a.x, b.x, -a.y * b.y);
+    r.y = fma(a.x, b.y, a.y * b.x);
+    return r;
+}
+// acc += a * b
+template <class T> __device__ __forceinline__ void cmac(T &acc, T a, T b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <class T> __device__ __forceinline__ void cmac_conj(T &acc, T a, T b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+// a / b as a * conj(b) / |b|^2 (operands here are O(1) Krylov scalars)
+template <class T> __device__ __forceinline__ T cdiv(T a, T b) {
+    auto d = b.x * b.x + b.y * b.y;
+    T r;
+    r.x = (a.x * b.x + a.y * b.y) / d;
+    r.y = (a.y * b.x - a.x * b.y) / d;
+    return r;
+}
+template <class T> __device__ __forceinline__ bool cis_zero(T a) { return a.x == 0 && a.y == 0; }
+
+__device__ __forceinline__ float2 to_c64(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 to_c128(float2 a) { return make_double2((double)a.x, (double)a.y); }
+
+// ---------------------------------------------------------------------------
+// global loads with cache hints (PTX ISA: createpolicy + ld ... L2::cache_hint).
+// The matrix is read once per product, so it is streamed with an L2
+// evict-first policy and kept out of L1; the gathered vector uses the default
+// cached path.  The asm statements are not volatile: they read data that no
+// kernel writes while it runs, so the compiler may schedule them freely.
+__device__ __forceinline__ uint64_t pol_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ double2 ld_stream(const double2 *ptr) {
+    double2 v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+        : "=d"(v.x), "=d"(v.y) : "l"(ptr), "l"(pol_evict_first()));
+    return v;
+}
+__device__ __forceinline__ float2 ld_stream(const float2 *ptr) {
+    float2 v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+        : "=f"(v.x), "=f"(v.y) : "l"(ptr), "l"(pol_evict_first()));
+    return v;
+}
+__device__ __forceinline__ int ld_stream(const int *ptr) {
+    int v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
+        : "=r"(v) : "l"(ptr), "l"(pol_evict_first()));
+    return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float4 *ptr) {
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(ptr), "l"(pol_evict_first()));
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// double-float ("ff") arithmetic on the binary32 pipes.
+//
+// GB300 executes binary64 FMAs at 1/58 of the binary32 rate (about 2 per SM
+// per clock), which caps a binary64 complex SpMV near 45% of HBM bandwidth.
+// The ff path represents a binary64 value d as hi + lo with
+// hi = fl32(d), lo = fl32(d - hi) (48 significant bits; relative
+// representation error <= 2^-48 for |d| in [2^-100, 2^100]) and forms
+// products and sums with the classical error-free transformations:
+//   TwoProd (Dekker, via FMA): p = fl(a*b), e = fma(a, b, -p), a*b = p + e
+//   TwoSum (Knuth):            s = fl(a+b), e = (a - (s - z)) + (b - z), z = s - a
+// The explicit __f*_rn intrinsics keep the compiler from contracting or
+// reassociating these sequences.
+__device__ __forceinline__ float4 split_ff(double2 d) {
+    const float hr = __double2float_rn(d.x), hi = __double2float_rn(d.y);
+    return make_float4(hr, __double2float_rn(d.x - (double)hr), hi, __double2float_rn(d.y - (double)hi));
+}
+
+// (s, c) += p, with the rounding error of s + p carried into c
+__device__ __forceinline__ void ff_acc(float &s, float &c, float p) {
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, e);
+}
+
+// (s, c) += (ah + al) * (xh + xl); the al*xl term (2^-48 relative) is dropped
+__device__ __forceinline__ void ff_mac(float &s, float &c, float ah, float al, float xh, float xl) {
+    const float p = __fmul_rn(ah, xh);
+    float e = __fmaf_rn(ah, xh, -p);
+    e = __fmaf_rn(ah, xl, e);
+    e = __fmaf_rn(al, xh, e);
+    ff_acc(s, c, p);
+    c = __fadd_rn(c, e);
+}
+
+// ---------------------------------------------------------------------------
+// deterministic single-pass grid reduction.
+//
+// Every block reduces its NV per-thread values (warp shuffles, then shared
+// memory), writes them to partials[blockIdx.x * NV + j], and increments a
+// completion counter.  The block that arrives last sums the partials in a
+// fixed order (thread t takes blocks t, t + blockDim, ...) and returns true
+// with the totals in tot[] (valid in thread 0).  For a fixed grid the result
+// is bitwise reproducible.  The counter is reset by the last block.
+struct RedScratch {
+    void *partials;            // >= max_blocks * NV * sizeof(R)
+    unsigned int *counter;     // one counter, zero between kernels
+};
+
+template <class R, int NV>
+__device__ __forceinline__ void block_sum(R (&v)[NV], R (*sh)[NV]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) sh[warp][j] = v[j];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            R t = lane < nwarps ? sh[lane][j] : R(0);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+            v[j] = t;
+        }
+    }
+    __syncthreads();
+}
+
+template <class R, int NV>
+__device__ __forceinline__ bool grid_reduce_last(R (&v)[NV], RedScratch red, R (&tot)[NV]) {
+    __shared__ R sh[32][NV];
+    __shared__ int am_last;
+    R *partials = reinterpret_cast<R *>(red.partials);
+    block_sum<R, NV>(v, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) partials[blockIdx.x * NV + j] = v[j];
+        __threadfence();
+        unsigned int t = atomicAdd(red.counter, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    R acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = R(0);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) acc[j] += __ldcg(&partials[b * NV + j]);
+    }
+    block_sum<R, NV>(acc, sh);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) tot[j] = acc[j];
+    if (threadIdx.x == 0) *red.counter = 0u;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// per-(device, stream) reduction scratch
+constexpr int kMaxRedBlocks = 4096;
+constexpr int kMaxRedValues = 8;
+hz_status get_scratch(cudaStream_t s, RedScratch *out);
+
+// grid size for streaming kernels: a whole number of waves over the SMs
+int stream_grid(const DevInfo &d, int64_t work_items, int block, int blocks_per_sm);
+
+}  // namespace hz
+
+// ---------------------------------------------------------------------------
+// matrix handle
+struct hz_mat {
+    int device = -1;
+    int32_t n = 0, nnz = 0;
+    const int32_t *rowptr = nullptr;   // 0-based, device
+    const int32_t *col = nullptr;
+    double2 *val = nullptr;            // caller's values (writable through set_diag)
+    int32_t *own_rowptr = nullptr;     // owned 0-based copies (index_base 1)
+    int32_t *own_col = nullptr;
+    // row statistics
+    int32_t max_row = 0, min_row = 0;
+    double mean_row = 0;
+    // SpMV selection
+    int spmv_kind = HZ_SPMV_CSR_VECTOR;
+    int group = 4;
+    // SELL-C-sigma copy (C = 32)
+    int32_t sell_nchunks = 0;
+    int32_t sell_sigma = 0;
+    int64_t sell_slots = 0;
+    int32_t *sell_chunk_off = nullptr;   // [nchunks+1] slot offsets
+    int32_t *sell_chunk_w = nullptr;     // [nchunks] chunk widths
+    int32_t *sell_perm = nullptr;        // [nchunks*32] original row of each lane (-1 pad)
+    int32_t *sell_col = nullptr;         // [slots] column (-1 = padding)
+    int32_t *sell_src = nullptr;         // [slots] CSR position of the slot (-1 = padding)
+    double2 *sell_val = nullptr;         // [slots]
+    float2 *sell_val32 = nullptr;        // [slots] complex64 copy, if c64
+    // complex64 copy
+    float2 *val32 = nullptr;
+    // double-float split of the values (hi_re, lo_re, hi_im, lo_im) and the
+    // handle's x scratch for hz_zspmv on that path
+    float4 *val_ff = nullptr;
+    float4 *x_ff = nullptr;
+    // diagonal positions (for set_diag), built on demand
+    int32_t *diag_pos = nullptr;
+    // solver state (one per mode), created on first solve
+    void *solver[2] = {nullptr, nullptr};
+};

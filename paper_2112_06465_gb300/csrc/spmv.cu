@@ -1,0 +1,421 @@
+// spmv.cu -- matrix handles, SpMV variant selection (row-length histogram
+// and optional timing-based autotuning), SELL-C-sigma construction and the
+// hz_zspmv / hz_cspmv entry points.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "spmv.cuh"
+
+namespace hz {
+
+// ---------------------------------------------------------------------------
+__global__ void k_rebase(int n, const int *in, int *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = in[i] - 1;
+}
+
+__global__ void k_to_c64(int64_t n, const double2 *__restrict__ in, float2 *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = to_c64(in[i]);
+}
+
+// SELL slot values from the CSR values through the slot -> CSR map
+__global__ void k_sell_gather(int64_t slots, const int *__restrict__ src, const double2 *__restrict__ val,
+                              double2 *__restrict__ sval, float2 *__restrict__ sval32) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < slots;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = src[i];
+        const double2 v = k >= 0 ? val[k] : make_double2(0.0, 0.0);
+        sval[i] = v;
+        if (sval32) sval32[i] = to_c64(v);
+    }
+}
+
+__global__ void k_split_ff(int64_t n, const double2 *__restrict__ x, float4 *__restrict__ xff) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        xff[i] = split_ff(x[i]);
+}
+
+cudaError_t split_ff_vec(int n, const double2 *x, float4 *xff, cudaStream_t s) {
+    DevInfo d;
+    if (dev_info(&d) != HZ_OK) return cudaErrorUnknown;
+    if (n > 0) k_split_ff<<<stream_grid(d, n, 256, 8), 256, 0, s>>>(n, x, xff);
+    return cudaGetLastError();
+}
+
+template <>
+MatView<double2> mat_view<double2>(const hz_mat *A) {
+    MatView<double2> v{};
+    v.n = A->n; v.rowptr = A->rowptr; v.col = A->col; v.val = A->val; v.vff = A->val_ff;
+    v.nchunks = A->sell_nchunks; v.chunk_off = A->sell_chunk_off; v.chunk_w = A->sell_chunk_w;
+    v.perm = A->sell_perm; v.scol = A->sell_col; v.sval = A->sell_val;
+    return v;
+}
+
+template <>
+MatView<float2> mat_view<float2>(const hz_mat *A) {
+    MatView<float2> v{};
+    v.n = A->n; v.rowptr = A->rowptr; v.col = A->col; v.val = A->val32;
+    v.nchunks = A->sell_nchunks; v.chunk_off = A->sell_chunk_off; v.chunk_w = A->sell_chunk_w;
+    v.perm = A->sell_perm; v.scol = A->sell_col; v.sval = A->sell_val32;
+    return v;
+}
+
+int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap) {
+    DevInfo d;
+    if (dev_info(&d) != HZ_OK) return 1;
+    int64_t threads = kind == HZ_SPMV_SELL ? (int64_t)A->sell_nchunks * 32 : (int64_t)A->n * group;
+    return stream_grid(d, threads, kSpmvBlock, blocks_per_sm_cap);
+}
+
+// lanes per row from the row-length histogram: about four entries per lane,
+// rounded to a power of two in [2, 32]
+static int pick_group(double mean_row) {
+    int w = 2;
+    while (w < 32 && w * 4 < mean_row) w *= 2;
+    return w;
+}
+
+static hz_status build_sell(hz_mat *A, cudaStream_t s, const std::vector<int> &rp,
+                            const std::vector<int> &cl, int sigma) {
+    const int n = A->n;
+    const int nchunks = (n + kSellC - 1) / kSellC;
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    for (int w0 = 0; w0 < n; w0 += sigma) {
+        const int w1 = std::min(n, w0 + sigma);
+        std::stable_sort(order.begin() + w0, order.begin() + w1, [&](int a, int b) {
+            return (rp[a + 1] - rp[a]) > (rp[b + 1] - rp[b]);
+        });
+    }
+    std::vector<int> perm((size_t)nchunks * kSellC, -1), cw(nchunks), coff(nchunks + 1);
+    int64_t slots = 0;
+    for (int c = 0; c < nchunks; ++c) {
+        int w = 0;
+        for (int l = 0; l < kSellC; ++l) {
+            const int r = c * kSellC + l;
+            if (r < n) {
+                perm[(size_t)c * kSellC + l] = order[r];
+                w = std::max(w, rp[order[r] + 1] - rp[order[r]]);
+            }
+        }
+        cw[c] = w;
+        coff[c] = (int)slots;
+        slots += (int64_t)w * kSellC;
+        if (slots > INT32_MAX) { set_error("SELL copy exceeds 2^31 slots"); return HZ_ERR_ARG; }
+    }
+    coff[nchunks] = (int)slots;
+    std::vector<int> scol(slots, -1), ssrc(slots, -1);
+    for (int c = 0; c < nchunks; ++c)
+        for (int l = 0; l < kSellC; ++l) {
+            const int row = perm[(size_t)c * kSellC + l];
+            if (row < 0) continue;
+            for (int j = 0; j < rp[row + 1] - rp[row]; ++j) {
+                const int64_t slot = coff[c] + (int64_t)j * kSellC + l;
+                scol[slot] = cl[rp[row] + j];
+                ssrc[slot] = rp[row] + j;
+            }
+        }
+    A->sell_nchunks = nchunks;
+    A->sell_sigma = sigma;
+    A->sell_slots = slots;
+    HZ_CUDA(cudaMalloc(&A->sell_chunk_off, sizeof(int) * (nchunks + 1)));
+    HZ_CUDA(cudaMalloc(&A->sell_chunk_w, sizeof(int) * std::max(nchunks, 1)));
+    HZ_CUDA(cudaMalloc(&A->sell_perm, sizeof(int) * std::max<size_t>(perm.size(), 1)));
+    HZ_CUDA(cudaMalloc(&A->sell_col, sizeof(int) * std::max<int64_t>(slots, 1)));
+    HZ_CUDA(cudaMalloc(&A->sell_src, sizeof(int) * std::max<int64_t>(slots, 1)));
+    HZ_CUDA(cudaMalloc(&A->sell_val, sizeof(double2) * std::max<int64_t>(slots, 1)));
+    HZ_CUDA(cudaMemcpyAsync(A->sell_chunk_off, coff.data(), sizeof(int) * (nchunks + 1), cudaMemcpyHostToDevice, s));
+    if (nchunks) {
+        HZ_CUDA(cudaMemcpyAsync(A->sell_chunk_w, cw.data(), sizeof(int) * nchunks, cudaMemcpyHostToDevice, s));
+        HZ_CUDA(cudaMemcpyAsync(A->sell_perm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice, s));
+    }
+    if (slots) {
+        HZ_CUDA(cudaMemcpyAsync(A->sell_col, scol.data(), sizeof(int) * slots, cudaMemcpyHostToDevice, s));
+        HZ_CUDA(cudaMemcpyAsync(A->sell_src, ssrc.data(), sizeof(int) * slots, cudaMemcpyHostToDevice, s));
+    }
+    HZ_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
+    return HZ_OK;
+}
+
+static hz_status refresh(hz_mat *A, cudaStream_t s) {
+    DevInfo d;
+    HZ_TRY(dev_info(&d));
+    if (A->val32 && A->nnz) {
+        k_to_c64<<<stream_grid(d, A->nnz, 256, 8), 256, 0, s>>>(A->nnz, A->val, A->val32);
+        HZ_CUDA(cudaGetLastError());
+    }
+    if (A->val_ff && A->nnz) {
+        k_split_ff<<<stream_grid(d, A->nnz, 256, 8), 256, 0, s>>>(A->nnz, A->val, A->val_ff);
+        HZ_CUDA(cudaGetLastError());
+    }
+    if (A->sell_val && A->sell_slots) {
+        k_sell_gather<<<stream_grid(d, A->sell_slots, 256, 8), 256, 0, s>>>(
+            A->sell_slots, A->sell_src, A->val, A->sell_val, A->sell_val32);
+        HZ_CUDA(cudaGetLastError());
+    }
+    return HZ_OK;
+}
+
+hz_status ensure_c64(hz_mat *A, cudaStream_t s) {
+    if (A->val32) return HZ_OK;
+    HZ_CUDA(cudaMalloc(&A->val32, sizeof(float2) * std::max(A->nnz, 1)));
+    if (A->sell_val) HZ_CUDA(cudaMalloc(&A->sell_val32, sizeof(float2) * std::max<int64_t>(A->sell_slots, 1)));
+    HZ_TRY(refresh(A, s));
+    HZ_CUDA(cudaStreamSynchronize(s));
+    return HZ_OK;
+}
+
+static hz_status autotune(hz_mat *A, cudaStream_t s) {
+    if (A->n == 0) return HZ_OK;
+    double2 *x = nullptr, *y = nullptr;
+    HZ_CUDA(cudaMalloc(&x, sizeof(double2) * A->n));
+    HZ_CUDA(cudaMalloc(&y, sizeof(double2) * A->n));
+    HZ_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * A->n, s));
+    cudaEvent_t e0, e1;
+    HZ_CUDA(cudaEventCreate(&e0));
+    HZ_CUDA(cudaEventCreate(&e1));
+    std::vector<std::pair<int, int>> cand;
+    for (int w : {2, 4, 8, 16, 32}) cand.push_back({HZ_SPMV_CSR_VECTOR, w});
+    if (A->sell_val) cand.push_back({HZ_SPMV_SELL, 0});
+    if (A->val_ff)
+        for (int w : {2, 4, 8, 16, 32}) cand.push_back({HZ_SPMV_FF, w});
+    float best = 1e30f;
+    MatView<double2> V = mat_view<double2>(A);
+    EpiStore<double2> epi{y};
+    hz_status st = HZ_OK;
+    for (auto &c : cand) {
+        const int grid = spmv_grid(A, c.first, c.second);
+        float tms[5];
+        for (int rep = -1; rep < 5; ++rep) {
+            cudaEventRecord(e0, s);
+            if (c.first == HZ_SPMV_FF) launch_spmv_ff(c.second, V, A->x_ff, epi, RedScratch{}, grid, s);
+            else launch_spmv<double2>(c.first, c.second, V, x, epi, RedScratch{}, grid, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { st = HZ_ERR_CUDA; break; }
+            if (rep >= 0) cudaEventElapsedTime(&tms[rep], e0, e1);
+        }
+        if (st != HZ_OK) break;
+        std::sort(tms, tms + 5);
+        if (tms[2] < best) {
+            best = tms[2];
+            A->spmv_kind = c.first;
+            if (c.first != HZ_SPMV_SELL) A->group = c.second;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(y);
+    if (st != HZ_OK) { set_error("SpMV autotuning launch failed"); return st; }
+    return HZ_OK;
+}
+
+void free_solvers(hz_mat *A);
+
+}  // namespace hz
+
+using namespace hz;
+
+extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, const int32_t *d_rowptr,
+                                          const int32_t *d_col, const hz_z *d_val, int32_t index_base,
+                                          uint32_t flags, void *stream) {
+    HZ_CHECK(out != nullptr, "hz_csr_create: null output handle");
+    *out = nullptr;
+    HZ_CHECK(n >= 0 && nnz >= 0, "hz_csr_create: negative size");
+    HZ_CHECK(index_base == 0 || index_base == 1, "hz_csr_create: index_base must be 0 or 1");
+    HZ_CHECK(d_rowptr != nullptr, "hz_csr_create: null rowptr");
+    HZ_CHECK(nnz == 0 || (d_col != nullptr && d_val != nullptr), "hz_csr_create: null col/val");
+    cudaStream_t s = (cudaStream_t)stream;
+    hz_mat *A = new hz_mat();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    A->device = dev;
+    A->n = n;
+    A->nnz = nnz;
+    A->val = (double2 *)d_val;
+    auto fail = [&](hz_status st) { hz_mat_destroy(A); return st; };
+    if (index_base == 1) {
+        if (cudaMalloc(&A->own_rowptr, sizeof(int) * (n + 1)) != cudaSuccess ||
+            cudaMalloc(&A->own_col, sizeof(int) * std::max(nnz, 1)) != cudaSuccess) {
+            set_error("hz_csr_create: allocation failed");
+            return fail(HZ_ERR_ALLOC);
+        }
+        k_rebase<<<64, 256, 0, s>>>(n + 1, d_rowptr, A->own_rowptr);
+        if (nnz) k_rebase<<<256, 256, 0, s>>>(nnz, d_col, A->own_col);
+        A->rowptr = A->own_rowptr;
+        A->col = A->own_col;
+    } else {
+        A->rowptr = d_rowptr;
+        A->col = d_col;
+    }
+    std::vector<int> rp(n + 1);
+    if (cudaMemcpyAsync(rp.data(), A->rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("hz_csr_create: cannot read rowptr (is it a device pointer?)");
+        return fail(HZ_ERR_CUDA);
+    }
+    const bool need_cols = (flags & (HZ_FLAG_VALIDATE | HZ_FLAG_SELL)) != 0;
+    std::vector<int> cl;
+    if (flags & HZ_FLAG_VALIDATE) {
+        if (rp[0] != 0 || rp[n] != nnz) {
+            set_error("hz_csr_create: rowptr[0] must be the base and rowptr[n] must equal nnz + base");
+            return fail(HZ_ERR_ARG);
+        }
+        for (int i = 0; i < n; ++i)
+            if (rp[i + 1] < rp[i]) {
+                set_error("hz_csr_create: rowptr is not monotone at row " + std::to_string(i));
+                return fail(HZ_ERR_ARG);
+            }
+    } else if (rp[n] != nnz) {
+        set_error("hz_csr_create: rowptr[n] does not match nnz");
+        return fail(HZ_ERR_ARG);
+    }
+    if (need_cols && nnz) {
+        cl.resize(nnz);
+        if (cudaMemcpy(cl.data(), A->col, sizeof(int) * nnz, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            set_error("hz_csr_create: cannot read col");
+            return fail(HZ_ERR_CUDA);
+        }
+        if (flags & HZ_FLAG_VALIDATE)
+            for (int k = 0; k < nnz; ++k)
+                if (cl[k] < 0 || cl[k] >= n) {
+                    set_error("hz_csr_create: column index out of range at entry " + std::to_string(k));
+                    return fail(HZ_ERR_ARG);
+                }
+    }
+    int mx = 0, mn = n ? INT32_MAX : 0;
+    for (int i = 0; i < n; ++i) {
+        const int l = rp[i + 1] - rp[i];
+        mx = std::max(mx, l);
+        mn = std::min(mn, l);
+    }
+    A->max_row = mx;
+    A->min_row = mn;
+    A->mean_row = n ? (double)nnz / n : 0.0;
+    A->group = pick_group(A->mean_row);
+    A->spmv_kind = HZ_SPMV_CSR_VECTOR;
+    hz_status st;
+    if (flags & HZ_FLAG_SELL) {
+        if ((st = build_sell(A, s, rp, cl, 1024)) != HZ_OK) return fail(st);
+        A->spmv_kind = HZ_SPMV_SELL;
+    }
+    if (flags & HZ_FLAG_C64) {
+        if (cudaMalloc(&A->val32, sizeof(float2) * std::max(nnz, 1)) != cudaSuccess ||
+            (A->sell_slots && cudaMalloc(&A->sell_val32, sizeof(float2) * A->sell_slots) != cudaSuccess)) {
+            set_error("hz_csr_create: allocation failed");
+            return fail(HZ_ERR_ALLOC);
+        }
+    }
+    if (flags & HZ_FLAG_FF) {
+        if (cudaMalloc(&A->val_ff, sizeof(float4) * std::max(nnz, 1)) != cudaSuccess ||
+            cudaMalloc(&A->x_ff, sizeof(float4) * std::max(n, 1)) != cudaSuccess) {
+            set_error("hz_csr_create: allocation failed");
+            return fail(HZ_ERR_ALLOC);
+        }
+        if (n) cudaMemsetAsync(A->x_ff, 0, sizeof(float4) * n, s);
+        A->spmv_kind = HZ_SPMV_FF;
+    }
+    if ((st = refresh(A, s)) != HZ_OK) return fail(st);
+    if (flags & HZ_FLAG_AUTOTUNE) {
+        if ((st = autotune(A, s)) != HZ_OK) return fail(st);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("hz_csr_create: stream error");
+        return fail(HZ_ERR_CUDA);
+    }
+    *out = A;
+    return HZ_OK;
+}
+
+extern "C" HZ_API hz_status hz_mat_destroy(hz_mat *A) {
+    if (!A) return HZ_OK;
+    cudaDeviceSynchronize();
+    free_solvers(A);
+    cudaFree(A->own_rowptr);
+    cudaFree(A->own_col);
+    cudaFree(A->sell_chunk_off);
+    cudaFree(A->sell_chunk_w);
+    cudaFree(A->sell_perm);
+    cudaFree(A->sell_col);
+    cudaFree(A->sell_src);
+    cudaFree(A->sell_val);
+    cudaFree(A->sell_val32);
+    cudaFree(A->val32);
+    cudaFree(A->val_ff);
+    cudaFree(A->x_ff);
+    cudaFree(A->diag_pos);
+    delete A;
+    return HZ_OK;
+}
+
+extern "C" HZ_API hz_status hz_mat_query(const hz_mat *A, hz_mat_props *p) {
+    HZ_CHECK(A && p, "hz_mat_query: null argument");
+    p->n = A->n;
+    p->nnz = A->nnz;
+    p->max_row = A->max_row;
+    p->min_row = A->min_row;
+    p->mean_row = A->mean_row;
+    p->spmv_kind = A->spmv_kind;
+    p->group = A->group;
+    p->sell_slots = A->sell_slots;
+    p->sell_sigma = A->sell_sigma;
+    p->has_c64 = A->val32 != nullptr;
+    return HZ_OK;
+}
+
+extern "C" HZ_API hz_status hz_mat_refresh_values(hz_mat *A, void *stream) {
+    HZ_CHECK(A, "hz_mat_refresh_values: null handle");
+    return refresh(A, (cudaStream_t)stream);
+}
+
+extern "C" HZ_API hz_status hz_zspmv(const hz_mat *A, const hz_z *d_x, hz_z *d_y, void *stream) {
+    HZ_CHECK(A, "hz_zspmv: null handle");
+    if (A->n == 0) return HZ_OK;
+    HZ_CHECK(d_x && d_y, "hz_zspmv: null vector");
+    HZ_CHECK((const void *)d_x != (const void *)d_y, "hz_zspmv: x and y must not alias");
+    const int grid = spmv_grid(A, A->spmv_kind, A->group);
+    EpiStore<double2> epi{(double2 *)d_y};
+    if (A->spmv_kind == HZ_SPMV_FF) {
+        HZ_CUDA(split_ff_vec(A->n, (const double2 *)d_x, A->x_ff, (cudaStream_t)stream));
+        HZ_CUDA(launch_spmv_ff(A->group, mat_view<double2>(A), A->x_ff, epi, RedScratch{}, grid,
+                               (cudaStream_t)stream));
+        return HZ_OK;
+    }
+    HZ_CUDA(launch_spmv<double2>(A->spmv_kind, A->group, mat_view<double2>(A), (const double2 *)d_x, epi,
+                                 RedScratch{}, grid, (cudaStream_t)stream));
+    return HZ_OK;
+}
+
+extern "C" HZ_API hz_status hz_cspmv(hz_mat *A, const hz_c *d_x, hz_c *d_y, void *stream) {
+    HZ_CHECK(A, "hz_cspmv: null handle");
+    if (A->n == 0) return HZ_OK;
+    HZ_CHECK(d_x && d_y, "hz_cspmv: null vector");
+    HZ_CHECK((const void *)d_x != (const void *)d_y, "hz_cspmv: x and y must not alias");
+    HZ_TRY(ensure_c64(A, (cudaStream_t)stream));
+    const int grid = spmv_grid(A, A->spmv_kind, A->group);
+    EpiStore<float2> epi{(float2 *)d_y};
+    HZ_CUDA(launch_spmv<float2>(A->spmv_kind, A->group, mat_view<float2>(A), (const float2 *)d_x, epi,
+                                RedScratch{}, grid, (cudaStream_t)stream));
+    return HZ_OK;
+}
+
+extern "C" HZ_API hz_status hz_mat_set_spmv(hz_mat *A, int32_t kind, int32_t group) {
+    HZ_CHECK(A, "hz_mat_set_spmv: null handle");
+    if (kind == HZ_SPMV_SELL) {
+        HZ_CHECK(A->sell_val != nullptr, "hz_mat_set_spmv: the handle has no SELL copy (HZ_FLAG_SELL)");
+        A->spmv_kind = HZ_SPMV_SELL;
+        return HZ_OK;
+    }
+    HZ_CHECK(kind == HZ_SPMV_CSR_VECTOR || kind == HZ_SPMV_FF, "hz_mat_set_spmv: unknown kind");
+    HZ_CHECK(kind != HZ_SPMV_FF || A->val_ff != nullptr,
+             "hz_mat_set_spmv: the handle has no double-float copy (HZ_FLAG_FF)");
+    HZ_CHECK(group == 2 || group == 4 || group == 8 || group == 16 || group == 32,
+             "hz_mat_set_spmv: group must be 2, 4, 8, 16 or 32");
+    A->spmv_kind = kind;
+    A->group = group;
+    return HZ_OK;
+}

@@ -1,0 +1,250 @@
+// spmv.cuh -- complex CSR / SELL-C-sigma sparse matrix-vector product cores
+// with fused epilogues (Section 6 of the paper: y = A x on CSR storage).
+//
+// Row i of y is sum_{k = rowptr[i]}^{rowptr[i+1]-1} val[k] * x[col[k]].
+//
+// CSR-vector: a group of W lanes (W in {2,4,8,16,32}) owns one row at a
+// time; lane l accumulates entries beg+l, beg+l+W, ... with four FMAs per
+// complex multiply-accumulate, then the group folds its partial sums with
+// xor shuffles.  The matrix streams through L2 with evict-first hints and
+// bypasses L1; the gathered x goes through the read-only cache.
+//
+// SELL-C-sigma (C = 32): rows are sorted by length inside windows of sigma
+// rows and packed in chunks of 32 rows stored column-major, so one warp
+// reads 32 consecutive slots per step; slot columns of -1 are padding.
+//
+// Epilogue functors see every finished row once (on one lane) and may store
+// it, transform it, and add to NV per-thread reduction values that the
+// kernel folds into one grid total (single pass, deterministic order).
+#pragma once
+
+#include "arith.cuh"
+
+namespace hz {
+
+constexpr int kSpmvBlock = 256;
+constexpr int kSellC = 32;
+#ifndef HZ_FF_UNROLL
+#define HZ_FF_UNROLL 4
+#endif
+constexpr int kFFUnroll = HZ_FF_UNROLL;
+
+template <class T>
+struct MatView {
+    int n;
+    const int *rowptr;
+    const int *col;
+    const T *val;
+    // SELL-C-sigma (used when the kernel's W == 0)
+    int nchunks;
+    const int *chunk_off;
+    const int *chunk_w;
+    const int *perm;
+    const int *scol;
+    const T *sval;
+    // double-float split values (used by the ff kernels)
+    const float4 *vff;
+};
+
+// Epilogue interface (every fused SpMV epilogue provides):
+//   using Acc, R;  static constexpr int NV;  static constexpr bool kFFRow;
+//   static void zero(Acc &);  static R total(const Acc &);
+//   bool skip() const;                       grid-uniform early exit
+//   void row(int i, Y y, Acc (&acc)[N]) const;  Y = T, or float4 if kFFRow
+//   void finish(R (&tot)[N]) const;          thread 0 of the last block
+template <int W, class T, class Epi, int NV>
+__device__ __forceinline__ void csr_rows(const MatView<T> &A, const T *__restrict__ x, const Epi &epi,
+                                         typename Epi::Acc (&acc)[NV]) {
+    const int lane = threadIdx.x & (W - 1);
+    const unsigned gmask =
+        (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << ((threadIdx.x & 31) & ~(W - 1)));
+    const int groups = (gridDim.x * blockDim.x) / W;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) / W; row < A.n; row += groups) {
+        const int beg = __ldg(A.rowptr + row), end = __ldg(A.rowptr + row + 1);
+        T y = czero<T>();
+        for (int k = beg + lane; k < end; k += W) {
+            const T a = ld_stream(A.val + k);
+            const int c = ld_stream(A.col + k);
+            cmac(y, a, __ldg(x + c));
+        }
+#pragma unroll
+        for (int off = W / 2; off > 0; off >>= 1) {
+            y.x += __shfl_xor_sync(gmask, y.x, off, W);
+            y.y += __shfl_xor_sync(gmask, y.y, off, W);
+        }
+        if (lane == 0) epi.row(row, y, acc);
+    }
+}
+
+template <class T, class Epi, int NV>
+__device__ __forceinline__ void sell_rows(const MatView<T> &A, const T *__restrict__ x, const Epi &epi,
+                                          typename Epi::Acc (&acc)[NV]) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < A.nchunks; c += warps) {
+        const int off = __ldg(A.chunk_off + c), w = __ldg(A.chunk_w + c);
+        const int row = __ldg(A.perm + c * kSellC + lane);
+        T y = czero<T>();
+        for (int j = 0; j < w; ++j) {
+            const int slot = off + j * kSellC + lane;
+            const int cc = ld_stream(A.scol + slot);
+            if (cc >= 0) cmac(y, ld_stream(A.sval + slot), __ldg(x + cc));
+        }
+        if (row >= 0) epi.row(row, y, acc);
+    }
+}
+
+// Double-float row core: the same CSR-vector schedule, with the binary64
+// multiply-accumulate replaced by ff_mac on the binary32 pipes (four real
+// ff products per complex entry) and an ff fold across the group's lanes.
+// x is the ff split of the vector.  The row result goes to the epilogue as
+// a normalized ff pair (kFFRow) or rounded once to binary64 as hi + lo.
+template <int W, class Epi, int NV>
+__device__ __forceinline__ void csr_rows_ff(const MatView<double2> &A, const float4 *__restrict__ x,
+                                            const Epi &epi, typename Epi::Acc (&acc)[NV]) {
+    const int lane = threadIdx.x & (W - 1);
+    const unsigned gmask =
+        (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << ((threadIdx.x & 31) & ~(W - 1)));
+    const int groups = (gridDim.x * blockDim.x) / W;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) / W; row < A.n; row += groups) {
+        const int beg = __ldg(A.rowptr + row), end = __ldg(A.rowptr + row + 1);
+        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+        // kFFUnroll entries per lane per step: all their loads are issued
+        // before the first dependent gather, so each lane keeps several
+        // HBM requests in flight instead of one
+        for (int k0 = beg + lane; k0 < end; k0 += W * kFFUnroll) {
+            int c[kFFUnroll];
+            float4 a[kFFUnroll], v[kFFUnroll];
+#pragma unroll
+            for (int u = 0; u < kFFUnroll; ++u) {
+                const int k = k0 + u * W;
+                c[u] = k < end ? ld_stream(A.col + k) : -1;
+                a[u] = k < end ? ld_stream(A.vff + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kFFUnroll; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < kFFUnroll; ++u) {
+                if (c[u] < 0) break;
+                ff_mac(sr, cr, a[u].x, a[u].y, v[u].x, v[u].y);
+                ff_mac(sr, cr, -a[u].z, -a[u].w, v[u].z, v[u].w);
+                ff_mac(si, ci, a[u].x, a[u].y, v[u].z, v[u].w);
+                ff_mac(si, ci, a[u].z, a[u].w, v[u].x, v[u].y);
+            }
+        }
+#pragma unroll
+        for (int off = W / 2; off > 0; off >>= 1) {
+            const float s2 = __shfl_xor_sync(gmask, sr, off, W), c2 = __shfl_xor_sync(gmask, cr, off, W);
+            const float s3 = __shfl_xor_sync(gmask, si, off, W), c3 = __shfl_xor_sync(gmask, ci, off, W);
+            ff_acc(sr, cr, s2);
+            cr = __fadd_rn(cr, c2);
+            ff_acc(si, ci, s3);
+            ci = __fadd_rn(ci, c3);
+        }
+        if (lane == 0) {
+            if constexpr (Epi::kFFRow) {
+                const float2 r = ff_norm(sr, cr), i = ff_norm(si, ci);
+                epi.row(row, make_float4(r.x, r.y, i.x, i.y), acc);
+            } else {
+                epi.row(row, make_double2((double)sr + (double)cr, (double)si + (double)ci), acc);
+            }
+        }
+    }
+}
+
+// per-thread accumulators -> one grid total -> epi.finish (last block)
+template <class Epi, int NV>
+__device__ __forceinline__ void spmv_reduce(const Epi &epi, typename Epi::Acc (&acc)[NV], RedScratch red) {
+    using R = typename Epi::R;
+    R v[NV], tot[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = Epi::total(acc[j]);
+    if (grid_reduce_last<R, NV>(v, red, tot)) {
+        if (threadIdx.x == 0) epi.finish(tot);
+    }
+}
+
+template <int W, class T, class Epi>
+__global__ void __launch_bounds__(kSpmvBlock) k_spmv(MatView<T> A, const T *__restrict__ x, Epi epi,
+                                                     RedScratch red) {
+    constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
+    if (epi.skip()) return;
+    typename Epi::Acc acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
+    if constexpr (W == 0) sell_rows<T, Epi, NV>(A, x, epi, acc);
+    else csr_rows<W, T, Epi, NV>(A, x, epi, acc);
+    if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
+}
+
+// the same kernel on the double-float path (x given as its ff split)
+template <int W, class Epi>
+__global__ void __launch_bounds__(kSpmvBlock) k_spmv_ff(MatView<double2> A, const float4 *__restrict__ x, Epi epi,
+                                                        RedScratch red) {
+    constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
+    if (epi.skip()) return;
+    typename Epi::Acc acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
+    csr_rows_ff<W, Epi, NV>(A, x, epi, acc);
+    if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
+}
+
+// binary64 -> double-float split of a vector (xff[i] = split_ff(x[i])), on stream s
+cudaError_t split_ff_vec(int n, const double2 *x, float4 *xff, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// plain store epilogue: y[i] = (A x)_i
+template <class T>
+struct EpiStore {
+    using R = typename Cplx<T>::R;
+    using Acc = R;
+    static constexpr int NV = 0;
+    static constexpr bool kFFRow = false;
+    T *y;
+    __device__ static void zero(Acc &a) { a = Acc(0); }
+    __device__ static R total(const Acc &a) { return a; }
+    __device__ bool skip() const { return false; }
+    template <int N> __device__ void row(int i, T v, Acc (&)[N]) const { y[i] = v; }
+    template <int N> __device__ void finish(R (&)[N]) const {}
+};
+
+// launch helper: picks the template instance for the handle's variant
+template <class T, class Epi>
+cudaError_t launch_spmv(int kind, int group, const MatView<T> &A, const T *x, const Epi &epi,
+                        RedScratch red, int grid, cudaStream_t s) {
+    if (kind == HZ_SPMV_SELL) {
+        k_spmv<0, T, Epi><<<grid, kSpmvBlock, 0, s>>>(A, x, epi, red);
+    } else {
+        switch (group) {
+            case 2: k_spmv<2, T, Epi><<<grid, kSpmvBlock, 0, s>>>(A, x, epi, red); break;
+            case 4: k_spmv<4, T, Epi><<<grid, kSpmvBlock, 0, s>>>(A, x, epi, red); break;
+            case 8: k_spmv<8, T, Epi><<<grid, kSpmvBlock, 0, s>>>(A, x, epi, red); break;
+            case 16: k_spmv<16, T, Epi><<<grid, kSpmvBlock, 0, s>>>(A, x, epi, red); break;
+            default: k_spmv<32, T, Epi><<<grid, kSpmvBlock, 0, s>>>(A, x, epi, red); break;
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <class Epi>
+cudaError_t launch_spmv_ff(int group, const MatView<double2> &A, const float4 *xff, const Epi &epi, RedScratch red,
+                           int grid, cudaStream_t s) {
+    switch (group) {
+        case 2: k_spmv_ff<2, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red); break;
+        case 4: k_spmv_ff<4, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red); break;
+        case 8: k_spmv_ff<8, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red); break;
+        case 16: k_spmv_ff<16, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red); break;
+        default: k_spmv_ff<32, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red); break;
+    }
+    return cudaGetLastError();
+}
+
+// grid for a fused SpMV: enough blocks to cover the rows once, capped at a
+// whole number of waves over the SMs (the row loop is grid-stride).
+int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap = 8);
+
+template <class T>
+MatView<T> mat_view(const hz_mat *A);
+
+}  // namespace hz

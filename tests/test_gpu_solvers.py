@@ -1,0 +1,243 @@
+"""GPU parity: BiCGStab (FP64, mixed precision, batched) and the adjoint
+gradient through the C ABI, against the CPU oracle and dense LU.
+
+Solver parity is on the final answer (iteration paths differ by rounding):
+true relative residual <= tol on both sides, the solution against dense LU
+(or the oracle's x) to 1e-8, and the first five recursive residuals of the
+GPU history against the oracle's to 1e-10 relative.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from tests import _cases as K
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.as_tensor(a).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def true_relres(oracle, A, x, b):
+    r = b - oracle.zspmv(A, x)
+    return oracle.dznrm2(r) / oracle.dznrm2(b)
+
+
+@pytest.mark.parametrize("ff", [False, True])
+def test_bicgstab_c1_vs_oracle_and_history(hz, oracle, ff):
+    A, b, _ = W.c1_small_fd()
+    M = hz.Matrix.from_csr(A, ff=ff)
+    hist = torch.zeros(2001, dtype=torch.float64, device="cuda")
+    x, info = hz.zsolve(M, dev(b), tol=1e-10, maxit=2000, hist=hist)
+    xo, io = oracle.bicgstab(A, b, tol=1e-10, maxit=2000)
+    assert info.converged and io.status == 0
+    assert abs(info.iters - io.iters) <= 5
+    xg = host(x)
+    assert true_relres(oracle, A, xg, b) <= 1e-10
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+    h = host(hist)
+    assert h[0] == 1.0
+    assert np.all(np.abs(h[1:6] - io.hist[1:6]) <= 1e-10 * io.hist[1:6])
+
+
+def test_bicgstab_vs_dense_lu_8cubed(hz, oracle):
+    A = W.fd_helmholtz_box(8, kh=0.5, damping=0.05)
+    b = K.vectors(A.n, 1001)[0]
+    x_lu = np.linalg.solve(A.to_scipy().toarray(), b)
+    M = hz.Matrix.from_csr(A)
+    x, info = hz.zsolve(M, dev(b), tol=1e-10, maxit=2000)
+    assert info.converged
+    assert np.linalg.norm(host(x) - x_lu) / np.linalg.norm(x_lu) <= 1e-8
+
+
+def test_bicgstab_manufactured_solution(hz, oracle):
+    A, _, xs = W.c1_small_fd()
+    b = oracle.zspmv(A, xs)
+    M = hz.Matrix.from_csr(A)
+    x, info = hz.zsolve(M, dev(b), tol=1e-12, maxit=2000)
+    assert info.converged and info.relres_true <= 1e-12
+    assert np.linalg.norm(host(x) - xs) / np.linalg.norm(xs) <= 1e-8
+
+
+@pytest.mark.parametrize("variant", [("csr", 2), ("csr", 8), ("sell", 0), ("ff", 4), ("ff", 8)])
+def test_bicgstab_cylinder_variants(hz, oracle, variant):
+    A, b = K.small_cylinder()
+    M = hz.Matrix.from_csr(A, sell=True, ff=True)
+    M.set_spmv(*variant)
+    x, info = hz.zsolve(M, dev(b), tol=1e-10, maxit=3000)
+    xo, io = oracle.bicgstab(A, b, tol=1e-10, maxit=3000)
+    assert info.status == io.status
+    if io.status == 0:
+        assert true_relres(oracle, A, host(x), b) <= 1e-10
+        assert np.linalg.norm(host(x) - xo) / np.linalg.norm(xo) <= 1e-7
+
+
+def test_bicgstab_edge_cases(hz, oracle):
+    A, b, _ = W.c1_small_fd()
+    M = hz.Matrix.from_csr(A)
+    # b = 0 gives x = 0 in zero iterations
+    x0 = dev(np.ones(A.n, dtype=np.complex128))
+    x, info = hz.zsolve(M, torch.zeros(A.n, dtype=torch.complex128, device="cuda"), x=x0)
+    assert info.converged and info.iters == 0 and np.all(host(x) == 0)
+    # maxit = 0: not converged, x = x0
+    x, info = hz.zsolve(M, dev(b), maxit=0)
+    assert info.status == 4 and info.iters == 0 and np.all(host(x) == 0)
+    # maxit = 3 stops at 3 iterations like the oracle
+    x, info = hz.zsolve(M, dev(b), maxit=3)
+    xo, io = oracle.bicgstab(A, b, maxit=3)
+    assert info.status == io.status == 4 and info.iters == io.iters == 3
+    assert np.linalg.norm(host(x) - xo) <= 1e-10 * np.linalg.norm(xo)
+    # exact start: x0 = solution of the oracle at 1e-12 converges immediately
+    xs, _ = oracle.bicgstab(A, b, tol=1e-13)
+    x, info = hz.zsolve(M, dev(b), x=dev(xs.copy()), tol=1e-10)
+    assert info.converged and info.iters == 0
+    # NaN in b is reported, not hidden
+    bn = b.copy()
+    bn[5] = np.nan
+    x, info = hz.zsolve(M, dev(bn))
+    assert info.status == 6
+
+
+def test_bicgstab_breakdown_2x2(hz, oracle):
+    A = K.breakdown_2x2()
+    b = np.array([1.0, 0.0], dtype=np.complex128)
+    M = hz.Matrix.from_csr(A)
+    x, info = hz.zsolve(M, dev(b), maxit=10)
+    _, io = oracle.bicgstab(A, b, maxit=10)
+    assert io.status == 5 and info.status == 5 and info.iters == io.iters == 1
+
+
+def test_bicgstab_reuse_graph_new_pointers(hz, oracle):
+    """A second solve with other b/x tensors reuses the captured graph."""
+    A, b, xs = W.c1_small_fd()
+    M = hz.Matrix.from_csr(A)
+    for seed in (1, 2, 3):
+        bb = K.vectors(A.n, seed)[0]
+        x, info = hz.zsolve(M, dev(bb), tol=1e-10)
+        assert info.converged and true_relres(oracle, A, host(x), bb) <= 1e-10
+
+
+def test_mixed_precision_c1(hz, oracle):
+    A, b, _ = W.c1_small_fd()
+    M = hz.Matrix.from_csr(A, c64=True)
+    x, info = hz.zsolve(M, dev(b), tol=1e-10, maxit=5000, mode="mixed")
+    xo, io = oracle.bicgstab(A, b, tol=1e-10, maxit=2000)
+    xm, dm = oracle.refine_mixed(A, b, tol=1e-10)
+    assert info.converged and dm["status"] == 0
+    xg = host(x)
+    assert true_relres(oracle, A, xg, b) <= 1e-10
+    # error against the FP64 oracle solution: bounded by the residual level
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+    assert info.outer >= 2
+
+
+def test_mixed_precision_fd_boxes(hz, oracle):
+    """Refinement on FD boxes of several sizes (SELL and CSR SpMV): the FP64
+    true residual reaches tol whenever the oracle's refinement converges."""
+    for m, kh in ((12, 0.3), (20, 0.5)):
+        A = W.fd_helmholtz_box(m, kh=kh, damping=0.05)
+        b = K.vectors(A.n, 300 + m)[0]
+        xm, dm = oracle.refine_mixed(A, b, tol=1e-10)
+        for sell in (False, True):
+            M = hz.Matrix.from_csr(A, c64=True, sell=sell)
+            x, info = hz.zsolve(M, dev(b), tol=1e-10, maxit=20000, mode="mixed")
+            if dm["status"] == 0:
+                assert info.converged, info
+                assert true_relres(oracle, A, host(x), b) <= 1e-10
+                assert np.linalg.norm(host(x) - xm) / np.linalg.norm(xm) <= 1e-8
+
+
+def test_mixed_precision_stagnation_reported(hz, oracle):
+    """On the jittered cylinder the complex64 inner solve cannot reach the
+    FP64 tolerance; the solver must stop at its caps and report it."""
+    A, b = K.small_cylinder()
+    M = hz.Matrix.from_csr(A, c64=True)
+    x, info = hz.zsolve(M, dev(b), tol=1e-10, maxit=20000, mode="mixed", max_outer=20)
+    assert info.status in (0, 4, 6)
+    if info.status == 4:
+        assert info.outer == 20 or info.iters >= 20000
+    if info.status == 0:
+        assert true_relres(oracle, A, host(x), b) <= 1e-10
+
+
+def test_batched_uneven_systems(hz, oracle):
+    systems = [W.fd_helmholtz_box(m, kh=kh, damping=0.05) for m in (6, 11, 16) for kh in (0.3, 0.7)]
+    Ac, bc = K.small_cylinder()
+    systems.append(Ac)
+    bs = [K.vectors(A.n, 4000 + s)[0] for s, A in enumerate(systems)]
+    bs[-1] = bc
+    mats = [hz.Matrix.from_csr(A) for A in systems]
+    xs, infos = hz.zsolve_batched(mats, [dev(b) for b in bs], tol=1e-10, maxit=3000)
+    for A, b, x, info in zip(systems, bs, xs, infos):
+        xo, io = oracle.bicgstab(A, b, tol=1e-10, maxit=3000)
+        assert info.status == io.status
+        if io.status == 0:
+            assert true_relres(oracle, A, host(x), b) <= 1e-10
+            assert np.linalg.norm(host(x) - xo) / np.linalg.norm(xo) <= 1e-8
+            # rounding-order differences move the exit by a few percent of the
+            # iterations on slowly converging systems
+            assert abs(info.iters - io.iters) <= max(5, 0.05 * io.iters)
+
+
+def test_batched_edge_cases(hz, oracle):
+    A, b, _ = W.c1_small_fd()
+    M = hz.Matrix.from_csr(A)
+    zero = torch.zeros(A.n, dtype=torch.complex128, device="cuda")
+    xs, infos = hz.zsolve_batched([M, M], [zero, dev(b)], tol=1e-10, maxit=0)
+    assert infos[0].status == 0 and infos[0].iters == 0
+    assert infos[1].status == 4
+
+
+def _loss_and_grad_dense(L, kappa2, theta, b, idx, d):
+    A = L - kappa2 * np.diag(theta)
+    x = np.linalg.solve(A, b)
+    res = x[idx] - d
+    loss = float(np.sum(np.abs(res) ** 2))
+    g = np.zeros_like(x)
+    g[idx] = 2 * res                      # conjugate-Wirtinger gradient wrt x
+    lam = np.linalg.solve(A.conj().T, g)  # A^H lambda = g
+    # dL/dA_ii = -lambda_i conj(x_i) and dA_ii/dtheta_i = -kappa2 (holomorphic)
+    grad_theta = kappa2 * lam * np.conj(x)
+    return loss, grad_theta
+
+
+def test_adjoint_gradient_dense_lu_and_fd(hz):
+    m = 10
+    prob = W.c5_inverse_problem(m=m, nsample=64)
+    L = prob["L"]
+    kappa2 = prob["kappa2"]
+    theta = prob["theta"]
+    # per-unknown damping keeps the small system well conditioned
+    theta = theta * (1 + 0.05j)
+    n = L.n
+    # the handle's value tensor is the operator A(theta) = L - kappa2 diag(theta)
+    A0 = W.fd_helmholtz_box(m, kh=0.5, damping=0.0, diag_shift=kappa2 * theta)
+    M = hz.Matrix.from_csr(A0)
+    base = dev(L.to_scipy().diagonal().astype(np.complex128))
+    idx = prob["sample_idx"]
+    d = prob["data"]
+    th = dev(theta).requires_grad_(True)
+    b = dev(prob["b"])
+    x = hz.solve_diag_param(th, b, M, base, -kappa2, tol=1e-12, maxit=5000)
+    loss = torch.sum(torch.abs(x[dev(idx)] - dev(d)) ** 2)
+    loss.backward()
+    g_gpu = host(th.grad)
+    loss_lu, g_lu = _loss_and_grad_dense(L.to_scipy().toarray(), kappa2, theta, prob["b"], idx, d)
+    assert abs(float(loss) - loss_lu) <= 1e-9 * loss_lu
+    assert np.linalg.norm(g_gpu - g_lu) <= 1e-6 * np.linalg.norm(g_lu)
+    # central differences along seeded directions: dL = Re sum conj(grad_i) v_i
+    eps = 1e-6
+    for v in W.c5_directions(n, count=5):
+        lp, _ = _loss_and_grad_dense(L.to_scipy().toarray(), kappa2, theta + eps * v, prob["b"], idx, d)
+        lm, _ = _loss_and_grad_dense(L.to_scipy().toarray(), kappa2, theta - eps * v, prob["b"], idx, d)
+        fd = (lp - lm) / (2 * eps)
+        an = float(np.real(np.vdot(g_gpu, v)))
+        assert abs(fd - an) <= 1e-5 * max(abs(fd), 1e-12)

@@ -1,0 +1,179 @@
+"""GPU parity: SpMV and BLAS-1 through the C ABI against the CPU oracle.
+
+Tolerances (derived from binary64 rounding): an SpMV entry is compared
+against the magnitude it is rounded against, |y_gpu - y_ref|_i <=
+1e-13 * sum_j |a_ij| |x_j|; a dot product against sum |x_i| |y_i|; a norm
+relative to itself.  Integer/structural work (pattern, index base) is exact.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from tests import _cases as K
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-13
+
+
+def dev(a):
+    return torch.as_tensor(a).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def check_spmv(hz, oracle, A, x, variants):
+    M = hz.Matrix.from_csr(A, sell=True, validate=True, ff=True)
+    ref = oracle.zspmv(A, x)
+    scale = K.row_abs_scale(A, x)
+    xd = dev(x)
+    for kind, g in variants:
+        M.set_spmv(kind, g)
+        y = host(hz.zspmv(M, xd))
+        err = np.abs(y - ref)
+        bad = err > TOL * scale + 1e-300
+        assert not bad.any(), (kind, g, int(bad.sum()), float((err / np.maximum(scale, 1e-300)).max()))
+    M.close()
+
+
+ALL_VARIANTS = [("csr", 2), ("csr", 4), ("csr", 8), ("csr", 16), ("csr", 32), ("sell", 0),
+                ("ff", 2), ("ff", 4), ("ff", 8), ("ff", 16), ("ff", 32)]
+
+
+def test_spmv_worked_example_exact(hz, oracle):
+    """The paper's 5x5 CSR example (Section 3.2): integer data, exact results."""
+    A = K.worked_example_csr(1 + 2j)
+    M = hz.Matrix.from_csr(A, sell=True, validate=True, ff=True)
+    for kind, g in ALL_VARIANTS:
+        M.set_spmv(kind, g)
+        y = host(hz.zspmv(M, dev(np.ones(5, dtype=np.complex128))))
+        assert np.array_equal(y, np.array([17, 9, 8, 5, 16]) * (1 + 2j))
+        for j in range(5):
+            e = np.zeros(5, dtype=np.complex128)
+            e[j] = 1
+            col = host(hz.zspmv(M, dev(e)))
+            assert np.array_equal(col, oracle.zspmv(A, e))
+
+
+def test_spmv_one_based(hz):
+    """index_base 1 (the paper's IA(n+1) = nz+1 convention) gives the same product."""
+    A = K.worked_example_csr(1 - 1j)
+    rp = dev(A.rowptr + 1)
+    cl = dev(A.col + 1)
+    vl = dev(A.val)
+    M = hz.Matrix(rp, cl, vl, index_base=1, validate=True)
+    x = K.vectors(5, 3)[0]
+    y = host(hz.zspmv(M, dev(x)))
+    assert np.allclose(y, A.to_scipy() @ x, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("seed,n,maxrow,longs", [(1, 1, 3, ()), (2, 37, 9, ()), (3, 1000, 40, (300, 513)),
+                                                  (4, 4099, 16, (700,)), (5, 257, 70, ())])
+def test_spmv_random_ragged(hz, oracle, seed, n, maxrow, longs):
+    A = K.random_csr(n, seed, max_row=maxrow, long_rows=longs)
+    x = K.vectors(n, seed + 100)[0]
+    check_spmv(hz, oracle, A, x, ALL_VARIANTS)
+
+
+def test_spmv_fd_and_cylinder(hz, oracle):
+    A, b, xs = W.c1_small_fd()
+    check_spmv(hz, oracle, A, xs, ALL_VARIANTS)
+    Ac, bc = K.small_cylinder()
+    check_spmv(hz, oracle, Ac, K.vectors(Ac.n, 11)[0], ALL_VARIANTS)
+
+
+def test_spmv_empty_matrix(hz):
+    M = hz.Matrix(dev(np.zeros(1, np.int32)), dev(np.zeros(0, np.int32)), dev(np.zeros(0, np.complex128)))
+    y = hz.zspmv(M, torch.zeros(0, dtype=torch.complex128, device="cuda"))
+    assert y.numel() == 0
+
+
+def test_spmv_bad_csr_rejected(hz):
+    A = K.worked_example_csr()
+    bad = A.col.copy()
+    bad[3] = 9
+    with pytest.raises(hz.HzError):
+        hz.Matrix(dev(A.rowptr), dev(bad), dev(A.val), validate=True)
+    rp = A.rowptr.copy()
+    rp[2], rp[3] = rp[3], rp[2]
+    with pytest.raises(hz.HzError):
+        hz.Matrix(dev(rp), dev(A.col), dev(A.val), validate=True)
+
+
+def test_spmv_c2_full_size_sampled(hz, oracle):
+    """C2 cylinder (~618k rows, ~9.2M nonzeros) in the launch configuration the
+    benchmark times, checked entry by entry against the oracle."""
+    A, b = W.c2_cylinder()
+    x = K.vectors(A.n, 2002)[0]
+    ref = oracle.zspmv(A, x)
+    scale = K.row_abs_scale(A, x)
+    for ff in (False, True):
+        M = hz.Matrix.from_csr(A, ff=ff)
+        y = host(hz.zspmv(M, dev(x)))
+        rel = np.abs(y - ref) / scale
+        assert rel.max() <= TOL, (ff, float(rel.max()))
+        M.close()
+
+
+def test_cspmv_complex64(hz, oracle):
+    A, b = K.small_cylinder()
+    x = K.vectors(A.n, 5)[0].astype(np.complex64)
+    M = hz.Matrix.from_csr(A, c64=True)
+    y = host(hz.cspmv(M, dev(x)))
+    ref = oracle.cspmv(A, x)
+    scale = K.row_abs_scale(A, x.astype(np.complex128))
+    assert np.all(np.abs(y - ref) <= 4e-6 * scale)
+
+
+# --------------------------------------------------------------------------- BLAS-1
+SIZES = [0, 1, 3, 1023, 1024, 4097, 100003, 1000000 + 7]
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_blas1_parity(hz, oracle, n):
+    x, y = K.vectors(n, 6001 + n) if n else (np.zeros(0, np.complex128),) * 2
+    xd, yd = dev(x), dev(y)
+    absdot = float(np.sum(np.abs(x) * np.abs(y)))
+    for fn, ref in ((hz.zdotc, oracle.zdotc), (hz.zdotu, oracle.zdotu)):
+        got = complex(host(fn(xd, yd))[0])
+        assert abs(got - ref(x, y)) <= TOL * absdot + 1e-300
+    nr = float(host(hz.dznrm2(xd))[0])
+    assert abs(nr - oracle.dznrm2(x)) <= TOL * max(oracle.dznrm2(x), 1e-300)
+    a = 0.3 - 1.7j
+    got = host(hz.zaxpy(a, xd, yd.clone()))
+    ref = oracle.zaxpy(a, x, y)
+    assert np.all(np.abs(got - ref) <= 1e-15 * (abs(a) * np.abs(x) + np.abs(y)))
+    got = host(hz.zscal(a, xd.clone()))
+    ref = oracle.zscal(a, x)
+    assert np.all(np.abs(got - ref) <= 1e-15 * abs(a) * np.abs(x))
+    assert np.array_equal(host(hz.zcopy(xd)), oracle.zcopy(x))
+    assert np.array_equal(host(hz.zconj(xd)), np.conj(x))
+
+
+def test_blas1_device_alpha_and_determinism(hz):
+    n = 3_000_001
+    x, y = K.vectors(n, 77)
+    xd, yd = dev(x), dev(y)
+    r1 = host(hz.zdotc(xd, yd))
+    r2 = host(hz.zdotc(xd, yd))
+    assert r1[0] == r2[0]              # fixed launch shape: bitwise reproducible
+    alpha = hz.zdotc(xd, xd)           # alpha read on the device, no host round trip
+    got = host(hz.zaxpy(alpha, xd, yd.clone()))
+    a = complex(host(alpha)[0])
+    assert np.allclose(got, a * x + y, rtol=1e-13, atol=1e-9)
+
+
+def test_blas1_closed_forms(hz):
+    """|x_i| = 1 gives ||x||^2 = n and zdotc(x, x) = n exactly up to rounding."""
+    n = 1 << 20
+    phi = np.random.default_rng(9).uniform(0, 2 * np.pi, n)
+    x = np.exp(1j * phi)
+    xd = dev(x)
+    assert abs(float(host(hz.dznrm2(xd))[0]) ** 2 - n) < 1e-9 * n
+    d = complex(host(hz.zdotc(xd, xd))[0])
+    assert abs(d.real - n) < 1e-9 * n and abs(d.imag) < 1e-9 * n

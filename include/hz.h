@@ -160,6 +160,32 @@ HZ_API hz_status hz_zdotc(int64_t n, const hz_z *d_x, const hz_z *d_y, hz_z *d_r
 HZ_API hz_status hz_zdotu(int64_t n, const hz_z *d_x, const hz_z *d_y, hz_z *d_result,
                           void *stream);
 
+/*
+ * hz_zdotc without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory,
+ * for example code that runs inside a fixed memory budget already handed to
+ * its own pool allocator, or code on a latency-critical path where the
+ * implicit device synchronisation of cudaMalloc is not acceptable.
+ * hz_zdotc allocates its reduction scratch on the first call on each stream;
+ * this variant instead keeps its scratch (1 MiB of tile partial sums and a
+ * completion counter) in a fixed array compiled into the library, present on
+ * every GPU that loads the library until the process exits.
+ *
+ * Result, arguments and errors as hz_zdotc, except:
+ *  - n must be at most 2^28 (268,435,456); larger n returns HZ_ERR_ARG.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call shares the one array (the counter is cleared on the caller's
+ *    stream at each call; the partial sums keep the last call's contents),
+ *    so calls whose kernels overlap on the GPU -- on different streams or
+ *    from different threads -- race and give wrong results.  Serialise them.
+ *  - The sum is folded over fixed tiles of 4096 elements, so the result is
+ *    bitwise reproducible across GPUs; it may differ from hz_zdotc's in the
+ *    last bits.
+ */
+HZ_API hz_status hz_zdotc_noalloc(int64_t n, const hz_z *d_x, const hz_z *d_y, hz_z *d_result,
+                                  void *stream);
+
 /* *d_result = sqrt(sum_i |x_i|^2) (Section 5, L2 norm). */
 HZ_API hz_status hz_dznrm2(int64_t n, const hz_z *d_x, double *d_result, void *stream);
 

@@ -28,7 +28,7 @@ EXPORTS = (
     "hz_zspmv",
     "hz_cspmv", "hz_zdotc", "hz_zdotu", "hz_dznrm2", "hz_zaxpy", "hz_zscal", "hz_zcopy",
     "hz_zconj", "hz_zsolve", "hz_zsolve_opts", "hz_zsolve_batched", "hz_outer_on_pattern",
-    "hz_mat_set_diag", "hz_diag_grad", "hz_last_error", "hz_version",
+    "hz_mat_set_diag", "hz_diag_grad", "hz_last_error", "hz_version", "hz_zdotc_noalloc",
 )
 
 
@@ -82,6 +82,7 @@ def load():
         "hz_cspmv": [P, P, P, P],
         "hz_zdotc": [i64, P, P, P, P],
         "hz_zdotu": [i64, P, P, P, P],
+        "hz_zdotc_noalloc": [i64, P, P, P, P],
         "hz_dznrm2": [i64, P, P, P],
         "hz_zaxpy": [i64, P, P, P, P],
         "hz_zscal": [i64, P, P, P],

@@ -89,7 +89,7 @@ def peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("spmv.cuh", "hz_internal.cuh", "spmv.cu"):
+    for f in ("spmv.cuh", "hz_internal.cuh", "arith.cuh", "spmv.cu"):
         with open(os.path.join(ROOT, "paper_2112_06465_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -213,6 +213,21 @@ def run_reference(args):
 DTYPES = {"fp64": "f64", "ff": "f32x2 (double-float complex128: hi+lo binary32 pairs)"}
 
 
+def run_spmv_only(args):
+    """Three launches of the C2 SpMV (the roofline kernel), for ncu captures."""
+    import torch
+    import paper_2112_06465_gb300 as hz
+    A, _ = build_workload()
+    M = hz.Matrix.from_csr(A, ff=args.arith == "ff")
+    M.set_spmv("ff" if args.arith == "ff" else "csr", args.group)
+    x = torch.randn(A.n, dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        hz.zspmv(M, x, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"spmv_only": True, "arith": args.arith, "group": args.group, "n": A.n, "nnz": A.nnz}))
+
+
 def workload_config(A, maxit, arith="fp64"):
     return {"workload": "C2 jittered P1-FEM cylinder nr=40 ntheta=96 nz=160 k=20 impedance ends, "
                         f"complex128 BiCGStab x0=0 tol=1e-10 maxit={maxit}",
@@ -229,12 +244,20 @@ def main():
     ap.add_argument("--impl", default="hz", choices=["hz", "reference"])
     ap.add_argument("--maxit", type=int, default=1000)
     ap.add_argument("--arith", default="ff", choices=["ff", "fp64"])
-    ap.add_argument("--ref-iters", type=int, default=60)
-    ap.add_argument("--cpu-iters", type=int, default=150)
+    # the oracle runs ~30 ms per C2 iteration on one Grace core: 500
+    # iterations are ~15 s of CPU work, 200 per reference step ~6 s
+    ap.add_argument("--ref-iters", type=int, default=200)
+    ap.add_argument("--cpu-iters", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spmv-only", action="store_true",
+                    help="profiling aid: build C2, run three SpMV launches of the chosen "
+                         "arithmetic (--arith, --group) and exit without timing")
+    ap.add_argument("--group", type=int, default=4, help="lanes per row for --spmv-only")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.spmv_only:
+        return run_spmv_only(args)
 
     import torch
     import torch.distributed as dist

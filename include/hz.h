@@ -80,10 +80,12 @@ enum {
 enum {
     HZ_SPMV_CSR_VECTOR = 0,  /* a group of `group` lanes per row */
     HZ_SPMV_SELL = 1,        /* SELL-C-sigma, one lane per row, C = 32 */
-    HZ_SPMV_FF = 2           /* CSR-vector in double-float arithmetic: every binary64 value is
+    HZ_SPMV_FF = 2,          /* CSR-vector in double-float arithmetic: every binary64 value is
                                 split into hi + lo binary32 parts (48 significant bits) and each
                                 product and sum uses error-free transformations; per-entry error
                                 <= about (4 + row length / group) * 2^-48 * sum_j |a_ij| |x_j| */
+    HZ_SPMV_SELL_FF = 3      /* SELL-C-sigma layout in double-float arithmetic (one lane per row;
+                                error bound as HZ_SPMV_FF with group 1) */
 };
 
 typedef struct {
@@ -128,7 +130,8 @@ HZ_API hz_status hz_mat_query(const hz_mat *A, hz_mat_props *props);
  * Force the SpMV variant of a handle: kind HZ_SPMV_CSR_VECTOR or HZ_SPMV_FF
  * with group in {2, 4, 8, 16, 32} lanes per row (HZ_SPMV_FF needs a handle
  * created with HZ_FLAG_FF), or HZ_SPMV_SELL (the handle must have been
- * created with HZ_FLAG_SELL).  Overrides the histogram choice and the
+ * created with HZ_FLAG_SELL), or HZ_SPMV_SELL_FF (both flags; group is
+ * ignored for the SELL kinds).  Overrides the histogram choice and the
  * autotuner; solver graphs built for the old variant are rebuilt on the
  * next solve.  Errors: HZ_ERR_ARG for an unknown variant.
  */
@@ -142,9 +145,10 @@ HZ_API hz_status hz_mat_refresh_values(hz_mat *A, void *stream);
 
 /*
  * y = A x (Section 6, CSR matrix-vector product), complex128.
- * d_x and d_y have n entries and must not overlap.  On the HZ_SPMV_FF
- * variant the handle's own x scratch holds the split of d_x, so calls on
- * one handle must not overlap in time (different handles may).
+ * d_x and d_y have n entries and must not overlap.  On the double-float
+ * variants (HZ_SPMV_FF, HZ_SPMV_SELL_FF) the handle's own x scratch holds
+ * the split of d_x, so calls on one handle must not overlap in time
+ * (different handles may).
  */
 HZ_API hz_status hz_zspmv(const hz_mat *A, const hz_z *d_x, hz_z *d_y, void *stream);
 

@@ -549,11 +549,12 @@ static hz_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &de
 // one SpMV with epilogue, on the kernel family of the vector element type
 template <class V, class Epi>
 static void spmv_on(const Solver *S, const hz_mat *A, const V *x, const Epi &e, cudaStream_t cs) {
+    const bool sell = S->kind == HZ_SPMV_SELL || S->kind == HZ_SPMV_SELL_FF;
     if constexpr (std::is_same<V, float4>::value) {
-        launch_spmv_ff(S->group, mat_view<double2>(A), x, e, S->red, S->grid_spmv, cs);
+        launch_spmv_ff(sell, S->group, mat_view<double2>(A), x, e, S->red, S->grid_spmv, cs);
     } else {
-        const int kind = S->kind == HZ_SPMV_SELL ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR;
-        launch_spmv<V>(kind, S->group, mat_view<V>(A), x, e, S->red, S->grid_spmv, cs);
+        launch_spmv<V>(sell ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR, S->group, mat_view<V>(A), x, e, S->red,
+                       S->grid_spmv, cs);
     }
 }
 
@@ -656,7 +657,7 @@ static hz_status build_graph(Solver *S, const hz_mat *A) {
     cudaGraph_t g;
     HZ_CUDA(cudaGraphCreate(&g, 0));
     S->graph = g;
-    const bool ff = S->kind == HZ_SPMV_FF;
+    const bool ff = S->kind == HZ_SPMV_FF || S->kind == HZ_SPMV_SELL_FF;
     if (S->mode == HZ_MODE_FP64)
         HZ_TRY(ff ? build_fp64_graph<float4>(S, A, g) : build_fp64_graph<double2>(S, A, g));
     else

@@ -125,6 +125,18 @@ __device__ __forceinline__ float4 ld_stream(const float4 *ptr) {
         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(ptr), "l"(pol_evict_first()));
     return v;
 }
+// the same loads with a policy created once by the caller
+__device__ __forceinline__ float4 ld_stream(const float4 *ptr, uint64_t pol) {
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int ld_stream(const int *ptr, uint64_t pol) {
+    int v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
 
 // ---------------------------------------------------------------------------
 // double-float ("ff") arithmetic on the binary32 pipes.
@@ -271,6 +283,7 @@ struct hz_mat {
     int32_t *sell_src = nullptr;         // [slots] CSR position of the slot (-1 = padding)
     double2 *sell_val = nullptr;         // [slots]
     float2 *sell_val32 = nullptr;        // [slots] complex64 copy, if c64
+    float4 *sell_vff = nullptr;          // [slots] double-float split, if SELL and FF
     // complex64 copy
     float2 *val32 = nullptr;
     // double-float split of the values (hi_re, lo_re, hi_im, lo_im) and the

@@ -24,13 +24,14 @@ __global__ void k_to_c64(int64_t n, const double2 *__restrict__ in, float2 *__re
 
 // SELL slot values from the CSR values through the slot -> CSR map
 __global__ void k_sell_gather(int64_t slots, const int *__restrict__ src, const double2 *__restrict__ val,
-                              double2 *__restrict__ sval, float2 *__restrict__ sval32) {
+                              double2 *__restrict__ sval, float2 *__restrict__ sval32, float4 *__restrict__ svff) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < slots;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int k = src[i];
         const double2 v = k >= 0 ? val[k] : make_double2(0.0, 0.0);
         sval[i] = v;
         if (sval32) sval32[i] = to_c64(v);
+        if (svff) svff[i] = split_ff(v);
     }
 }
 
@@ -49,7 +50,7 @@ cudaError_t split_ff_vec(int n, const double2 *x, float4 *xff, cudaStream_t s) {
 template <>
 MatView<double2> mat_view<double2>(const hz_mat *A) {
     MatView<double2> v{};
-    v.n = A->n; v.rowptr = A->rowptr; v.col = A->col; v.val = A->val; v.vff = A->val_ff;
+    v.n = A->n; v.rowptr = A->rowptr; v.col = A->col; v.val = A->val; v.vff = A->val_ff; v.svff = A->sell_vff;
     v.nchunks = A->sell_nchunks; v.chunk_off = A->sell_chunk_off; v.chunk_w = A->sell_chunk_w;
     v.perm = A->sell_perm; v.scol = A->sell_col; v.sval = A->sell_val;
     return v;
@@ -67,7 +68,8 @@ MatView<float2> mat_view<float2>(const hz_mat *A) {
 int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap) {
     DevInfo d;
     if (dev_info(&d) != HZ_OK) return 1;
-    int64_t threads = kind == HZ_SPMV_SELL ? (int64_t)A->sell_nchunks * 32 : (int64_t)A->n * group;
+    const bool sell = kind == HZ_SPMV_SELL || kind == HZ_SPMV_SELL_FF;
+    int64_t threads = sell ? (int64_t)A->sell_nchunks * 32 : (int64_t)A->n * group;
     return stream_grid(d, threads, kSpmvBlock, blocks_per_sm_cap);
 }
 
@@ -154,7 +156,7 @@ static hz_status refresh(hz_mat *A, cudaStream_t s) {
     }
     if (A->sell_val && A->sell_slots) {
         k_sell_gather<<<stream_grid(d, A->sell_slots, 256, 8), 256, 0, s>>>(
-            A->sell_slots, A->sell_src, A->val, A->sell_val, A->sell_val32);
+            A->sell_slots, A->sell_src, A->val, A->sell_val, A->sell_val32, A->sell_vff);
         HZ_CUDA(cudaGetLastError());
     }
     return HZ_OK;
@@ -183,6 +185,7 @@ static hz_status autotune(hz_mat *A, cudaStream_t s) {
     if (A->sell_val) cand.push_back({HZ_SPMV_SELL, 0});
     if (A->val_ff)
         for (int w : {2, 4, 8, 16, 32}) cand.push_back({HZ_SPMV_FF, w});
+    if (A->sell_vff) cand.push_back({HZ_SPMV_SELL_FF, 0});
     float best = 1e30f;
     MatView<double2> V = mat_view<double2>(A);
     EpiStore<double2> epi{y};
@@ -192,7 +195,8 @@ static hz_status autotune(hz_mat *A, cudaStream_t s) {
         float tms[5];
         for (int rep = -1; rep < 5; ++rep) {
             cudaEventRecord(e0, s);
-            if (c.first == HZ_SPMV_FF) launch_spmv_ff(c.second, V, A->x_ff, epi, RedScratch{}, grid, s);
+            if (c.first == HZ_SPMV_FF || c.first == HZ_SPMV_SELL_FF)
+                launch_spmv_ff(c.first == HZ_SPMV_SELL_FF, c.second, V, A->x_ff, epi, RedScratch{}, grid, s);
             else launch_spmv<double2>(c.first, c.second, V, x, epi, RedScratch{}, grid, s);
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess) { st = HZ_ERR_CUDA; break; }
@@ -318,6 +322,13 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
         }
         if (n) cudaMemsetAsync(A->x_ff, 0, sizeof(float4) * n, s);
         A->spmv_kind = HZ_SPMV_FF;
+        if (A->sell_slots) {
+            if (cudaMalloc(&A->sell_vff, sizeof(float4) * A->sell_slots) != cudaSuccess) {
+                set_error("hz_csr_create: allocation failed");
+                return fail(HZ_ERR_ALLOC);
+            }
+            A->spmv_kind = HZ_SPMV_SELL_FF;
+        }
     }
     if ((st = refresh(A, s)) != HZ_OK) return fail(st);
     if (flags & HZ_FLAG_AUTOTUNE) {
@@ -343,6 +354,7 @@ extern "C" HZ_API hz_status hz_mat_destroy(hz_mat *A) {
     cudaFree(A->sell_col);
     cudaFree(A->sell_src);
     cudaFree(A->sell_val);
+    cudaFree(A->sell_vff);
     cudaFree(A->sell_val32);
     cudaFree(A->val32);
     cudaFree(A->val_ff);
@@ -379,10 +391,10 @@ extern "C" HZ_API hz_status hz_zspmv(const hz_mat *A, const hz_z *d_x, hz_z *d_y
     HZ_CHECK((const void *)d_x != (const void *)d_y, "hz_zspmv: x and y must not alias");
     const int grid = spmv_grid(A, A->spmv_kind, A->group);
     EpiStore<double2> epi{(double2 *)d_y};
-    if (A->spmv_kind == HZ_SPMV_FF) {
+    if (A->spmv_kind == HZ_SPMV_FF || A->spmv_kind == HZ_SPMV_SELL_FF) {
         HZ_CUDA(split_ff_vec(A->n, (const double2 *)d_x, A->x_ff, (cudaStream_t)stream));
-        HZ_CUDA(launch_spmv_ff(A->group, mat_view<double2>(A), A->x_ff, epi, RedScratch{}, grid,
-                               (cudaStream_t)stream));
+        HZ_CUDA(launch_spmv_ff(A->spmv_kind == HZ_SPMV_SELL_FF, A->group, mat_view<double2>(A), A->x_ff, epi,
+                               RedScratch{}, grid, (cudaStream_t)stream));
         return HZ_OK;
     }
     HZ_CUDA(launch_spmv<double2>(A->spmv_kind, A->group, mat_view<double2>(A), (const double2 *)d_x, epi,
@@ -396,10 +408,12 @@ extern "C" HZ_API hz_status hz_cspmv(hz_mat *A, const hz_c *d_x, hz_c *d_y, void
     HZ_CHECK(d_x && d_y, "hz_cspmv: null vector");
     HZ_CHECK((const void *)d_x != (const void *)d_y, "hz_cspmv: x and y must not alias");
     HZ_TRY(ensure_c64(A, (cudaStream_t)stream));
-    const int grid = spmv_grid(A, A->spmv_kind, A->group);
+    const int kind = (A->spmv_kind == HZ_SPMV_SELL || A->spmv_kind == HZ_SPMV_SELL_FF) ? HZ_SPMV_SELL
+                                                                                     : HZ_SPMV_CSR_VECTOR;
+    const int grid = spmv_grid(A, kind, A->group);
     EpiStore<float2> epi{(float2 *)d_y};
-    HZ_CUDA(launch_spmv<float2>(A->spmv_kind, A->group, mat_view<float2>(A), (const float2 *)d_x, epi,
-                                RedScratch{}, grid, (cudaStream_t)stream));
+    HZ_CUDA(launch_spmv<float2>(kind, A->group, mat_view<float2>(A), (const float2 *)d_x, epi, RedScratch{}, grid,
+                                (cudaStream_t)stream));
     return HZ_OK;
 }
 
@@ -408,6 +422,12 @@ extern "C" HZ_API hz_status hz_mat_set_spmv(hz_mat *A, int32_t kind, int32_t gro
     if (kind == HZ_SPMV_SELL) {
         HZ_CHECK(A->sell_val != nullptr, "hz_mat_set_spmv: the handle has no SELL copy (HZ_FLAG_SELL)");
         A->spmv_kind = HZ_SPMV_SELL;
+        return HZ_OK;
+    }
+    if (kind == HZ_SPMV_SELL_FF) {
+        HZ_CHECK(A->sell_vff != nullptr,
+                 "hz_mat_set_spmv: the handle has no double-float SELL copy (HZ_FLAG_SELL | HZ_FLAG_FF)");
+        A->spmv_kind = HZ_SPMV_SELL_FF;
         return HZ_OK;
     }
     HZ_CHECK(kind == HZ_SPMV_CSR_VECTOR || kind == HZ_SPMV_FF, "hz_mat_set_spmv: unknown kind");

@@ -28,6 +28,17 @@ constexpr int kSellC = 32;
 #define HZ_FF_UNROLL 4
 #endif
 constexpr int kFFUnroll = HZ_FF_UNROLL;
+#ifndef HZ_FF_MIN_BLOCKS
+#define HZ_FF_MIN_BLOCKS 1
+#endif
+#ifndef HZ_FF_CONTIG
+#define HZ_FF_CONTIG 0
+#endif
+#ifndef HZ_FF_TRANSPOSE
+#define HZ_FF_TRANSPOSE 0
+#endif
+constexpr bool kFFContig = HZ_FF_CONTIG != 0;        // contiguous row range per block
+constexpr bool kFFTranspose = HZ_FF_TRANSPOSE != 0;  // lane-transposed row outputs
 
 template <class T>
 struct MatView {
@@ -42,8 +53,9 @@ struct MatView {
     const int *perm;
     const int *scol;
     const T *sval;
-    // double-float split values (used by the ff kernels)
+    // double-float split values (used by the ff kernels), CSR and SELL order
     const float4 *vff;
+    const float4 *svff;
 };
 
 // Epilogue interface (every fused SpMV epilogue provides):
@@ -94,6 +106,18 @@ __device__ __forceinline__ void sell_rows(const MatView<T> &A, const T *__restri
     }
 }
 
+// row result handed to the epilogue: ff pair, or binary64 rounded once
+template <class Epi, int NV>
+__device__ __forceinline__ void ff_row_out(const Epi &epi, int row, float sr, float cr, float si, float ci,
+                                           typename Epi::Acc (&acc)[NV]) {
+    if constexpr (Epi::kFFRow) {
+        const float2 r = ff_norm(sr, cr), i = ff_norm(si, ci);
+        epi.row(row, make_float4(r.x, r.y, i.x, i.y), acc);
+    } else {
+        epi.row(row, make_double2((double)sr + (double)cr, (double)si + (double)ci), acc);
+    }
+}
+
 // Double-float row core: the same CSR-vector schedule, with the binary64
 // multiply-accumulate replaced by ff_mac on the binary32 pipes (four real
 // ff products per complex entry) and an ff fold across the group's lanes.
@@ -105,27 +129,46 @@ __device__ __forceinline__ void csr_rows_ff(const MatView<double2> &A, const flo
     const int lane = threadIdx.x & (W - 1);
     const unsigned gmask =
         (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << ((threadIdx.x & 31) & ~(W - 1)));
-    const int groups = (gridDim.x * blockDim.x) / W;
-    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) / W; row < A.n; row += groups) {
+    const uint64_t pol = pol_evict_first();
+    int row0, rstep, r_end;
+    if constexpr (kFFContig) {
+        // each block owns one contiguous range of rows, walked blockDim/W
+        // rows at a time (x reuse between neighbouring rows stays in L1)
+        rstep = blockDim.x / W;
+        int chunk = (A.n + gridDim.x - 1) / gridDim.x;
+        chunk = (chunk + rstep - 1) / rstep * rstep;
+        row0 = blockIdx.x * chunk + (int)threadIdx.x / W;
+        r_end = min(A.n, (blockIdx.x + 1) * chunk);
+    } else {
+        rstep = (gridDim.x * blockDim.x) / W;
+        row0 = (blockIdx.x * blockDim.x + threadIdx.x) / W;
+        r_end = A.n;
+    }
+    // with kFFTranspose, lane q of a group keeps the result of every W-th row
+    // the group finishes (q = k mod W), so the output conversion and the
+    // epilogue run once per W rows on all lanes instead of on one lane per row
+    float ksr = 0.f, kcr = 0.f, ksi = 0.f, kci = 0.f;
+    int krow = -1, q = 0;
+    for (int row = row0; row < r_end; row += rstep) {
         const int beg = __ldg(A.rowptr + row), end = __ldg(A.rowptr + row + 1);
         float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
         // kFFUnroll entries per lane per step: all their loads are issued
         // before the first dependent gather, so each lane keeps several
-        // HBM requests in flight instead of one
+        // HBM requests in flight instead of one.  Slots past the row end
+        // hold zeros and add exact zeros (no divergent exit).
         for (int k0 = beg + lane; k0 < end; k0 += W * kFFUnroll) {
             int c[kFFUnroll];
             float4 a[kFFUnroll], v[kFFUnroll];
 #pragma unroll
             for (int u = 0; u < kFFUnroll; ++u) {
                 const int k = k0 + u * W;
-                c[u] = k < end ? ld_stream(A.col + k) : -1;
-                a[u] = k < end ? ld_stream(A.vff + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                c[u] = k < end ? ld_stream(A.col + k, pol) : -1;
+                a[u] = k < end ? ld_stream(A.vff + k, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
             for (int u = 0; u < kFFUnroll; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int u = 0; u < kFFUnroll; ++u) {
-                if (c[u] < 0) break;
                 ff_mac(sr, cr, a[u].x, a[u].y, v[u].x, v[u].y);
                 ff_mac(sr, cr, -a[u].z, -a[u].w, v[u].z, v[u].w);
                 ff_mac(si, ci, a[u].x, a[u].y, v[u].z, v[u].w);
@@ -141,14 +184,59 @@ __device__ __forceinline__ void csr_rows_ff(const MatView<double2> &A, const flo
             ff_acc(si, ci, s3);
             ci = __fadd_rn(ci, c3);
         }
-        if (lane == 0) {
-            if constexpr (Epi::kFFRow) {
-                const float2 r = ff_norm(sr, cr), i = ff_norm(si, ci);
-                epi.row(row, make_float4(r.x, r.y, i.x, i.y), acc);
-            } else {
-                epi.row(row, make_double2((double)sr + (double)cr, (double)si + (double)ci), acc);
+        if constexpr (kFFTranspose) {
+            // the xor fold leaves the row total on every lane of the group
+            if (lane == q) { ksr = sr; kcr = cr; ksi = si; kci = ci; krow = row; }
+            if (++q == W) {
+                if (krow >= 0) ff_row_out<Epi, NV>(epi, krow, ksr, kcr, ksi, kci, acc);
+                q = 0;
+                krow = -1;
+            }
+        } else {
+            if (lane == 0) ff_row_out<Epi, NV>(epi, row, sr, cr, si, ci, acc);
+        }
+    }
+    if constexpr (kFFTranspose) {
+        if (krow >= 0) ff_row_out<Epi, NV>(epi, krow, ksr, kcr, ksi, kci, acc);
+    }
+}
+
+// Double-float SELL-C-sigma core: one lane per row, 32 rows per chunk stored
+// column-major, so each step of a warp reads 32 consecutive slots (512
+// contiguous bytes of values).  kFFUnroll slots per lane are loaded before
+// the first dependent gather.  No cross-lane fold, and the binary64 output
+// conversion covers 32 rows per instruction.  Padding slots hold value 0 and
+// column -1 (no gather; they add exact zeros).
+template <class Epi, int NV>
+__device__ __forceinline__ void sell_rows_ff(const MatView<double2> &A, const float4 *__restrict__ x,
+                                             const Epi &epi, typename Epi::Acc (&acc)[NV]) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < A.nchunks; c += warps) {
+        const int off = __ldg(A.chunk_off + c), w = __ldg(A.chunk_w + c);
+        const int row = __ldg(A.perm + c * kSellC + lane);
+        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+        for (int j0 = 0; j0 < w; j0 += kFFUnroll) {
+            int cc[kFFUnroll];
+            float4 a[kFFUnroll], v[kFFUnroll];
+#pragma unroll
+            for (int u = 0; u < kFFUnroll; ++u) {
+                const int slot = off + (j0 + u) * kSellC + lane;
+                const bool in = j0 + u < w;
+                cc[u] = in ? ld_stream(A.scol + slot) : -1;
+                a[u] = in ? ld_stream(A.svff + slot) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kFFUnroll; ++u) v[u] = cc[u] >= 0 ? __ldg(x + cc[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < kFFUnroll; ++u) {
+                ff_mac(sr, cr, a[u].x, a[u].y, v[u].x, v[u].y);
+                ff_mac(sr, cr, -a[u].z, -a[u].w, v[u].z, v[u].w);
+                ff_mac(si, ci, a[u].x, a[u].y, v[u].z, v[u].w);
+                ff_mac(si, ci, a[u].z, a[u].w, v[u].x, v[u].y);
             }
         }
+        if (row >= 0) ff_row_out<Epi, NV>(epi, row, sr, cr, si, ci, acc);
     }
 }
 
@@ -179,14 +267,15 @@ __global__ void __launch_bounds__(kSpmvBlock) k_spmv(MatView<T> A, const T *__re
 
 // the same kernel on the double-float path (x given as its ff split)
 template <int W, class Epi>
-__global__ void __launch_bounds__(kSpmvBlock) k_spmv_ff(MatView<double2> A, const float4 *__restrict__ x, Epi epi,
+__global__ void __launch_bounds__(kSpmvBlock, HZ_FF_MIN_BLOCKS) k_spmv_ff(MatView<double2> A, const float4 *__restrict__ x, Epi epi,
                                                         RedScratch red) {
     constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
     if (epi.skip()) return;
     typename Epi::Acc acc[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
-    csr_rows_ff<W, Epi, NV>(A, x, epi, acc);
+    if constexpr (W == 0) sell_rows_ff<Epi, NV>(A, x, epi, acc);
+    else csr_rows_ff<W, Epi, NV>(A, x, epi, acc);
     if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
 }
 
@@ -227,9 +316,14 @@ cudaError_t launch_spmv(int kind, int group, const MatView<T> &A, const T *x, co
     return cudaGetLastError();
 }
 
+// double-float kernels: SELL layout (sell != 0) or CSR-vector with `group` lanes
 template <class Epi>
-cudaError_t launch_spmv_ff(int group, const MatView<double2> &A, const float4 *xff, const Epi &epi, RedScratch red,
-                           int grid, cudaStream_t s) {
+cudaError_t launch_spmv_ff(int sell, int group, const MatView<double2> &A, const float4 *xff, const Epi &epi,
+                           RedScratch red, int grid, cudaStream_t s) {
+    if (sell) {
+        k_spmv_ff<0, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red);
+        return cudaGetLastError();
+    }
     switch (group) {
         case 2: k_spmv_ff<2, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red); break;
         case 4: k_spmv_ff<4, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red); break;

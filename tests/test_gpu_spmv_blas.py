@@ -42,7 +42,7 @@ def check_spmv(hz, oracle, A, x, variants):
 
 
 ALL_VARIANTS = [("csr", 2), ("csr", 4), ("csr", 8), ("csr", 16), ("csr", 32), ("sell", 0),
-                ("ff", 2), ("ff", 4), ("ff", 8), ("ff", 16), ("ff", 32)]
+                ("ff", 2), ("ff", 4), ("ff", 8), ("ff", 16), ("ff", 32), ("sellff", 0)]
 
 
 def test_spmv_worked_example_exact(hz, oracle):

@@ -49,6 +49,20 @@ def test_spmv_brute_force_dense(oracle, seed, n):
     assert np.all(np.abs(oracle.zspmv(A, x) - ref) <= 1e-13 * K.row_abs_scale(A, x) + 1e-300)
 
 
+def test_cspmv_brute_force_dense(oracle):
+    """complex64 product with binary32 sums against the exact product of the
+    same rounded data (binary32 error bound ~ row length * 2^-24)."""
+    A = K.random_csr(400, 21, max_row=30, long_rows=(300,))
+    x = K.vectors(400, 22)[0].astype(np.complex64)
+    a32 = A.val.astype(np.complex64)
+    exact = sp.csr_matrix((a32.astype(np.complex128), A.col, A.rowptr), shape=(400, 400)) @ x.astype(np.complex128)
+    got = oracle.cspmv(A, x, val32=a32)
+    scale = sp.csr_matrix((np.abs(a32).astype(np.float64), A.col, A.rowptr), shape=(400, 400)) @ np.abs(x)
+    lens = np.diff(A.rowptr)
+    assert np.all(np.abs(got - exact) <= (lens + 2) * 2.0 ** -23 * scale + 1e-30)
+    assert np.any(np.abs(got - exact) > 0)        # really binary32 arithmetic
+
+
 def test_spmv_complex_symmetry_invariant(oracle):
     """Helmholtz matrices are complex symmetric: u^T (A v) = v^T (A u)."""
     for A in (W.c1_small_fd()[0], K.small_cylinder()[0]):

@@ -84,8 +84,11 @@ enum {
                                 split into hi + lo binary32 parts (48 significant bits) and each
                                 product and sum uses error-free transformations; per-entry error
                                 <= about (4 + row length / group) * 2^-48 * sum_j |a_ij| |x_j| */
-    HZ_SPMV_SELL_FF = 3      /* SELL-C-sigma layout in double-float arithmetic (one lane per row;
+    HZ_SPMV_SELL_FF = 3,     /* SELL-C-sigma layout in double-float arithmetic (one lane per row;
                                 error bound as HZ_SPMV_FF with group 1) */
+    HZ_SPMV_FF_FLAT = 4      /* double-float, row blocks streamed flat: each entry's product is
+                                formed with coalesced loads and all lanes busy, then whole rows
+                                are summed from shared memory (the default with HZ_FLAG_FF) */
 };
 
 typedef struct {

@@ -87,6 +87,12 @@ __device__ __forceinline__ void vec_tiles(int n, F f) {
 
 __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
 
+// loop condition of the enclosing WHILE node; handle 0 = the graph has no
+// conditional node (the unrolled profiling graph), nothing to set
+__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, unsigned v) {
+    if (h) cudaGraphSetConditional(h, v);
+}
+
 template <class V, int NV>
 __device__ __forceinline__ bool vec_reduce(typename Ar<V>::Acc (&acc)[NV], RedScratch red,
                                            typename Ar<V>::R (&tot)[NV]) {
@@ -114,6 +120,8 @@ __global__ void __launch_bounds__(kVecBlock) k_bicg_p(int n, StateOf<V> *st, V *
                                                       const V *__restrict__ r, const V *__restrict__ v,
                                                       int *total_iters) {
     using A = Ar<V>;
+    pdl_wait();
+    pdl_release();
     if (*(volatile int *)&st->done) return;
     const typename A::S beta = A::scal(st->beta), omega = A::scal(st->omega);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -151,6 +159,8 @@ __global__ void __launch_bounds__(kVecBlock) k_bicg_s(int n, StateOf<V> *st, con
                                                       const V *__restrict__ r, const V *__restrict__ v,
                                                       RedScratch red, int outer_level) {
     using A = Ar<V>;
+    pdl_wait();
+    pdl_release();
     if (st->done) return;
     const typename A::S alpha = A::scal(st->alpha);
     typename A::Acc acc[1];
@@ -203,8 +213,10 @@ __global__ void __launch_bounds__(kVecBlock) k_bicg_xr(int n, StateOf<V> *st, co
                                                        RedScratch red, cudaGraphConditionalHandle h,
                                                        int outer_level) {
     using A = Ar<V>;
+    pdl_wait();
+    pdl_release();
     if (st->done) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0);
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(h, 0);
         return;
     }
     const typename A::S alpha = A::scal(st->alpha);
@@ -217,7 +229,7 @@ __global__ void __launch_bounds__(kVecBlock) k_bicg_xr(int n, StateOf<V> *st, co
             st->status = HZ_OK;
             st->done = 1;
             if (outer_level && ctl->hist) ctl->hist[st->iter] = st->rel;
-            cudaGraphSetConditional(h, 0);
+            set_cond(h, 0);
         }
         return;
     }
@@ -253,7 +265,7 @@ __global__ void __launch_bounds__(kVecBlock) k_bicg_xr(int n, StateOf<V> *st, co
             st->rho_old = st->rho;
             st->rho = rn;
         }
-        cudaGraphSetConditional(h, st->done ? 0 : 1);
+        set_cond(h, st->done ? 0 : 1);
     }
 }
 
@@ -312,7 +324,7 @@ struct EpiInit : EpiBase<V> {
             else if (st->iter >= ctl->maxit) st->status = HZ_NOT_CONVERGED;
             else { st->status = HZ_NOT_CONVERGED; st->done = 0; }
         }
-        cudaGraphSetConditional(h, st->done ? 0 : 1);
+        set_cond(h, st->done ? 0 : 1);
     }
 };
 
@@ -444,6 +456,8 @@ struct Solver {
     int n = 0;
     int kind = 0, group = 4;
     int grid_spmv = 1, grid_vec = 1;
+    int grid_spmv_cv = 1;   // grid of the binary64/complex64 CSR or SELL kernels
+    bool pdl = false;       // programmatic dependent launches inside the iteration
     void *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
     float2 *r32 = nullptr, *rh32 = nullptr, *p32 = nullptr, *v32 = nullptr, *s32 = nullptr, *t32 = nullptr,
            *d32 = nullptr;
@@ -548,30 +562,36 @@ static hz_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &de
 
 // one SpMV with epilogue, on the kernel family of the vector element type
 template <class V, class Epi>
-static void spmv_on(const Solver *S, const hz_mat *A, const V *x, const Epi &e, cudaStream_t cs) {
+static void spmv_on(const Solver *S, const hz_mat *A, const V *x, const Epi &e, cudaStream_t cs,
+                    bool pdl = false) {
     const bool sell = S->kind == HZ_SPMV_SELL || S->kind == HZ_SPMV_SELL_FF;
     if constexpr (std::is_same<V, float4>::value) {
-        launch_spmv_ff(sell, S->group, mat_view<double2>(A), x, e, S->red, S->grid_spmv, cs);
+        launch_spmv_ff(S->kind, S->group, mat_view<double2>(A), x, e, S->red, S->grid_spmv, cs, pdl);
     } else {
         launch_spmv<V>(sell ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR, S->group, mat_view<V>(A), x, e, S->red,
-                       S->grid_spmv, cs);
+                       S->grid_spmv_cv, cs, pdl);
     }
 }
 
 template <class V>
 static void launch_iteration(const Solver *S, const hz_mat *A, StateOf<V> *st, V *x, V *r, V *rh, V *p, V *v, V *s,
                              V *t, int *total, cudaGraphConditionalHandle h, int outer_level, cudaStream_t cs) {
+    // with S->pdl, F2..F5 are launched as programmatic dependents of their
+    // predecessor: each kernel's CTAs may be scheduled while the previous one
+    // drains and wait in pdl_wait() for its results
     const int n = S->n;
-    k_bicg_p<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, p, r, v, total);
+    const bool pdl = S->pdl;
+    launch_k(false, k_bicg_p<V>, S->grid_vec, kVecBlock, cs, n, st, p, r, v, total);
     EpiSigma<V> e2;
     e2.st = st; e2.v = v; e2.rh = rh;
-    spmv_on<V>(S, A, p, e2, cs);
-    k_bicg_s<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->dctl, s, r, v, S->red, outer_level);
+    spmv_on<V>(S, A, p, e2, cs, pdl);
+    launch_k(pdl, k_bicg_s<V>, S->grid_vec, kVecBlock, cs, n, st, (const Ctl *)S->dctl, s, r, v, S->red,
+             outer_level);
     EpiOmega<V> e4;
     e4.st = st; e4.t = t; e4.s = s;
-    spmv_on<V>(S, A, s, e4, cs);
-    k_bicg_xr<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->dctl, x, r, rh, p, s, t, total, S->red, h,
-                                                     outer_level);
+    spmv_on<V>(S, A, s, e4, cs, pdl);
+    launch_k(pdl, k_bicg_xr<V>, S->grid_vec, kVecBlock, cs, n, st, (const Ctl *)S->dctl, x, r, rh, p, s, t,
+             (const int *)total, S->red, h, outer_level);
 }
 
 // FP64-mode graph: start -> WHILE{F1..F5} -> true residual, copy-out, info
@@ -584,23 +604,33 @@ static hz_status build_fp64_graph(Solver *S, const hz_mat *A, cudaGraph_t g) {
     V *x = (V *)S->x, *r = (V *)S->r, *rh = (V *)S->rh, *p = (V *)S->p, *v = (V *)S->v, *s = (V *)S->s,
       *t = (V *)S->t;
     StateOf<V> *st = (StateOf<V> *)S->st;
-    cudaGraphConditionalHandle h;
-    HZ_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    // HZ_PROFILE_UNROLL=k (environment) builds a plain graph with k copies of
+    // the iteration and no conditional node, for profilers that do not
+    // descend into conditional bodies; the kernels are the same (once the
+    // solve is done, the remaining copies exit at their first instruction)
+    const char *unroll_env = getenv("HZ_PROFILE_UNROLL");
+    const int unroll = unroll_env ? atoi(unroll_env) : 0;
+    cudaGraphConditionalHandle h = 0;
+    if (unroll <= 0) HZ_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, mode));
     cudaMemcpyAsync(S->dctl, S->hctl, sizeof(Ctl), cudaMemcpyHostToDevice, cs);
     k_init_x<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->dctl, x);
     EpiInit<V> ei;
     ei.st = st; ei.info = S->dinfo; ei.ctl = S->dctl; ei.r = r; ei.rh = rh; ei.p = p; ei.v = v; ei.h = h;
     spmv_on<V>(S, A, x, ei, cs);
-    HZ_TRY(capture_leaves(cs, &leaves));
-    HZ_CUDA(cudaStreamEndCapture(cs, &g));
-    cudaGraphNode_t wn;
-    cudaGraph_t body;
-    HZ_TRY(add_while(g, leaves, h, &wn, &body));
-    HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
-    launch_iteration<V>(S, A, st, x, r, rh, p, v, s, t, nullptr, h, 1, cs);
-    HZ_CUDA(cudaStreamEndCapture(cs, &body));
-    HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, &wn, nullptr, 1, mode));
+    if (unroll > 0) {
+        for (int k = 0; k < unroll; ++k) launch_iteration<V>(S, A, st, x, r, rh, p, v, s, t, nullptr, 0, 1, cs);
+    } else {
+        HZ_TRY(capture_leaves(cs, &leaves));
+        HZ_CUDA(cudaStreamEndCapture(cs, &g));
+        cudaGraphNode_t wn;
+        cudaGraph_t body;
+        HZ_TRY(add_while(g, leaves, h, &wn, &body));
+        HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
+        launch_iteration<V>(S, A, st, x, r, rh, p, v, s, t, nullptr, h, 1, cs);
+        HZ_CUDA(cudaStreamEndCapture(cs, &body));
+        HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, &wn, nullptr, 1, mode));
+    }
     EpiTrue<V> et;
     et.st = st; et.info = S->dinfo; et.ctl = S->dctl;
     spmv_on<V>(S, A, x, et, cs);
@@ -657,7 +687,7 @@ static hz_status build_graph(Solver *S, const hz_mat *A) {
     cudaGraph_t g;
     HZ_CUDA(cudaGraphCreate(&g, 0));
     S->graph = g;
-    const bool ff = S->kind == HZ_SPMV_FF || S->kind == HZ_SPMV_SELL_FF;
+    const bool ff = S->kind == HZ_SPMV_FF || S->kind == HZ_SPMV_SELL_FF || S->kind == HZ_SPMV_FF_FLAT;
     if (S->mode == HZ_MODE_FP64)
         HZ_TRY(ff ? build_fp64_graph<float4>(S, A, g) : build_fp64_graph<double2>(S, A, g));
     else
@@ -682,6 +712,13 @@ static hz_status get_solver(hz_mat *A, uint32_t mode, cudaStream_t s, Solver **o
         S->kind = A->spmv_kind;
         S->group = A->group;
         S->grid_spmv = spmv_grid(A, S->kind, S->group);
+        const bool sell = S->kind == HZ_SPMV_SELL || S->kind == HZ_SPMV_SELL_FF;
+        S->grid_spmv_cv = spmv_grid(A, sell ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR, S->group);
+        // HZ_PDL=1 (environment) captures F2..F5 as programmatic dependent
+        // launches; measured slower on the C2 solve (185 vs 175 us per
+        // iteration), so plain launches are the default
+        const char *pdl_env = getenv("HZ_PDL");
+        S->pdl = pdl_env && atoi(pdl_env) != 0;
         S->grid_vec = stream_grid(d, (A->n + kVecUnroll - 1) / kVecUnroll, kVecBlock, 8);
         hz_status st = solver_alloc(S);
         if (st == HZ_OK) st = build_graph(S, A);

@@ -176,6 +176,34 @@ __device__ __forceinline__ void ff_mac(float &s, float &c, float ah, float al, f
 }
 
 // ---------------------------------------------------------------------------
+// programmatic dependent launch (PTX griddepcontrol).  A kernel launched with
+// the programmatic-serialization attribute may start while its predecessor
+// is still draining; pdl_wait() blocks until the predecessor grid has
+// completed and its memory is visible, so every kernel calls it before its
+// first read of data another kernel produced.  pdl_release() lets the next
+// kernel in the stream begin launching.  Both are no-ops without the
+// attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// host: launch `k` with the programmatic-serialization attribute set (the
+// launch may overlap the tail of the previous kernel on the stream)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, ((KArgs)args)...);
+}
+
+// ---------------------------------------------------------------------------
 // deterministic single-pass grid reduction.
 //
 // Every block reduces its NV per-thread values (warp shuffles, then shared
@@ -290,6 +318,9 @@ struct hz_mat {
     // handle's x scratch for hz_zspmv on that path
     float4 *val_ff = nullptr;
     float4 *x_ff = nullptr;
+    // row blocks of the block-flat double-float kernel (complete rows)
+    int32_t nfblk = 0;
+    int32_t *fblk = nullptr;
     // diagonal positions (for set_diag), built on demand
     int32_t *diag_pos = nullptr;
     // solver state (one per mode), created on first solve

@@ -51,6 +51,7 @@ template <>
 MatView<double2> mat_view<double2>(const hz_mat *A) {
     MatView<double2> v{};
     v.n = A->n; v.rowptr = A->rowptr; v.col = A->col; v.val = A->val; v.vff = A->val_ff; v.svff = A->sell_vff;
+    v.nfblk = A->nfblk; v.fblk = A->fblk;
     v.nchunks = A->sell_nchunks; v.chunk_off = A->sell_chunk_off; v.chunk_w = A->sell_chunk_w;
     v.perm = A->sell_perm; v.scol = A->sell_col; v.sval = A->sell_val;
     return v;
@@ -68,6 +69,18 @@ MatView<float2> mat_view<float2>(const hz_mat *A) {
 int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap) {
     DevInfo d;
     if (dev_info(&d) != HZ_OK) return 1;
+    if (kind == HZ_SPMV_FF_FLAT) {
+        // persistent: exactly the CTAs that fit at once (blocks are taken
+        // grid-stride, so CTAs beyond one wave would only add a tail)
+        static int occ = 0;
+        if (occ == 0) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_ffb<EpiStore<double2>>, kFlatThreads, 0) !=
+                    cudaSuccess || occ < 1)
+                occ = 1;
+        }
+        int64_t g = std::min<int64_t>(A->nfblk, (int64_t)d.num_sms * occ);
+        return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
+    }
     const bool sell = kind == HZ_SPMV_SELL || kind == HZ_SPMV_SELL_FF;
     int64_t threads = sell ? (int64_t)A->sell_nchunks * 32 : (int64_t)A->n * group;
     return stream_grid(d, threads, kSpmvBlock, blocks_per_sm_cap);
@@ -186,6 +199,7 @@ static hz_status autotune(hz_mat *A, cudaStream_t s) {
     if (A->val_ff)
         for (int w : {2, 4, 8, 16, 32}) cand.push_back({HZ_SPMV_FF, w});
     if (A->sell_vff) cand.push_back({HZ_SPMV_SELL_FF, 0});
+    if (A->fblk) cand.push_back({HZ_SPMV_FF_FLAT, 0});
     float best = 1e30f;
     MatView<double2> V = mat_view<double2>(A);
     EpiStore<double2> epi{y};
@@ -195,8 +209,8 @@ static hz_status autotune(hz_mat *A, cudaStream_t s) {
         float tms[5];
         for (int rep = -1; rep < 5; ++rep) {
             cudaEventRecord(e0, s);
-            if (c.first == HZ_SPMV_FF || c.first == HZ_SPMV_SELL_FF)
-                launch_spmv_ff(c.first == HZ_SPMV_SELL_FF, c.second, V, A->x_ff, epi, RedScratch{}, grid, s);
+            if (c.first == HZ_SPMV_FF || c.first == HZ_SPMV_SELL_FF || c.first == HZ_SPMV_FF_FLAT)
+                launch_spmv_ff(c.first, c.second, V, A->x_ff, epi, RedScratch{}, grid, s);
             else launch_spmv<double2>(c.first, c.second, V, x, epi, RedScratch{}, grid, s);
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess) { st = HZ_ERR_CUDA; break; }
@@ -321,14 +335,28 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
             return fail(HZ_ERR_ALLOC);
         }
         if (n) cudaMemsetAsync(A->x_ff, 0, sizeof(float4) * n, s);
-        A->spmv_kind = HZ_SPMV_FF;
         if (A->sell_slots) {
             if (cudaMalloc(&A->sell_vff, sizeof(float4) * A->sell_slots) != cudaSuccess) {
                 set_error("hz_csr_create: allocation failed");
                 return fail(HZ_ERR_ALLOC);
             }
-            A->spmv_kind = HZ_SPMV_SELL_FF;
         }
+        // row blocks for the block-flat kernel: greedy runs of complete rows
+        // with at most kFlatCap entries; a longer row is a block of its own
+        std::vector<int> fb{0};
+        for (int r = 0; r < n;) {
+            int r1 = r + 1;
+            while (r1 < n && rp[r1 + 1] - rp[r] <= kFlatCap) ++r1;
+            fb.push_back(r1);
+            r = r1;
+        }
+        A->nfblk = (int)fb.size() - 1;
+        if (cudaMalloc(&A->fblk, sizeof(int) * fb.size()) != cudaSuccess ||
+            cudaMemcpy(A->fblk, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            set_error("hz_csr_create: allocation failed");
+            return fail(HZ_ERR_ALLOC);
+        }
+        A->spmv_kind = HZ_SPMV_FF_FLAT;
     }
     if ((st = refresh(A, s)) != HZ_OK) return fail(st);
     if (flags & HZ_FLAG_AUTOTUNE) {
@@ -355,6 +383,7 @@ extern "C" HZ_API hz_status hz_mat_destroy(hz_mat *A) {
     cudaFree(A->sell_src);
     cudaFree(A->sell_val);
     cudaFree(A->sell_vff);
+    cudaFree(A->fblk);
     cudaFree(A->sell_val32);
     cudaFree(A->val32);
     cudaFree(A->val_ff);
@@ -391,9 +420,9 @@ extern "C" HZ_API hz_status hz_zspmv(const hz_mat *A, const hz_z *d_x, hz_z *d_y
     HZ_CHECK((const void *)d_x != (const void *)d_y, "hz_zspmv: x and y must not alias");
     const int grid = spmv_grid(A, A->spmv_kind, A->group);
     EpiStore<double2> epi{(double2 *)d_y};
-    if (A->spmv_kind == HZ_SPMV_FF || A->spmv_kind == HZ_SPMV_SELL_FF) {
+    if (A->spmv_kind == HZ_SPMV_FF || A->spmv_kind == HZ_SPMV_SELL_FF || A->spmv_kind == HZ_SPMV_FF_FLAT) {
         HZ_CUDA(split_ff_vec(A->n, (const double2 *)d_x, A->x_ff, (cudaStream_t)stream));
-        HZ_CUDA(launch_spmv_ff(A->spmv_kind == HZ_SPMV_SELL_FF, A->group, mat_view<double2>(A), A->x_ff, epi,
+        HZ_CUDA(launch_spmv_ff(A->spmv_kind, A->group, mat_view<double2>(A), A->x_ff, epi,
                                RedScratch{}, grid, (cudaStream_t)stream));
         return HZ_OK;
     }
@@ -422,6 +451,11 @@ extern "C" HZ_API hz_status hz_mat_set_spmv(hz_mat *A, int32_t kind, int32_t gro
     if (kind == HZ_SPMV_SELL) {
         HZ_CHECK(A->sell_val != nullptr, "hz_mat_set_spmv: the handle has no SELL copy (HZ_FLAG_SELL)");
         A->spmv_kind = HZ_SPMV_SELL;
+        return HZ_OK;
+    }
+    if (kind == HZ_SPMV_FF_FLAT) {
+        HZ_CHECK(A->fblk != nullptr, "hz_mat_set_spmv: the handle has no double-float copy (HZ_FLAG_FF)");
+        A->spmv_kind = HZ_SPMV_FF_FLAT;
         return HZ_OK;
     }
     if (kind == HZ_SPMV_SELL_FF) {

@@ -39,6 +39,17 @@ constexpr int kFFUnroll = HZ_FF_UNROLL;
 #endif
 constexpr bool kFFContig = HZ_FF_CONTIG != 0;        // contiguous row range per block
 constexpr bool kFFTranspose = HZ_FF_TRANSPOSE != 0;  // lane-transposed row outputs
+// block-flat double-float kernel: one warp per row block, kFlatU entries per
+// lane per pass, so a row block holds up to kFlatCap = 32 * kFlatU entries
+#ifndef HZ_FLAT_THREADS
+#define HZ_FLAT_THREADS 128
+#endif
+#ifndef HZ_FLAT_U
+#define HZ_FLAT_U 8
+#endif
+constexpr int kFlatThreads = HZ_FLAT_THREADS;   // warps per CTA = kFlatThreads / 32
+constexpr int kFlatU = HZ_FLAT_U;
+constexpr int kFlatCap = 32 * kFlatU;           // entries per warp row block
 
 template <class T>
 struct MatView {
@@ -56,6 +67,10 @@ struct MatView {
     // double-float split values (used by the ff kernels), CSR and SELL order
     const float4 *vff;
     const float4 *svff;
+    // row blocks of the block-flat double-float kernel: block b holds the
+    // complete rows [fblk[b], fblk[b+1]) (<= kFlatCap entries, or one row)
+    int nfblk;
+    const int *fblk;
 };
 
 // Epilogue interface (every fused SpMV epilogue provides):
@@ -240,6 +255,77 @@ __device__ __forceinline__ void sell_rows_ff(const MatView<double2> &A, const fl
     }
 }
 
+// Block-flat double-float core, one warp per row block (complete rows,
+// <= kFlatCap = 32*kFlatU entries, or a single longer row).  Two phases:
+//  1. lane l takes entries kb + l + 32*u (coalesced loads, every lane busy),
+//     forms each entry's complex product a*x in double-float and stores it
+//     to the warp's slab of shared memory;
+//  2. lane j sums the products of row r0 + j (+32, ...) from the slab and
+//     hands the row to the epilogue.
+// Row boundaries never enter the streaming phase, which runs like a flat
+// gather-stream; warps need only __syncwarp.  A single row longer than
+// kFlatCap is processed in kFlatCap-entry passes, lane 0 carrying its sum.
+template <class Epi, int NV>
+__device__ __forceinline__ void flat_rows_ff(const MatView<double2> &A, const float4 *__restrict__ x,
+                                             const Epi &epi, typename Epi::Acc (&acc)[NV], float4 *slab) {
+    const uint64_t pol = pol_evict_first();
+    const int lane = threadIdx.x & 31;
+    float4 *prod = slab + (threadIdx.x >> 5) * kFlatCap;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < A.nfblk; b += nwarps) {
+        const int r0 = __ldg(A.fblk + b), r1 = __ldg(A.fblk + b + 1);
+        const int kb = __ldg(A.rowptr + r0), ke = __ldg(A.rowptr + r1);
+        const bool long_row = r1 - r0 == 1 && ke - kb > kFlatCap;
+        float lsr = 0.f, lcr = 0.f, lsi = 0.f, lci = 0.f;   // long-row carry (lane 0)
+        for (int kc = kb;; kc += kFlatCap) {
+            const int kend = min(ke, kc + kFlatCap);
+            // phase 1: products
+            int c[kFlatU];
+            float4 a[kFlatU], v[kFlatU];
+#pragma unroll
+            for (int u = 0; u < kFlatU; ++u) {
+                const int k = kc + lane + 32 * u;
+                c[u] = k < kend ? ld_stream(A.col + k, pol) : -1;
+                a[u] = k < kend ? ld_stream(A.vff + k, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kFlatU; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < kFlatU; ++u) {
+                if (c[u] < 0) continue;
+                float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+                ff_mac(sr, cr, a[u].x, a[u].y, v[u].x, v[u].y);
+                ff_mac(sr, cr, -a[u].z, -a[u].w, v[u].z, v[u].w);
+                ff_mac(si, ci, a[u].x, a[u].y, v[u].z, v[u].w);
+                ff_mac(si, ci, a[u].z, a[u].w, v[u].x, v[u].y);
+                prod[lane + 32 * u] = make_float4(sr, cr, si, ci);
+            }
+            __syncwarp();
+            // phase 2: row sums (rows clipped to this pass's entries)
+            for (int row = r0 + lane; row < r1; row += 32) {
+                const int beg = max(__ldg(A.rowptr + row), kc), end = min(__ldg(A.rowptr + row + 1), kend);
+                float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+                for (int k = beg; k < end; ++k) {
+                    const float4 q = prod[k - kc];
+                    ff_acc(sr, cr, q.x);
+                    cr = __fadd_rn(cr, q.y);
+                    ff_acc(si, ci, q.z);
+                    ci = __fadd_rn(ci, q.w);
+                }
+                if (long_row) {
+                    ff_acc(lsr, lcr, sr); lcr = __fadd_rn(lcr, cr);
+                    ff_acc(lsi, lci, si); lci = __fadd_rn(lci, ci);
+                    if (kend == ke) ff_row_out<Epi, NV>(epi, row, lsr, lcr, lsi, lci, acc);
+                } else {
+                    ff_row_out<Epi, NV>(epi, row, sr, cr, si, ci, acc);
+                }
+            }
+            __syncwarp();
+            if (kend >= ke) break;
+        }
+    }
+}
+
 // per-thread accumulators -> one grid total -> epi.finish (last block)
 template <class Epi, int NV>
 __device__ __forceinline__ void spmv_reduce(const Epi &epi, typename Epi::Acc (&acc)[NV], RedScratch red) {
@@ -256,6 +342,8 @@ template <int W, class T, class Epi>
 __global__ void __launch_bounds__(kSpmvBlock) k_spmv(MatView<T> A, const T *__restrict__ x, Epi epi,
                                                      RedScratch red) {
     constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
+    pdl_wait();
+    pdl_release();
     if (epi.skip()) return;
     typename Epi::Acc acc[NV];
 #pragma unroll
@@ -270,12 +358,30 @@ template <int W, class Epi>
 __global__ void __launch_bounds__(kSpmvBlock, HZ_FF_MIN_BLOCKS) k_spmv_ff(MatView<double2> A, const float4 *__restrict__ x, Epi epi,
                                                         RedScratch red) {
     constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
+    pdl_wait();
+    pdl_release();
     if (epi.skip()) return;
     typename Epi::Acc acc[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
     if constexpr (W == 0) sell_rows_ff<Epi, NV>(A, x, epi, acc);
     else csr_rows_ff<W, Epi, NV>(A, x, epi, acc);
+    if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
+}
+
+// the block-flat double-float kernel (kFlatThreads threads, row blocks)
+template <class Epi>
+__global__ void __launch_bounds__(kFlatThreads) k_spmv_ffb(MatView<double2> A, const float4 *__restrict__ x, Epi epi,
+                                                           RedScratch red) {
+    __shared__ float4 prod[(kFlatThreads / 32) * kFlatCap];   // one slab per warp
+    constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
+    pdl_wait();
+    pdl_release();
+    if (epi.skip()) return;
+    typename Epi::Acc acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
+    flat_rows_ff<Epi, NV>(A, x, epi, acc, prod);
     if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
 }
 
@@ -298,38 +404,51 @@ struct EpiStore {
     template <int N> __device__ void finish(R (&)[N]) const {}
 };
 
+// plain or programmatic-dependent launch of kernel k
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    if (pdl) return launch_pdl(k, grid, block, s, args...);
+    k<<<grid, block, 0, s>>>(((KArgs)args)...);
+    return cudaGetLastError();
+}
+
 // launch helper: picks the template instance for the handle's variant
 template <class T, class Epi>
 cudaError_t launch_spmv(int kind, int group, const MatView<T> &A, const T *x, const Epi &epi,
-                        RedScratch red, int grid, cudaStream_t s) {
+                        RedScratch red, int grid, cudaStream_t s, bool pdl = false) {
     if (kind == HZ_SPMV_SELL) {
-        k_spmv<0, T, Epi><<<grid, kSpmvBlock, 0, s>>>(A, x, epi, red);
+        launch_k(pdl, k_spmv<0, T, Epi>, grid, kSpmvBlock, s, A, x, epi, red);
     } else {
         switch (group) {
-            case 2: k_spmv<2, T, Epi><<<grid, kSpmvBlock, 0, s>>>(A, x, epi, red); break;
-            case 4: k_spmv<4, T, Epi><<<grid, kSpmvBlock, 0, s>>>(A, x, epi, red); break;
-            case 8: k_spmv<8, T, Epi><<<grid, kSpmvBlock, 0, s>>>(A, x, epi, red); break;
-            case 16: k_spmv<16, T, Epi><<<grid, kSpmvBlock, 0, s>>>(A, x, epi, red); break;
-            default: k_spmv<32, T, Epi><<<grid, kSpmvBlock, 0, s>>>(A, x, epi, red); break;
+            case 2: launch_k(pdl, k_spmv<2, T, Epi>, grid, kSpmvBlock, s, A, x, epi, red); break;
+            case 4: launch_k(pdl, k_spmv<4, T, Epi>, grid, kSpmvBlock, s, A, x, epi, red); break;
+            case 8: launch_k(pdl, k_spmv<8, T, Epi>, grid, kSpmvBlock, s, A, x, epi, red); break;
+            case 16: launch_k(pdl, k_spmv<16, T, Epi>, grid, kSpmvBlock, s, A, x, epi, red); break;
+            default: launch_k(pdl, k_spmv<32, T, Epi>, grid, kSpmvBlock, s, A, x, epi, red); break;
         }
     }
     return cudaGetLastError();
 }
 
-// double-float kernels: SELL layout (sell != 0) or CSR-vector with `group` lanes
+// double-float kernels by handle kind: HZ_SPMV_FF_FLAT (row blocks),
+// HZ_SPMV_SELL_FF, or HZ_SPMV_FF (CSR-vector with `group` lanes per row)
 template <class Epi>
-cudaError_t launch_spmv_ff(int sell, int group, const MatView<double2> &A, const float4 *xff, const Epi &epi,
-                           RedScratch red, int grid, cudaStream_t s) {
-    if (sell) {
-        k_spmv_ff<0, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red);
+cudaError_t launch_spmv_ff(int kind, int group, const MatView<double2> &A, const float4 *xff, const Epi &epi,
+                           RedScratch red, int grid, cudaStream_t s, bool pdl = false) {
+    if (kind == HZ_SPMV_FF_FLAT) {
+        launch_k(pdl, k_spmv_ffb<Epi>, grid, kFlatThreads, s, A, xff, epi, red);
+        return cudaGetLastError();
+    }
+    if (kind == HZ_SPMV_SELL_FF) {
+        launch_k(pdl, k_spmv_ff<0, Epi>, grid, kSpmvBlock, s, A, xff, epi, red);
         return cudaGetLastError();
     }
     switch (group) {
-        case 2: k_spmv_ff<2, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red); break;
-        case 4: k_spmv_ff<4, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red); break;
-        case 8: k_spmv_ff<8, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red); break;
-        case 16: k_spmv_ff<16, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red); break;
-        default: k_spmv_ff<32, Epi><<<grid, kSpmvBlock, 0, s>>>(A, xff, epi, red); break;
+        case 2: launch_k(pdl, k_spmv_ff<2, Epi>, grid, kSpmvBlock, s, A, xff, epi, red); break;
+        case 4: launch_k(pdl, k_spmv_ff<4, Epi>, grid, kSpmvBlock, s, A, xff, epi, red); break;
+        case 8: launch_k(pdl, k_spmv_ff<8, Epi>, grid, kSpmvBlock, s, A, xff, epi, red); break;
+        case 16: launch_k(pdl, k_spmv_ff<16, Epi>, grid, kSpmvBlock, s, A, xff, epi, red); break;
+        default: launch_k(pdl, k_spmv_ff<32, Epi>, grid, kSpmvBlock, s, A, xff, epi, red); break;
     }
     return cudaGetLastError();
 }

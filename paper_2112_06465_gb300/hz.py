@@ -80,9 +80,10 @@ class Matrix:
         return {f: getattr(p, f) for f, _ in p._fields_}
 
     def set_spmv(self, kind="csr", group=4):
-        """Force the SpMV variant: ("csr" | "ff", lanes per row) or ("sell" | "sellff", ignored)."""
-        k = {"sell": _lib.HZ_SPMV_SELL, "ff": _lib.HZ_SPMV_FF,
-             "sellff": _lib.HZ_SPMV_SELL_FF}.get(kind, _lib.HZ_SPMV_CSR_VECTOR)
+        """Force the SpMV variant: ("csr" | "ff", lanes per row) or ("sell" | "sellff" |
+        "ffflat", ignored)."""
+        k = {"sell": _lib.HZ_SPMV_SELL, "ff": _lib.HZ_SPMV_FF, "sellff": _lib.HZ_SPMV_SELL_FF,
+             "ffflat": _lib.HZ_SPMV_FF_FLAT}.get(kind, _lib.HZ_SPMV_CSR_VECTOR)
         check(_L.hz_mat_set_spmv(self.handle, k, int(group)))
 
     def refresh_values(self):

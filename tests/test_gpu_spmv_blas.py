@@ -42,7 +42,7 @@ def check_spmv(hz, oracle, A, x, variants):
 
 
 ALL_VARIANTS = [("csr", 2), ("csr", 4), ("csr", 8), ("csr", 16), ("csr", 32), ("sell", 0),
-                ("ff", 2), ("ff", 4), ("ff", 8), ("ff", 16), ("ff", 32), ("sellff", 0)]
+                ("ff", 2), ("ff", 4), ("ff", 8), ("ff", 16), ("ff", 32), ("sellff", 0), ("ffflat", 0)]
 
 
 def test_spmv_worked_example_exact(hz, oracle):
@@ -73,7 +73,8 @@ def test_spmv_one_based(hz):
 
 
 @pytest.mark.parametrize("seed,n,maxrow,longs", [(1, 1, 3, ()), (2, 37, 9, ()), (3, 1000, 40, (300, 513)),
-                                                  (4, 4099, 16, (700,)), (5, 257, 70, ())])
+                                                  (4, 4099, 16, (700,)), (5, 257, 70, ()),
+                                                  (6, 3000, 12, (2500, 1300, 1024, 1025))])
 def test_spmv_random_ragged(hz, oracle, seed, n, maxrow, longs):
     A = K.random_csr(n, seed, max_row=maxrow, long_rows=longs)
     x = K.vectors(n, seed + 100)[0]

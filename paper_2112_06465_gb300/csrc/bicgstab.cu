@@ -33,7 +33,10 @@ namespace hz {
 hz_status ensure_c64(hz_mat *A, cudaStream_t s);
 
 constexpr int kVecBlock = 256;
-constexpr int kVecUnroll = 4;
+#ifndef HZ_VEC_UNROLL
+#define HZ_VEC_UNROLL 8
+#endif
+constexpr int kVecUnroll = HZ_VEC_UNROLL;   // elements per thread per tile of the vector kernels
 
 // host-written controls of one solve (uploaded by the graph itself)
 struct Ctl {
@@ -85,6 +88,29 @@ __device__ __forceinline__ void vec_tiles(int n, F f) {
     }
 }
 
+// Tile walker that issues every load of a tile before the first compute:
+// load(i) returns the element's inputs (indices are clamped to n-1, so the
+// loads need no branch), comp(i, in) computes and stores for i < n.
+template <class Ld, class Cp>
+__device__ __forceinline__ void vec_tiles_staged(int n, Ld load, Cp comp) {
+    using In = decltype(load(0));
+    const int tile = kVecUnroll * blockDim.x;
+    for (int base = blockIdx.x * tile; base < n; base += gridDim.x * tile) {
+        In in[kVecUnroll];
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) in[u] = load(min(base + u * (int)blockDim.x + (int)threadIdx.x, n - 1));
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int i = base + u * blockDim.x + threadIdx.x;
+            if (i < n) comp(i, in[u]);
+        }
+    }
+}
+
+template <class V> struct In2 { V a, b; };
+template <class V> struct In3 { V a, b, c; };
+template <class V> struct In5 { V a, b, c, d, e; };
+
 __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
 
 // loop condition of the enclosing WHILE node; handle 0 = the graph has no
@@ -129,7 +155,9 @@ __global__ void __launch_bounds__(kVecBlock) k_bicg_p(int n, StateOf<V> *st, V *
         if (total_iters) *total_iters += 1;
         if (cis_zero(st->rho)) { st->status = HZ_BREAKDOWN; st->done = 1; }
     }
-    vec_tiles(n, [&](int i) { p[i] = A::axpy(r[i], beta, A::axmy(p[i], omega, v[i])); });
+    vec_tiles_staged(
+        n, [&](int i) { return In3<V>{r[i], p[i], v[i]}; },
+        [&](int i, const In3<V> &q) { p[i] = A::axpy(q.a, beta, A::axmy(q.b, omega, q.c)); });
 }
 
 // F2 epilogue: v = A p, sigma = <rh, v>, alpha = rho / sigma
@@ -165,11 +193,13 @@ __global__ void __launch_bounds__(kVecBlock) k_bicg_s(int n, StateOf<V> *st, con
     const typename A::S alpha = A::scal(st->alpha);
     typename A::Acc acc[1];
     A::acc_zero(acc[0]);
-    vec_tiles(n, [&](int i) {
-        const V o = A::axmy(r[i], alpha, v[i]);
-        s[i] = o;
-        A::nrm2(acc[0], o);
-    });
+    vec_tiles_staged(
+        n, [&](int i) { return In2<V>{r[i], v[i]}; },
+        [&](int i, const In2<V> &q) {
+            const V o = A::axmy(q.a, alpha, q.b);
+            s[i] = o;
+            A::nrm2(acc[0], o);
+        });
     typename A::R tot[1];
     if (vec_reduce<V, 1>(acc, red, tot) && threadIdx.x == 0) {
         const double ss = (double)tot[0];
@@ -238,14 +268,15 @@ __global__ void __launch_bounds__(kVecBlock) k_bicg_xr(int n, StateOf<V> *st, co
     typename A::Acc acc[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) A::acc_zero(acc[j]);
-    vec_tiles(n, [&](int i) {
-        const V si = s[i];
-        x[i] = A::axpy(A::axpy(x[i], alpha, p[i]), omega, si);
-        const V ri = A::axmy(si, omega, t[i]);
-        r[i] = ri;
-        A::dotc(acc[0], acc[1], rh[i], ri);
-        A::nrm2(acc[2], ri);
-    });
+    vec_tiles_staged(
+        n, [&](int i) { return In5<V>{s[i], x[i], p[i], t[i], rh[i]}; },
+        [&](int i, const In5<V> &q) {
+            x[i] = A::axpy(A::axpy(q.b, alpha, q.c), omega, q.a);
+            const V ri = A::axmy(q.a, omega, q.d);
+            r[i] = ri;
+            A::dotc(acc[0], acc[1], q.e, ri);
+            A::nrm2(acc[2], ri);
+        });
     typename A::R tot[3];
     if (vec_reduce<V, 3>(acc, red, tot) && threadIdx.x == 0) {
         const double rel = sqrt((double)tot[2]) / st->nb;

@@ -213,7 +213,8 @@ def run_reference(args):
 DTYPES = {"fp64": "f64", "ff": "f32x2 (double-float complex128: hi+lo binary32 pairs)"}
 SPMV_KINDS = {0: "binary64 CSR-vector (k_spmv)", 1: "binary64 SELL-C-sigma (k_spmv<0>)",
               2: "double-float CSR-vector (k_spmv_ff)", 3: "double-float SELL-C-sigma (k_spmv_ff<0>)",
-              4: "double-float block-flat (k_spmv_ffb)"}
+              4: "double-float block-flat (k_spmv_ffb)",
+              5: "double-float block-flat, bulk-copy staged (k_spmv_fft)"}
 
 
 def run_spmv_only(args):
@@ -222,14 +223,17 @@ def run_spmv_only(args):
     import paper_2112_06465_gb300 as hz
     A, _ = build_workload()
     M = hz.Matrix.from_csr(A, ff=args.arith == "ff")
-    if args.arith == "fp64":
-        M.set_spmv("csr", args.group)    # otherwise the handle's default (block-flat double-float)
+    if args.spmv:
+        M.set_spmv(args.spmv, args.group)
+    elif args.arith == "fp64":
+        M.set_spmv("csr", args.group)
     x = torch.randn(A.n, dtype=torch.complex128, device="cuda")
     y = torch.empty_like(x)
     for _ in range(3):
         hz.zspmv(M, x, y)
     torch.cuda.synchronize()
-    print(json.dumps({"spmv_only": True, "arith": args.arith, "group": args.group, "n": A.n, "nnz": A.nnz}))
+    print(json.dumps({"spmv_only": True, "arith": args.arith, "kind": M.props()["spmv_kind"], "group": args.group,
+                      "n": A.n, "nnz": A.nnz}))
 
 
 def workload_config(A, maxit, arith="fp64"):
@@ -256,7 +260,9 @@ def main():
     ap.add_argument("--spmv-only", action="store_true",
                     help="profiling aid: build C2, run three SpMV launches of the chosen "
                          "arithmetic (--arith, --group) and exit without timing")
-    ap.add_argument("--group", type=int, default=4, help="lanes per row for --spmv-only")
+    ap.add_argument("--group", type=int, default=4, help="lanes per row of the CSR-vector kinds")
+    ap.add_argument("--spmv", default=None, choices=["csr", "sell", "ff", "sellff", "ffflat", "fftma"],
+                    help="force an SpMV variant (default: the handle's own choice)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -283,6 +289,8 @@ def main():
     vl = torch.as_tensor(A.val).to(dev)
     bd = torch.as_tensor(b).to(dev)
     M = hz.Matrix(rp, cl, vl, ff=args.arith == "ff")
+    if args.spmv:
+        M.set_spmv(args.spmv, args.group)
     xd = torch.zeros_like(bd)
 
     def barrier():
@@ -329,6 +337,8 @@ def main():
         d_vl = h_vl.to(dev, non_blocking=True)
         d_b = h_b.to(dev, non_blocking=True)
         M2 = hz.Matrix(d_rp, d_cl, d_vl, ff=args.arith == "ff")
+        if args.spmv:
+            M2.set_spmv(args.spmv, args.group)
         x2, inf2 = hz.zsolve(M2, d_b, tol=1e-10, maxit=args.maxit)
         h_x.copy_(x2, non_blocking=True)
         torch.cuda.synchronize()

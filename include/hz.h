@@ -86,9 +86,12 @@ enum {
                                 <= about (4 + row length / group) * 2^-48 * sum_j |a_ij| |x_j| */
     HZ_SPMV_SELL_FF = 3,     /* SELL-C-sigma layout in double-float arithmetic (one lane per row;
                                 error bound as HZ_SPMV_FF with group 1) */
-    HZ_SPMV_FF_FLAT = 4      /* double-float, row blocks streamed flat: each entry's product is
+    HZ_SPMV_FF_FLAT = 4,     /* double-float, row blocks streamed flat: each entry's product is
                                 formed with coalesced loads and all lanes busy, then whole rows
                                 are summed from shared memory (the default with HZ_FLAG_FF) */
+    HZ_SPMV_FF_TMA = 5       /* HZ_SPMV_FF_FLAT with the values and columns moved into shared
+                                memory by bulk asynchronous copies, one row block ahead of the
+                                arithmetic */
 };
 
 typedef struct {
@@ -130,11 +133,23 @@ HZ_API hz_status hz_mat_destroy(hz_mat *A);
 HZ_API hz_status hz_mat_query(const hz_mat *A, hz_mat_props *props);
 
 /*
+ * Health of the asynchronous work on a handle (no counterpart in the paper).
+ * The HZ_SPMV_FF_TMA kernel waits on its bulk copies with a wall-time limit
+ * (1 s); if a wait ever expires, the kernel stops early, its output is
+ * incomplete, and it sets a sticky fault word in the handle.  This call
+ * synchronises `stream` and returns HZ_ERR_TIMEOUT if that word is set,
+ * HZ_OK otherwise.  A solve on the handle reports the same condition in its
+ * own status.
+ */
+HZ_API hz_status hz_mat_check(const hz_mat *A, void *stream);
+
+/*
  * Force the SpMV variant of a handle: kind HZ_SPMV_CSR_VECTOR or HZ_SPMV_FF
  * with group in {2, 4, 8, 16, 32} lanes per row (HZ_SPMV_FF needs a handle
  * created with HZ_FLAG_FF), or HZ_SPMV_SELL (the handle must have been
- * created with HZ_FLAG_SELL), or HZ_SPMV_SELL_FF (both flags; group is
- * ignored for the SELL kinds).  Overrides the histogram choice and the
+ * created with HZ_FLAG_SELL), or HZ_SPMV_SELL_FF (both flags), or
+ * HZ_SPMV_FF_FLAT / HZ_SPMV_FF_TMA (HZ_FLAG_FF); group is ignored for all
+ * but the CSR-vector kinds.  Overrides the histogram choice and the
  * autotuner; solver graphs built for the old variant are rebuilt on the
  * next solve.  Errors: HZ_ERR_ARG for an unknown variant.
  */
@@ -149,7 +164,8 @@ HZ_API hz_status hz_mat_refresh_values(hz_mat *A, void *stream);
 /*
  * y = A x (Section 6, CSR matrix-vector product), complex128.
  * d_x and d_y have n entries and must not overlap.  On the double-float
- * variants (HZ_SPMV_FF, HZ_SPMV_SELL_FF) the handle's own x scratch holds
+ * variants (HZ_SPMV_FF, HZ_SPMV_SELL_FF, HZ_SPMV_FF_FLAT, HZ_SPMV_FF_TMA)
+ * the handle's own x scratch holds
  * the split of d_x, so calls on one handle must not overlap in time
  * (different handles may).
  */

@@ -20,7 +20,7 @@ SOLVE_OUTCOMES = (HZ_OK, HZ_NOT_CONVERGED, HZ_BREAKDOWN, HZ_ERR_NAN)
 
 HZ_FLAG_VALIDATE, HZ_FLAG_SELL, HZ_FLAG_C64, HZ_FLAG_AUTOTUNE, HZ_FLAG_FF = 1, 2, 4, 8, 16
 HZ_MODE_FP64, HZ_MODE_MIXED = 0, 1
-HZ_SPMV_CSR_VECTOR, HZ_SPMV_SELL, HZ_SPMV_FF, HZ_SPMV_SELL_FF, HZ_SPMV_FF_FLAT = 0, 1, 2, 3, 4
+HZ_SPMV_CSR_VECTOR, HZ_SPMV_SELL, HZ_SPMV_FF, HZ_SPMV_SELL_FF, HZ_SPMV_FF_FLAT, HZ_SPMV_FF_TMA = 0, 1, 2, 3, 4, 5
 
 # every symbol include/hz.h declares
 EXPORTS = (
@@ -29,6 +29,7 @@ EXPORTS = (
     "hz_cspmv", "hz_zdotc", "hz_zdotu", "hz_dznrm2", "hz_zaxpy", "hz_zscal", "hz_zcopy",
     "hz_zconj", "hz_zsolve", "hz_zsolve_opts", "hz_zsolve_batched", "hz_outer_on_pattern",
     "hz_mat_set_diag", "hz_diag_grad", "hz_last_error", "hz_version", "hz_zdotc_noalloc",
+    "hz_mat_check",
 )
 
 
@@ -76,6 +77,7 @@ def load():
         "hz_csr_create": [C.POINTER(C.c_void_p), i32, i32, P, P, P, i32, u32, P],
         "hz_mat_destroy": [P],
         "hz_mat_query": [P, C.POINTER(hz_mat_props)],
+        "hz_mat_check": [P, P],
         "hz_mat_set_spmv": [P, i32, i32],
         "hz_mat_refresh_values": [P, P],
         "hz_zspmv": [P, P, P, P],

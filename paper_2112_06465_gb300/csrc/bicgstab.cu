@@ -382,10 +382,12 @@ struct EpiTrue : EpiBase<V> {
 };
 
 template <class V>
-__global__ void __launch_bounds__(kVecBlock) k_copy_out(int n, const Ctl *ctl, const Info *info,
-                                                        const V *__restrict__ xw) {
+__global__ void __launch_bounds__(kVecBlock) k_copy_out(int n, const Ctl *ctl, Info *info,
+                                                        const V *__restrict__ xw, const int *fault) {
     double2 *x = ctl->x;
     const bool zero = info->zero_x != 0;
+    // an expired bounded wait in an SpMV of this solve voids the result
+    if (fault && blockIdx.x == 0 && threadIdx.x == 0 && *(volatile const int *)fault) info->status = HZ_ERR_TIMEOUT;
     vec_tiles(n, [&](int i) { x[i] = zero ? make_double2(0.0, 0.0) : Ar<V>::to_c128(xw[i]); });
 }
 
@@ -665,7 +667,7 @@ static hz_status build_fp64_graph(Solver *S, const hz_mat *A, cudaGraph_t g) {
     EpiTrue<V> et;
     et.st = st; et.info = S->dinfo; et.ctl = S->dctl;
     spmv_on<V>(S, A, x, et, cs);
-    k_copy_out<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->dctl, S->dinfo, x);
+    k_copy_out<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->dctl, S->dinfo, x, A->fault);
     cudaMemcpyAsync(S->hinfo, S->dinfo, sizeof(Info), cudaMemcpyDeviceToHost, cs);
     HZ_CUDA(cudaStreamEndCapture(cs, &g));
     return HZ_OK;
@@ -708,7 +710,7 @@ static hz_status build_mixed_graph(Solver *S, const hz_mat *A, cudaGraph_t g) {
     k_mixed_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->ost, x, S->d32);
     HZ_CUDA(cudaStreamEndCapture(cs, &obody));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, &wo, nullptr, 1, mode));
-    k_copy_out<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->dctl, S->dinfo, x);
+    k_copy_out<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->dctl, S->dinfo, x, A->fault);
     cudaMemcpyAsync(S->hinfo, S->dinfo, sizeof(Info), cudaMemcpyDeviceToHost, cs);
     HZ_CUDA(cudaStreamEndCapture(cs, &g));
     return HZ_OK;
@@ -718,7 +720,7 @@ static hz_status build_graph(Solver *S, const hz_mat *A) {
     cudaGraph_t g;
     HZ_CUDA(cudaGraphCreate(&g, 0));
     S->graph = g;
-    const bool ff = S->kind == HZ_SPMV_FF || S->kind == HZ_SPMV_SELL_FF || S->kind == HZ_SPMV_FF_FLAT;
+    const bool ff = is_ff_kind(S->kind);
     if (S->mode == HZ_MODE_FP64)
         HZ_TRY(ff ? build_fp64_graph<float4>(S, A, g) : build_fp64_graph<double2>(S, A, g));
     else

@@ -175,6 +175,16 @@ __device__ __forceinline__ void ff_mac(float &s, float &c, float ah, float al, f
     c = __fadd_rn(c, e);
 }
 
+// (s, c) = (ah + al) * (xh + xl): ff_mac into a zero accumulator with the
+// exact steps 0 + p = p and 0 + e = e left out (the same values; only the
+// sign of a zero can differ)
+__device__ __forceinline__ void ff_mul(float &s, float &c, float ah, float al, float xh, float xl) {
+    s = __fmul_rn(ah, xh);
+    float e = __fmaf_rn(ah, xh, -s);
+    e = __fmaf_rn(ah, xl, e);
+    c = __fmaf_rn(al, xh, e);
+}
+
 // ---------------------------------------------------------------------------
 // programmatic dependent launch (PTX griddepcontrol).  A kernel launched with
 // the programmatic-serialization attribute may start while its predecessor
@@ -202,6 +212,59 @@ cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t 
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k, ((KArgs)args)...);
 }
+
+// ---------------------------------------------------------------------------
+// bulk asynchronous copies (the TMA unit's untiled cp.async.bulk) into
+// shared memory, completed on an mbarrier by transaction count.  Source and
+// destination must be 16-byte aligned and the size a multiple of 16 bytes.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// make initialised barriers visible to the async proxy
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// arrive once and add `bytes` to the transactions the current phase waits for
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for phase `parity` of the barrier to complete, giving up after
+// about `limit_ns` of wall time; returns false on expiry
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
+}
+// order this thread's earlier shared-memory accesses before later
+// async-proxy (bulk copy) writes to the same locations
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // deterministic single-pass grid reduction.
@@ -285,6 +348,11 @@ int stream_grid(const DevInfo &d, int64_t work_items, int block, int blocks_per_
 }  // namespace hz
 
 // ---------------------------------------------------------------------------
+// SpMV kinds that run in double-float arithmetic on the split x
+inline bool is_ff_kind(int k) {
+    return k == HZ_SPMV_FF || k == HZ_SPMV_SELL_FF || k == HZ_SPMV_FF_FLAT || k == HZ_SPMV_FF_TMA;
+}
+
 // matrix handle
 struct hz_mat {
     int device = -1;
@@ -321,6 +389,11 @@ struct hz_mat {
     // row blocks of the block-flat double-float kernel (complete rows)
     int32_t nfblk = 0;
     int32_t *fblk = nullptr;
+    // owned copy of col, 16-byte aligned and padded by 8 entries, that the
+    // bulk-copy kernel reads in 16-byte units; and its device fault word
+    // (nonzero once a bounded wait on a bulk copy expired)
+    int32_t *col_pad = nullptr;
+    int *fault = nullptr;
     // diagonal positions (for set_diag), built on demand
     int32_t *diag_pos = nullptr;
     // solver state (one per mode), created on first solve

@@ -51,7 +51,7 @@ template <>
 MatView<double2> mat_view<double2>(const hz_mat *A) {
     MatView<double2> v{};
     v.n = A->n; v.rowptr = A->rowptr; v.col = A->col; v.val = A->val; v.vff = A->val_ff; v.svff = A->sell_vff;
-    v.nfblk = A->nfblk; v.fblk = A->fblk;
+    v.nfblk = A->nfblk; v.fblk = A->fblk; v.colp = A->col_pad; v.fault = A->fault;
     v.nchunks = A->sell_nchunks; v.chunk_off = A->sell_chunk_off; v.chunk_w = A->sell_chunk_w;
     v.perm = A->sell_perm; v.scol = A->sell_col; v.sval = A->sell_val;
     return v;
@@ -69,14 +69,21 @@ MatView<float2> mat_view<float2>(const hz_mat *A) {
 int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap) {
     DevInfo d;
     if (dev_info(&d) != HZ_OK) return 1;
-    if (kind == HZ_SPMV_FF_FLAT) {
+    if (kind == HZ_SPMV_FF_FLAT || kind == HZ_SPMV_FF_TMA) {
         // persistent: exactly the CTAs that fit at once (blocks are taken
         // grid-stride, so CTAs beyond one wave would only add a tail)
-        static int occ = 0;
+        static int occ_flat = 0, occ_tma = 0;
+        int &occ = kind == HZ_SPMV_FF_TMA ? occ_tma : occ_flat;
         if (occ == 0) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_ffb<EpiStore<double2>>, kFlatThreads, 0) !=
-                    cudaSuccess || occ < 1)
-                occ = 1;
+            cudaError_t e;
+            if (kind == HZ_SPMV_FF_TMA) {
+                cudaFuncSetAttribute(k_spmv_fft<EpiStore<double2>>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_fft<EpiStore<double2>>, kFlatThreads, 0);
+            } else {
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_ffb<EpiStore<double2>>, kFlatThreads, 0);
+            }
+            if (e != cudaSuccess || occ < 1) occ = 1;
         }
         int64_t g = std::min<int64_t>(A->nfblk, (int64_t)d.num_sms * occ);
         return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
@@ -200,6 +207,7 @@ static hz_status autotune(hz_mat *A, cudaStream_t s) {
         for (int w : {2, 4, 8, 16, 32}) cand.push_back({HZ_SPMV_FF, w});
     if (A->sell_vff) cand.push_back({HZ_SPMV_SELL_FF, 0});
     if (A->fblk) cand.push_back({HZ_SPMV_FF_FLAT, 0});
+    if (A->col_pad) cand.push_back({HZ_SPMV_FF_TMA, 0});
     float best = 1e30f;
     MatView<double2> V = mat_view<double2>(A);
     EpiStore<double2> epi{y};
@@ -209,7 +217,7 @@ static hz_status autotune(hz_mat *A, cudaStream_t s) {
         float tms[5];
         for (int rep = -1; rep < 5; ++rep) {
             cudaEventRecord(e0, s);
-            if (c.first == HZ_SPMV_FF || c.first == HZ_SPMV_SELL_FF || c.first == HZ_SPMV_FF_FLAT)
+            if (is_ff_kind(c.first))
                 launch_spmv_ff(c.first, c.second, V, A->x_ff, epi, RedScratch{}, grid, s);
             else launch_spmv<double2>(c.first, c.second, V, x, epi, RedScratch{}, grid, s);
             cudaEventRecord(e1, s);
@@ -323,7 +331,8 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
     }
     if (flags & HZ_FLAG_C64) {
         if (cudaMalloc(&A->val32, sizeof(float2) * std::max(nnz, 1)) != cudaSuccess ||
-            (A->sell_slots && cudaMalloc(&A->sell_val32, sizeof(float2) * A->sell_slots) != cudaSuccess)) {
+            (A->sell_val && cudaMalloc(&A->sell_val32, sizeof(float2) * std::max<int64_t>(A->sell_slots, 1)) !=
+                                cudaSuccess)) {
             set_error("hz_csr_create: allocation failed");
             return fail(HZ_ERR_ALLOC);
         }
@@ -335,8 +344,8 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
             return fail(HZ_ERR_ALLOC);
         }
         if (n) cudaMemsetAsync(A->x_ff, 0, sizeof(float4) * n, s);
-        if (A->sell_slots) {
-            if (cudaMalloc(&A->sell_vff, sizeof(float4) * A->sell_slots) != cudaSuccess) {
+        if (A->sell_val) {
+            if (cudaMalloc(&A->sell_vff, sizeof(float4) * std::max<int64_t>(A->sell_slots, 1)) != cudaSuccess) {
                 set_error("hz_csr_create: allocation failed");
                 return fail(HZ_ERR_ALLOC);
             }
@@ -356,6 +365,16 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
             set_error("hz_csr_create: allocation failed");
             return fail(HZ_ERR_ALLOC);
         }
+        // padded column copy (16-byte aligned, 8 spare zero entries) for the
+        // bulk-copy kernel, which reads whole 16-byte units around each block
+        if (cudaMalloc(&A->col_pad, sizeof(int) * ((size_t)nnz + 8)) != cudaSuccess ||
+            cudaMalloc(&A->fault, sizeof(int)) != cudaSuccess) {
+            set_error("hz_csr_create: allocation failed");
+            return fail(HZ_ERR_ALLOC);
+        }
+        if (nnz) cudaMemcpyAsync(A->col_pad, A->col, sizeof(int) * nnz, cudaMemcpyDeviceToDevice, s);
+        cudaMemsetAsync(A->col_pad + nnz, 0, sizeof(int) * 8, s);
+        cudaMemsetAsync(A->fault, 0, sizeof(int), s);
         A->spmv_kind = HZ_SPMV_FF_FLAT;
     }
     if ((st = refresh(A, s)) != HZ_OK) return fail(st);
@@ -384,6 +403,8 @@ extern "C" HZ_API hz_status hz_mat_destroy(hz_mat *A) {
     cudaFree(A->sell_val);
     cudaFree(A->sell_vff);
     cudaFree(A->fblk);
+    cudaFree(A->col_pad);
+    cudaFree(A->fault);
     cudaFree(A->sell_val32);
     cudaFree(A->val32);
     cudaFree(A->val_ff);
@@ -408,6 +429,19 @@ extern "C" HZ_API hz_status hz_mat_query(const hz_mat *A, hz_mat_props *p) {
     return HZ_OK;
 }
 
+extern "C" HZ_API hz_status hz_mat_check(const hz_mat *A, void *stream) {
+    HZ_CHECK(A, "hz_mat_check: null handle");
+    if (!A->fault) return HZ_OK;
+    int f = 0;
+    HZ_CUDA(cudaMemcpyAsync(&f, A->fault, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    HZ_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (f) {
+        set_error("hz_mat_check: a bulk copy of the matrix stream did not complete within its wait limit");
+        return HZ_ERR_TIMEOUT;
+    }
+    return HZ_OK;
+}
+
 extern "C" HZ_API hz_status hz_mat_refresh_values(hz_mat *A, void *stream) {
     HZ_CHECK(A, "hz_mat_refresh_values: null handle");
     return refresh(A, (cudaStream_t)stream);
@@ -420,7 +454,7 @@ extern "C" HZ_API hz_status hz_zspmv(const hz_mat *A, const hz_z *d_x, hz_z *d_y
     HZ_CHECK((const void *)d_x != (const void *)d_y, "hz_zspmv: x and y must not alias");
     const int grid = spmv_grid(A, A->spmv_kind, A->group);
     EpiStore<double2> epi{(double2 *)d_y};
-    if (A->spmv_kind == HZ_SPMV_FF || A->spmv_kind == HZ_SPMV_SELL_FF || A->spmv_kind == HZ_SPMV_FF_FLAT) {
+    if (is_ff_kind(A->spmv_kind)) {
         HZ_CUDA(split_ff_vec(A->n, (const double2 *)d_x, A->x_ff, (cudaStream_t)stream));
         HZ_CUDA(launch_spmv_ff(A->spmv_kind, A->group, mat_view<double2>(A), A->x_ff, epi,
                                RedScratch{}, grid, (cudaStream_t)stream));
@@ -453,9 +487,9 @@ extern "C" HZ_API hz_status hz_mat_set_spmv(hz_mat *A, int32_t kind, int32_t gro
         A->spmv_kind = HZ_SPMV_SELL;
         return HZ_OK;
     }
-    if (kind == HZ_SPMV_FF_FLAT) {
+    if (kind == HZ_SPMV_FF_FLAT || kind == HZ_SPMV_FF_TMA) {
         HZ_CHECK(A->fblk != nullptr, "hz_mat_set_spmv: the handle has no double-float copy (HZ_FLAG_FF)");
-        A->spmv_kind = HZ_SPMV_FF_FLAT;
+        A->spmv_kind = kind;
         return HZ_OK;
     }
     if (kind == HZ_SPMV_SELL_FF) {

@@ -71,6 +71,9 @@ struct MatView {
     // complete rows [fblk[b], fblk[b+1]) (<= kFlatCap entries, or one row)
     int nfblk;
     const int *fblk;
+    // padded copy of col read by the bulk-copy kernel, and its fault word
+    const int *colp;
+    int *fault;
 };
 
 // Epilogue interface (every fused SpMV epilogue provides):
@@ -293,10 +296,10 @@ __device__ __forceinline__ void flat_rows_ff(const MatView<double2> &A, const fl
 #pragma unroll
             for (int u = 0; u < kFlatU; ++u) {
                 if (c[u] < 0) continue;
-                float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-                ff_mac(sr, cr, a[u].x, a[u].y, v[u].x, v[u].y);
+                float sr, cr, si, ci;
+                ff_mul(sr, cr, a[u].x, a[u].y, v[u].x, v[u].y);
                 ff_mac(sr, cr, -a[u].z, -a[u].w, v[u].z, v[u].w);
-                ff_mac(si, ci, a[u].x, a[u].y, v[u].z, v[u].w);
+                ff_mul(si, ci, a[u].x, a[u].y, v[u].z, v[u].w);
                 ff_mac(si, ci, a[u].z, a[u].w, v[u].x, v[u].y);
                 prod[lane + 32 * u] = make_float4(sr, cr, si, ci);
             }
@@ -323,6 +326,156 @@ __device__ __forceinline__ void flat_rows_ff(const MatView<double2> &A, const fl
             __syncwarp();
             if (kend >= ke) break;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block-flat double-float core with the matrix stream staged by bulk copies.
+//
+// The same row blocks and arithmetic as flat_rows_ff, but a warp's entries
+// (values and columns) reach shared memory through cp.async.bulk issued one
+// chunk ahead: while the warp gathers x and forms the products of chunk j,
+// the copy engine already moves chunk j+1 into the warp's other stage.  A
+// chunk is a row block, or a kFlatCap-entry piece of a longer single row.
+// The products overwrite the values in place (each lane reads and writes its
+// own slots), and phase 2 sums them per row as before.
+//
+// Every wait on a stage is bounded (kStageWaitNs of wall time); on expiry
+// the warp records the fault in A.fault, waits (bounded again) for its copy
+// still in flight, and stops.  The row outputs are then incomplete and the
+// fault word tells the host so.
+struct alignas(16) FlatStage {
+    float4 val[kFlatCap];   // values of the chunk, later its products
+    int col[kFlatCap + 8];  // columns from the 16-byte boundary below the chunk
+};
+constexpr int kTmaWarps = kFlatThreads / 32;
+constexpr uint64_t kStageWaitNs = 1000000000ull;
+
+template <class Epi, int NV>
+__device__ __forceinline__ void flat_rows_ff_tma(const MatView<double2> &A, const float4 *__restrict__ x,
+                                                 const Epi &epi, typename Epi::Acc (&acc)[NV],
+                                                 FlatStage *stg, uint64_t *bar) {
+    const uint64_t pol = pol_evict_first();
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * kTmaWarps;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    // chunk = entries [kc, kend) of row block b = rows [r0, r1), entries [kb, ke)
+    struct Chunk {
+        int b, r0, r1, kb, ke, kc, kend;
+    };
+    auto block_chunk = [&](int b) {
+        Chunk c;
+        c.b = b;
+        c.r0 = c.r1 = c.kb = c.ke = c.kc = c.kend = 0;
+        if (b < A.nfblk) {
+            c.r0 = __ldg(A.fblk + b);
+            c.r1 = __ldg(A.fblk + b + 1);
+            c.kb = __ldg(A.rowptr + c.r0);
+            c.ke = __ldg(A.rowptr + c.r1);
+            c.kc = c.kb;
+            c.kend = min(c.ke, c.kb + kFlatCap);
+        }
+        return c;
+    };
+    auto issue = [&](const Chunk &c, int s) {
+        if (lane != 0) return;
+        const int cnt = c.kend - c.kc;
+        if (cnt == 0) {   // rows without entries: complete the phase with no copy
+            mbar_arrive(bar + s);
+            return;
+        }
+        const int ca = c.kc & ~3, ce = (c.kend + 3) & ~3;
+        const unsigned bv = 16u * (unsigned)cnt, bc = 4u * (unsigned)(ce - ca);
+        mbar_arrive_tx(bar + s, bv + bc);
+        bulk_load(stg[s].val, A.vff + c.kc, bv, bar + s, pol);
+        bulk_load(stg[s].col, A.colp + ca, bc, bar + s, pol);
+    };
+    Chunk cur = block_chunk(blockIdx.x * kTmaWarps + (threadIdx.x >> 5));
+    if (cur.b >= A.nfblk) return;
+    issue(cur, 0);
+    unsigned phase = 0;   // bit s: parity of stage s's next completion
+    int s = 0;
+    float lsr = 0.f, lcr = 0.f, lsi = 0.f, lci = 0.f;   // long-row carry (lane 0)
+    for (;;) {
+        Chunk nxt;
+        if (cur.kend < cur.ke) {   // next piece of the same long row
+            nxt = cur;
+            nxt.kc = cur.kend;
+            nxt.kend = min(cur.ke, cur.kend + kFlatCap);
+        } else {
+            nxt = block_chunk(cur.b + nwarps);
+        }
+        const bool more = nxt.b < A.nfblk;
+        if (more) issue(nxt, s ^ 1);
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar + s, (phase >> s) & 1u, kStageWaitNs));
+        phase ^= 1u << s;
+        if (!ok) {
+            if (lane == 0) {
+                atomicExch(A.fault, 1);
+                mbar_wait_bounded(bar + s, ((phase >> s) & 1u) ^ 1u, kStageWaitNs);
+                if (more) mbar_wait_bounded(bar + (s ^ 1), (phase >> (s ^ 1)) & 1u, kStageWaitNs);
+            }
+            __syncwarp();
+            return;
+        }
+        FlatStage &S = stg[s];
+        const int cnt = cur.kend - cur.kc, off = cur.kc & 3;
+        // phase 1: products
+        int c[kFlatU];
+        float4 v[kFlatU];
+#pragma unroll
+        for (int u = 0; u < kFlatU; ++u) {
+            const int k = lane + 32 * u;
+            c[u] = k < cnt ? S.col[off + k] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kFlatU; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < kFlatU; ++u) {
+            if (c[u] < 0) continue;
+            const int k = lane + 32 * u;
+            const float4 a = S.val[k];
+            float sr, cr, si, ci;
+            ff_mul(sr, cr, a.x, a.y, v[u].x, v[u].y);
+            ff_mac(sr, cr, -a.z, -a.w, v[u].z, v[u].w);
+            ff_mul(si, ci, a.x, a.y, v[u].z, v[u].w);
+            ff_mac(si, ci, a.z, a.w, v[u].x, v[u].y);
+            S.val[k] = make_float4(sr, cr, si, ci);
+        }
+        __syncwarp();
+        // phase 2: row sums (rows clipped to this chunk's entries)
+        const bool long_row = cur.r1 - cur.r0 == 1 && cur.ke - cur.kb > kFlatCap;
+        if (long_row && cur.kc == cur.kb) lsr = lcr = lsi = lci = 0.f;
+        for (int row = cur.r0 + lane; row < cur.r1; row += 32) {
+            const int beg = max(__ldg(A.rowptr + row), cur.kc), end = min(__ldg(A.rowptr + row + 1), cur.kend);
+            float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+            for (int k = beg; k < end; ++k) {
+                const float4 q = S.val[k - cur.kc];
+                ff_acc(sr, cr, q.x);
+                cr = __fadd_rn(cr, q.y);
+                ff_acc(si, ci, q.z);
+                ci = __fadd_rn(ci, q.w);
+            }
+            if (long_row) {
+                ff_acc(lsr, lcr, sr); lcr = __fadd_rn(lcr, cr);
+                ff_acc(lsi, lci, si); lci = __fadd_rn(lci, ci);
+                if (cur.kend == cur.ke) ff_row_out<Epi, NV>(epi, row, lsr, lcr, lsi, lci, acc);
+            } else {
+                ff_row_out<Epi, NV>(epi, row, sr, cr, si, ci, acc);
+            }
+        }
+        // the copy issued at the top of the next iteration refills this
+        // stage: order this lane's reads and writes of it before that copy
+        fence_async_smem();
+        __syncwarp();
+        if (!more) break;
+        cur = nxt;
+        s ^= 1;
     }
 }
 
@@ -385,6 +538,25 @@ __global__ void __launch_bounds__(kFlatThreads) k_spmv_ffb(MatView<double2> A, c
     if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
 }
 
+// the block-flat double-float kernel with bulk-copy staging (kFlatThreads
+// threads; two stages of FlatStage per warp)
+template <class Epi>
+__global__ void __launch_bounds__(kFlatThreads) k_spmv_fft(MatView<double2> A, const float4 *__restrict__ x, Epi epi,
+                                                           RedScratch red) {
+    __shared__ FlatStage stg[kTmaWarps][2];
+    __shared__ uint64_t bar[kTmaWarps][2];
+    constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
+    pdl_wait();
+    pdl_release();
+    if (epi.skip()) return;
+    typename Epi::Acc acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
+    const int w = threadIdx.x >> 5;
+    flat_rows_ff_tma<Epi, NV>(A, x, epi, acc, stg[w], bar[w]);
+    if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
+}
+
 // binary64 -> double-float split of a vector (xff[i] = split_ff(x[i])), on stream s
 cudaError_t split_ff_vec(int n, const double2 *x, float4 *xff, cudaStream_t s);
 
@@ -437,6 +609,16 @@ cudaError_t launch_spmv_ff(int kind, int group, const MatView<double2> &A, const
                            RedScratch red, int grid, cudaStream_t s, bool pdl = false) {
     if (kind == HZ_SPMV_FF_FLAT) {
         launch_k(pdl, k_spmv_ffb<Epi>, grid, kFlatThreads, s, A, xff, epi, red);
+        return cudaGetLastError();
+    }
+    if (kind == HZ_SPMV_FF_TMA) {
+        static bool carveout = false;   // ask for the largest shared-memory carveout once
+        if (!carveout) {
+            cudaFuncSetAttribute(k_spmv_fft<Epi>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+            carveout = true;
+        }
+        launch_k(pdl, k_spmv_fft<Epi>, grid, kFlatThreads, s, A, xff, epi, red);
         return cudaGetLastError();
     }
     if (kind == HZ_SPMV_SELL_FF) {

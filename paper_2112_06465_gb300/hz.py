@@ -81,10 +81,15 @@ class Matrix:
 
     def set_spmv(self, kind="csr", group=4):
         """Force the SpMV variant: ("csr" | "ff", lanes per row) or ("sell" | "sellff" |
-        "ffflat", ignored)."""
+        "ffflat" | "fftma", ignored)."""
         k = {"sell": _lib.HZ_SPMV_SELL, "ff": _lib.HZ_SPMV_FF, "sellff": _lib.HZ_SPMV_SELL_FF,
-             "ffflat": _lib.HZ_SPMV_FF_FLAT}.get(kind, _lib.HZ_SPMV_CSR_VECTOR)
+             "ffflat": _lib.HZ_SPMV_FF_FLAT, "fftma": _lib.HZ_SPMV_FF_TMA}.get(kind, _lib.HZ_SPMV_CSR_VECTOR)
         check(_L.hz_mat_set_spmv(self.handle, k, int(group)))
+
+    def check(self):
+        """Synchronise the current stream and raise HzError(ERR_TIMEOUT) if a bounded
+        wait of an asynchronous SpMV on this handle expired."""
+        check(_L.hz_mat_check(self.handle, _stream()))
 
     def refresh_values(self):
         check(_L.hz_mat_refresh_values(self.handle, _stream()))

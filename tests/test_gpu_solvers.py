@@ -68,7 +68,7 @@ def test_bicgstab_manufactured_solution(hz, oracle):
 
 
 @pytest.mark.parametrize("variant", [("csr", 2), ("csr", 8), ("sell", 0), ("ff", 4), ("ff", 8), ("sellff", 0),
-                                     ("ffflat", 0)])
+                                     ("ffflat", 0), ("fftma", 0)])
 def test_bicgstab_cylinder_variants(hz, oracle, variant):
     A, b = K.small_cylinder()
     M = hz.Matrix.from_csr(A, sell=True, ff=True)

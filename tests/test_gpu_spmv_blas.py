@@ -38,11 +38,13 @@ def check_spmv(hz, oracle, A, x, variants):
         err = np.abs(y - ref)
         bad = err > TOL * scale + 1e-300
         assert not bad.any(), (kind, g, int(bad.sum()), float((err / np.maximum(scale, 1e-300)).max()))
+    M.check()
     M.close()
 
 
 ALL_VARIANTS = [("csr", 2), ("csr", 4), ("csr", 8), ("csr", 16), ("csr", 32), ("sell", 0),
-                ("ff", 2), ("ff", 4), ("ff", 8), ("ff", 16), ("ff", 32), ("sellff", 0), ("ffflat", 0)]
+                ("ff", 2), ("ff", 4), ("ff", 8), ("ff", 16), ("ff", 32), ("sellff", 0), ("ffflat", 0),
+                ("fftma", 0)]
 
 
 def test_spmv_worked_example_exact(hz, oracle):
@@ -89,9 +91,24 @@ def test_spmv_fd_and_cylinder(hz, oracle):
 
 
 def test_spmv_empty_matrix(hz):
-    M = hz.Matrix(dev(np.zeros(1, np.int32)), dev(np.zeros(0, np.int32)), dev(np.zeros(0, np.complex128)))
-    y = hz.zspmv(M, torch.zeros(0, dtype=torch.complex128, device="cuda"))
-    assert y.numel() == 0
+    for ff in (False, True):
+        M = hz.Matrix(dev(np.zeros(1, np.int32)), dev(np.zeros(0, np.int32)), dev(np.zeros(0, np.complex128)),
+                      ff=ff)
+        y = hz.zspmv(M, torch.zeros(0, dtype=torch.complex128, device="cuda"))
+        assert y.numel() == 0
+
+
+def test_spmv_rows_without_entries(hz):
+    """n > 0 with nnz = 0 (every row block empty): y = 0 on every variant."""
+    n = 70
+    M = hz.Matrix(dev(np.zeros(n + 1, np.int32)), dev(np.zeros(0, np.int32)), dev(np.zeros(0, np.complex128)),
+                  sell=True, ff=True)
+    x = dev(K.vectors(n, 9)[0])
+    for kind, g in ALL_VARIANTS:
+        M.set_spmv(kind, g)
+        y = host(hz.zspmv(M, x))
+        assert np.array_equal(y, np.zeros(n, dtype=np.complex128)), (kind, g)
+    M.check()
 
 
 def test_spmv_bad_csr_rejected(hz):
@@ -113,11 +130,14 @@ def test_spmv_c2_full_size_sampled(hz, oracle):
     x = K.vectors(A.n, 2002)[0]
     ref = oracle.zspmv(A, x)
     scale = K.row_abs_scale(A, x)
-    for ff in (False, True):
+    for ff, kind in ((False, None), (True, None), (True, "ffflat")):
         M = hz.Matrix.from_csr(A, ff=ff)
+        if kind:
+            M.set_spmv(kind)
         y = host(hz.zspmv(M, dev(x)))
         rel = np.abs(y - ref) / scale
-        assert rel.max() <= TOL, (ff, float(rel.max()))
+        assert rel.max() <= TOL, (ff, kind, float(rel.max()))
+        M.check()
         M.close()
 
 

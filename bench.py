@@ -236,6 +236,78 @@ def run_spmv_only(args):
                       "n": A.n, "nnz": A.nnz}))
 
 
+def compare_modes(hz, torch, full_c4, maxit):
+    """Mixed precision and the batched sweep against the plain complex128
+    solver on the C4 frequency-sweep systems, each to relative residual 1e-10.
+
+    Every system is solved (x0 = 0) by: the binary64 solver (CSR-vector
+    SpMV), the double-float complex128 solver (block-flat SpMV), the mixed
+    solver (complex64 inner BiCGStab, binary64 outer refinement) and, for all
+    systems at once, the persistent batched binary64 solver.  Times are CUDA
+    events around each call, after one untimed call of each kind (graph
+    capture).  Speedups are over the systems every variant solved."""
+    import workloads as W
+    from workloads import configs as WC
+    cyl = WC.C4_CYLINDERS if full_c4 else WC.C4_CYLINDERS[:1]
+    systems = W.c4_sweep_systems(cylinders=cyl)
+    stream = torch.cuda.current_stream()
+    mats, bs = [], []
+    for name, A, b in systems:
+        M = hz.Matrix.from_csr(A, ff=True, c64=True)
+        mats.append(M)
+        bs.append(torch.as_tensor(b).to("cuda"))
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    variants = {"fp64_binary64": ("csr", "fp64"), "fp64_double_float": ("ffflat", "fp64"),
+                "mixed": ("csr", "mixed")}
+    res = {k: [] for k in variants}
+    for M, b in zip(mats, bs):
+        for key, (kind, mode) in variants.items():
+            M.set_spmv(kind, M.props()["group"] if kind == "csr" else 0)
+            hz.zsolve(M, b, tol=1e-10, maxit=maxit, mode=mode)          # graph capture
+            (_, info), ms = timed(lambda: hz.zsolve(M, b, tol=1e-10, maxit=maxit, mode=mode))
+            res[key].append((ms, info))
+    hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit)
+    (_, binfos), bms = timed(lambda: hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit))
+    ok_all = [all(res[k][i][1].converged for k in variants) and binfos[i].converged
+              for i in range(len(mats))]
+
+    def summary(rows):
+        t_ok = sum(ms for (ms, _), ok in zip(rows, ok_all) if ok)
+        return {"s_total": sum(ms for ms, _ in rows) / 1e3, "s_on_common": t_ok / 1e3,
+                "converged": sum(1 for _, i in rows if i.converged),
+                "iters": sum(i.iters for _, i in rows),
+                "max_relres_true": max(i.relres_true for _, i in rows)}
+
+    out = {"systems": len(mats), "solved_by_all": sum(ok_all), "tol": 1e-10, "maxit": maxit,
+           "workload": "C4 frequency sweep: FD boxes %s x 8 kh in [0.2, 0.8] + jittered P1 cylinders %s x 8 kh, "
+                       "shift 0.05i" % (list(WC.C4_BOXES), [list(c) for c in cyl])}
+    for key in variants:
+        out[key] = summary(res[key])
+    out["mixed"]["outer"] = sum(i.outer for _, i in res["mixed"])
+    out["batched_fp64"] = {"s_total": bms / 1e3, "converged": sum(1 for i in binfos if i.converged),
+                           "iters": sum(i.iters for i in binfos),
+                           "max_relres_true": max(i.relres_true for i in binfos)}
+    base = out["fp64_binary64"]["s_on_common"]
+    out["speedup_vs_fp64_binary64_on_common"] = {
+        "fp64_double_float": base / max(out["fp64_double_float"]["s_on_common"], 1e-12),
+        "mixed": base / max(out["mixed"]["s_on_common"], 1e-12)}
+    out["speedup_vs_fp64_binary64_all_systems"] = {
+        "fp64_double_float": out["fp64_binary64"]["s_total"] / out["fp64_double_float"]["s_total"],
+        "mixed": out["fp64_binary64"]["s_total"] / out["mixed"]["s_total"],
+        "batched_fp64": out["fp64_binary64"]["s_total"] / out["batched_fp64"]["s_total"]}
+    for M in mats:
+        M.close()
+    return out
+
+
 def workload_config(A, maxit, arith="fp64"):
     return {"workload": "C2 jittered P1-FEM cylinder nr=40 ntheta=96 nz=160 k=20 impedance ends, "
                         f"complex128 BiCGStab x0=0 tol=1e-10 maxit={maxit}",
@@ -257,6 +329,11 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=200)
     ap.add_argument("--cpu-iters", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the mixed / batched / double-float comparison on the C4 sweep")
+    ap.add_argument("--c4-full", action="store_true",
+                    help="compare on all 64 C4 systems (default: the boxes and the smallest cylinder)")
+    ap.add_argument("--compare-maxit", type=int, default=3000)
     ap.add_argument("--spmv-only", action="store_true",
                     help="profiling aid: build C2, run three SpMV launches of the chosen "
                          "arithmetic (--arith, --group) and exit without timing")
@@ -389,13 +466,15 @@ def main():
                   "spmv_variant": {"kind": props["spmv_kind"], "group": props["group"]}},
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
+                     "frac": achieved / peak, "traffic": traffic, "frac_of_nominal_8000": achieved / 8000.0,
                      "kernel": "%s SpMV through hz_zspmv alone, L2 flushed; peak %s (burst copy)"
                                % (SPMV_KINDS.get(props["spmv_kind"], props["spmv_kind"]), peak_src),
                      "algorithmic_bytes_per_launch": spmv_bytes(A.n, A.nnz), "launch_ms": sp_avg},
         "clocks": clk.summary(),
         "gpu_launches": launches,
     }
+    if rank == 0 and not args.no_compare:
+        line["compare"] = compare_modes(hz, torch, args.c4_full, args.compare_maxit)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, dt, it = cpu_oracle_rate(A, b, args.cpu_iters)
         line["cpu_baseline"] = {"value": r, "unit": "GB/s", "cores": 1, "kind": "oracle",

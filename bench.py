@@ -98,7 +98,7 @@ def kernel_source_sha():
 def recorded_traffic():
     """DRAM bytes per SpMV launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "spmv_csr_c2_traffic.txt")
+    p = os.path.join(ROOT, "profiles", "spmv_ffb_c2_traffic.txt")
     try:
         kv = {}
         with open(p) as f:

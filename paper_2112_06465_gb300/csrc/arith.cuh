@@ -89,7 +89,7 @@ template <> struct Ar<float4> {
     __device__ static V zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
     __device__ static V from_c128(double2 a) { return split_ff(a); }
     __device__ static double2 to_c128(V a) {
-        return make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
+        return make_double2(join_d(a.x, a.y), join_d(a.z, a.w));
     }
     // y + a x, each component accumulated exactly from y then rounded once
     __device__ static V axpy(V y, S a, V x) {

@@ -151,10 +151,61 @@ __device__ __forceinline__ int ld_stream(const int *ptr, uint64_t pol) {
 //   TwoSum (Knuth):            s = fl(a+b), e = (a - (s - z)) + (b - z), z = s - a
 // The explicit __f*_rn intrinsics keep the compiler from contracting or
 // reassociating these sequences.
-__device__ __forceinline__ float4 split_ff(double2 d) {
-    const float hr = __double2float_rn(d.x), hi = __double2float_rn(d.y);
-    return make_float4(hr, __double2float_rn(d.x - (double)hr), hi, __double2float_rn(d.y - (double)hi));
+//
+// Conversions between binary64 and binary32 run on GB300's slow conversion
+// path (about 276 G conversions/s for the whole GPU, measured), so the split
+// and the widening below work on the bit patterns with integer operations
+// and fall back to the conversion instructions only outside the range where
+// the bit formula holds.  Both give the same bits as the conversions.
+//
+// split: hi = RN_32(d), lo = RN_32(d - hi).  With d = (-1)^s * m * 2^(E-52),
+// m a 53-bit integer, hi takes the top 24 bits of m rounded to nearest even
+// and lo is the signed 29-bit remainder times 2^(E-52); for -74 <= E <= 126
+// both are normal binary32 numbers (or lo = 0) and the power-of-two scaling
+// is exact.
+__device__ __forceinline__ void split_d(double d, float &hi, float &lo) {
+    const unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
+    const int E = (int)((hw >> 20) & 0x7ffu) - 1023;
+    if (((hw & 0x7fffffffu) | lw) == 0u) {   // signed zero
+        hi = __uint_as_float(hw & 0x80000000u);
+        lo = 0.f;
+        return;
+    }
+    if (E >= -74 && E <= 126) {
+        unsigned top = (((hw & 0xfffffu) | 0x100000u) << 3) | (lw >> 29);   // 24 bits
+        int low = (int)(lw & 0x1fffffffu);                                 // 29 bits
+        constexpr int kHalf = 1 << 28;
+        if (low > kHalf || (low == kHalf && (top & 1u))) {
+            top += 1u;   // a carry into bit 24 moves hi to the next binade below
+            low -= 1 << 29;
+        }
+        hi = __uint_as_float((hw & 0x80000000u) | (((unsigned)(E + 127) << 23) + (top - 0x800000u)));
+        if (hw & 0x80000000u) low = -low;
+        lo = __fmul_rn(__int2float_rn(low), __uint_as_float((unsigned)(E - 52 + 127) << 23));
+        return;
+    }
+    hi = __double2float_rn(d);
+    lo = __double2float_rn(d - (double)hi);
 }
+
+// exact binary32 -> binary64 widening (normal numbers by bits, others by conversion)
+__device__ __forceinline__ double widen_d(float f) {
+    const unsigned u = __float_as_uint(f), ex = (u >> 23) & 0xffu;
+    if (ex - 1u < 254u)
+        return __hiloint2double((int)((u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3)),
+                                (int)(u << 29));
+    return (double)f;
+}
+
+__device__ __forceinline__ float4 split_ff(double2 d) {
+    float4 r;
+    split_d(d.x, r.x, r.y);
+    split_d(d.y, r.z, r.w);
+    return r;
+}
+
+// ff pair (hi, lo) rounded once to binary64
+__device__ __forceinline__ double join_d(float hi, float lo) { return widen_d(hi) + widen_d(lo); }
 
 // (s, c) += p, with the rounding error of s + p carried into c
 __device__ __forceinline__ void ff_acc(float &s, float &c, float p) {

@@ -132,7 +132,7 @@ __device__ __forceinline__ void ff_row_out(const Epi &epi, int row, float sr, fl
         const float2 r = ff_norm(sr, cr), i = ff_norm(si, ci);
         epi.row(row, make_float4(r.x, r.y, i.x, i.y), acc);
     } else {
-        epi.row(row, make_double2((double)sr + (double)cr, (double)si + (double)ci), acc);
+        epi.row(row, make_double2(join_d(sr, cr), join_d(si, ci)), acc);
     }
 }
 

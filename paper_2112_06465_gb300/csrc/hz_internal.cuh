@@ -237,6 +237,66 @@ __device__ __forceinline__ void ff_mul(float &s, float &c, float ah, float al, f
 }
 
 // ---------------------------------------------------------------------------
+// packed binary32 pairs (PTX .f32x2 on sm_100 and later): one instruction
+// applies the same IEEE round-to-nearest operation to two lanes, so the
+// error-free transformations above stay exact lane by lane while the real
+// and imaginary halves of a complex double-float sum share instructions.
+// GB300 retires these at the scalar lane rate with half the issue slots.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// TwoSum on both lanes: s + p = t + e exactly
+__device__ __forceinline__ void two_sum2(f32x2 s, f32x2 p, f32x2 &t, f32x2 &e) {
+    t = add2(s, p);
+    const f32x2 z = sub2(t, s);
+    e = add2(sub2(s, sub2(t, z)), sub2(p, z));
+}
+
+// complex double-float product a * x for a, x in the (re_hi, re_lo, im_hi,
+// im_lo) layout.  The four real products are formed by ff_mul; the pairs
+// (re, im) are then summed with one packed TwoSum.  Returned as
+// (re_hi, im_hi, re_lo, im_lo): the hi pair and the pair of their error
+// sums (not renormalised).  The dropped lo*lo terms are 2^-48 relative.
+__device__ __forceinline__ float4 ff_cprod(float4 a, float4 x) {
+    float prr, err, pii, eii, pri, eri, pir, eir;
+    ff_mul(prr, err, a.x, a.y, x.x, x.y);
+    ff_mul(pii, eii, -a.z, -a.w, x.z, x.w);
+    ff_mul(pri, eri, a.x, a.y, x.z, x.w);
+    ff_mul(pir, eir, a.z, a.w, x.x, x.y);
+    f32x2 t, e;
+    two_sum2(pk2(prr, pri), pk2(pii, pir), t, e);
+    const f32x2 c = add2(add2(pk2(err, eri), pk2(eii, eir)), e);
+    float4 r;
+    upk2(t, r.x, r.y);
+    upk2(c, r.z, r.w);
+    return r;
+}
+
+// (S, C) += q for a product q in the layout ff_cprod returns
+__device__ __forceinline__ void ff_cacc(f32x2 &S, f32x2 &C, float4 q) {
+    f32x2 t, e;
+    two_sum2(S, pk2(q.x, q.y), t, e);
+    S = t;
+    C = add2(C, add2(e, pk2(q.z, q.w)));
+}
+
+// ---------------------------------------------------------------------------
 // programmatic dependent launch (PTX griddepcontrol).  A kernel launched with
 // the programmatic-serialization attribute may start while its predecessor
 // is still draining; pdl_wait() blocks until the predecessor grid has
@@ -440,6 +500,8 @@ struct hz_mat {
     // row blocks of the block-flat double-float kernel (complete rows)
     int32_t nfblk = 0;
     int32_t *fblk = nullptr;
+    int32_t nfblk_t = 0;       // the same for the bulk-copy kernel's smaller chunks
+    int32_t *fblk_t = nullptr;
     // owned copy of col, 16-byte aligned and padded by 8 entries, that the
     // bulk-copy kernel reads in 16-byte units; and its device fault word
     // (nonzero once a bounded wait on a bulk copy expired)

@@ -51,7 +51,7 @@ template <>
 MatView<double2> mat_view<double2>(const hz_mat *A) {
     MatView<double2> v{};
     v.n = A->n; v.rowptr = A->rowptr; v.col = A->col; v.val = A->val; v.vff = A->val_ff; v.svff = A->sell_vff;
-    v.nfblk = A->nfblk; v.fblk = A->fblk; v.colp = A->col_pad; v.fault = A->fault;
+    v.nfblk = A->nfblk; v.fblk = A->fblk; v.nfblk_t = A->nfblk_t; v.fblk_t = A->fblk_t; v.colp = A->col_pad; v.fault = A->fault;
     v.nchunks = A->sell_nchunks; v.chunk_off = A->sell_chunk_off; v.chunk_w = A->sell_chunk_w;
     v.perm = A->sell_perm; v.scol = A->sell_col; v.sval = A->sell_val;
     return v;
@@ -85,7 +85,7 @@ int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap) {
             }
             if (e != cudaSuccess || occ < 1) occ = 1;
         }
-        int64_t g = std::min<int64_t>(A->nfblk, (int64_t)d.num_sms * occ);
+        int64_t g = std::min<int64_t>(kind == HZ_SPMV_FF_TMA ? A->nfblk_t : A->nfblk, (int64_t)d.num_sms * occ);
         return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
     }
     const bool sell = kind == HZ_SPMV_SELL || kind == HZ_SPMV_SELL_FF;
@@ -350,18 +350,22 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
                 return fail(HZ_ERR_ALLOC);
             }
         }
-        // row blocks for the block-flat kernel: greedy runs of complete rows
-        // with at most kFlatCap entries; a longer row is a block of its own
-        std::vector<int> fb{0};
-        for (int r = 0; r < n;) {
-            int r1 = r + 1;
-            while (r1 < n && rp[r1 + 1] - rp[r] <= kFlatCap) ++r1;
-            fb.push_back(r1);
-            r = r1;
-        }
-        A->nfblk = (int)fb.size() - 1;
-        if (cudaMalloc(&A->fblk, sizeof(int) * fb.size()) != cudaSuccess ||
-            cudaMemcpy(A->fblk, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        // row blocks for the block-flat kernels: greedy runs of at most
+        // kFlatRows complete rows with at most `cap` entries; a longer row is
+        // a block of its own
+        auto row_blocks = [&](int cap, int32_t **dev, int32_t *count) {
+            std::vector<int> fb{0};
+            for (int r = 0; r < n;) {
+                int r1 = r + 1;
+                while (r1 < n && r1 - r < kFlatRows && rp[r1 + 1] - rp[r] <= cap) ++r1;
+                fb.push_back(r1);
+                r = r1;
+            }
+            *count = (int32_t)fb.size() - 1;
+            return cudaMalloc(dev, sizeof(int) * fb.size()) == cudaSuccess &&
+                   cudaMemcpy(*dev, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+        };
+        if (!row_blocks(kFlatCap, &A->fblk, &A->nfblk) || !row_blocks(kTmaCap, &A->fblk_t, &A->nfblk_t)) {
             set_error("hz_csr_create: allocation failed");
             return fail(HZ_ERR_ALLOC);
         }
@@ -403,6 +407,7 @@ extern "C" HZ_API hz_status hz_mat_destroy(hz_mat *A) {
     cudaFree(A->sell_val);
     cudaFree(A->sell_vff);
     cudaFree(A->fblk);
+    cudaFree(A->fblk_t);
     cudaFree(A->col_pad);
     cudaFree(A->fault);
     cudaFree(A->sell_val32);

@@ -45,11 +45,17 @@ constexpr bool kFFTranspose = HZ_FF_TRANSPOSE != 0;  // lane-transposed row outp
 #define HZ_FLAT_THREADS 128
 #endif
 #ifndef HZ_FLAT_U
-#define HZ_FLAT_U 8
+#define HZ_FLAT_U 16
+#endif
+#ifndef HZ_FLAT_GROUP
+#define HZ_FLAT_GROUP 8
 #endif
 constexpr int kFlatThreads = HZ_FLAT_THREADS;   // warps per CTA = kFlatThreads / 32
 constexpr int kFlatU = HZ_FLAT_U;
+constexpr int kFlatGroup = HZ_FLAT_GROUP;       // entries per lane whose loads are in flight together
 constexpr int kFlatCap = 32 * kFlatU;           // entries per warp row block
+constexpr int kFlatRows = 32;                   // rows per row block (one per lane in phase 2)
+static_assert(kFlatU % kFlatGroup == 0, "kFlatU must be a multiple of kFlatGroup");
 
 template <class T>
 struct MatView {
@@ -67,10 +73,13 @@ struct MatView {
     // double-float split values (used by the ff kernels), CSR and SELL order
     const float4 *vff;
     const float4 *svff;
-    // row blocks of the block-flat double-float kernel: block b holds the
-    // complete rows [fblk[b], fblk[b+1]) (<= kFlatCap entries, or one row)
+    // row blocks of the block-flat double-float kernels: block b holds the
+    // complete rows [fblk[b], fblk[b+1]) (<= 32 rows and kFlatCap entries, or
+    // one longer row); fblk_t the same with kTmaCap for the bulk-copy kernel
     int nfblk;
     const int *fblk;
+    int nfblk_t;
+    const int *fblk_t;
     // padded copy of col read by the bulk-copy kernel, and its fault word
     const int *colp;
     int *fault;
@@ -258,13 +267,61 @@ __device__ __forceinline__ void sell_rows_ff(const MatView<double2> &A, const fl
     }
 }
 
-// Block-flat double-float core, one warp per row block (complete rows,
-// <= kFlatCap = 32*kFlatU entries, or a single longer row).  Two phases:
+// row result from packed accumulators S = (re_hi, im_hi), C = (re_lo, im_lo):
+// normalised ff pair (kFFRow, both halves by one packed TwoSum) or binary64
+template <class Epi, int NV>
+__device__ __forceinline__ void ff_row_out2(const Epi &epi, int row, f32x2 S, f32x2 C,
+                                            typename Epi::Acc (&acc)[NV]) {
+    if constexpr (Epi::kFFRow) {
+        f32x2 h, l;
+        two_sum2(S, C, h, l);
+        float hr, hi, lr, li;
+        upk2(h, hr, hi);
+        upk2(l, lr, li);
+        epi.row(row, make_float4(hr, lr, hi, li), acc);
+    } else {
+        float sr, si, cr, ci;
+        upk2(S, sr, si);
+        upk2(C, cr, ci);
+        epi.row(row, make_double2(join_d(sr, cr), join_d(si, ci)), acc);
+    }
+}
+
+// Phase 2 of the block-flat kernels: lane j sums the products of row r0 + j
+// (+32, ...) held in prod[] for entries [kc, kend) and hands finished rows to
+// the epilogue.  A single row longer than one chunk is summed over several
+// chunks, lane 0 carrying (LS, LC) until the chunk that ends at ke.
+template <class Epi, int NV>
+__device__ __forceinline__ void flat_row_sums(const MatView<double2> &A, const float4 *prod, int r0, int r1,
+                                              int kc, int kend, int ke, bool long_row, f32x2 &LS, f32x2 &LC,
+                                              const Epi &epi, typename Epi::Acc (&acc)[NV]) {
+    for (int row = r0 + (threadIdx.x & 31); row < r1; row += 32) {
+        const int beg = max(__ldg(A.rowptr + row), kc), end = min(__ldg(A.rowptr + row + 1), kend);
+        f32x2 S = 0ull, C = 0ull;   // +0.0f in both lanes
+        for (int k = beg; k < end; ++k) ff_cacc(S, C, prod[k - kc]);
+        if (long_row) {
+            f32x2 t, e;
+            two_sum2(LS, S, t, e);
+            LS = t;
+            LC = add2(LC, add2(e, C));
+            if (kend == ke) ff_row_out2<Epi, NV>(epi, row, LS, LC, acc);
+        } else {
+            ff_row_out2<Epi, NV>(epi, row, S, C, acc);
+        }
+    }
+}
+
+// Block-flat double-float core, one warp per row block (complete rows: at
+// most 32 rows and kFlatCap = 32*kFlatU entries, or a single longer row).
+// Two phases:
 //  1. lane l takes entries kb + l + 32*u (coalesced loads, every lane busy),
-//     forms each entry's complex product a*x in double-float and stores it
-//     to the warp's slab of shared memory;
-//  2. lane j sums the products of row r0 + j (+32, ...) from the slab and
-//     hands the row to the epilogue.
+//     forms each entry's complex product a*x in double-float (ff_cprod) and
+//     stores it to the warp's slab of shared memory; the kFlatU entries of a
+//     lane go in groups of kFlatGroup (loads of a group, then its gathers,
+//     then its products);
+//  2. lane j sums the products of row r0 + j from the slab (packed pairs,
+//     one pass since a block has at most 32 rows) and hands the row to the
+//     epilogue.
 // Row boundaries never enter the streaming phase, which runs like a flat
 // gather-stream; warps need only __syncwarp.  A single row longer than
 // kFlatCap is processed in kFlatCap-entry passes, lane 0 carrying its sum.
@@ -279,50 +336,31 @@ __device__ __forceinline__ void flat_rows_ff(const MatView<double2> &A, const fl
         const int r0 = __ldg(A.fblk + b), r1 = __ldg(A.fblk + b + 1);
         const int kb = __ldg(A.rowptr + r0), ke = __ldg(A.rowptr + r1);
         const bool long_row = r1 - r0 == 1 && ke - kb > kFlatCap;
-        float lsr = 0.f, lcr = 0.f, lsi = 0.f, lci = 0.f;   // long-row carry (lane 0)
+        f32x2 LS = 0ull, LC = 0ull;   // long-row carry (lane 0)
         for (int kc = kb;; kc += kFlatCap) {
             const int kend = min(ke, kc + kFlatCap);
             // phase 1: products
-            int c[kFlatU];
-            float4 a[kFlatU], v[kFlatU];
+#pragma unroll 1
+            for (int g = 0; g < kFlatU; g += kFlatGroup) {
+                int c[kFlatGroup];
+                float4 a[kFlatGroup], v[kFlatGroup];
 #pragma unroll
-            for (int u = 0; u < kFlatU; ++u) {
-                const int k = kc + lane + 32 * u;
-                c[u] = k < kend ? ld_stream(A.col + k, pol) : -1;
-                a[u] = k < kend ? ld_stream(A.vff + k, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+                for (int u = 0; u < kFlatGroup; ++u) {
+                    const int k = kc + lane + 32 * (g + u);
+                    c[u] = k < kend ? ld_stream(A.col + k, pol) : -1;
+                    a[u] = k < kend ? ld_stream(A.vff + k, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
 #pragma unroll
-            for (int u = 0; u < kFlatU; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int u = 0; u < kFlatGroup; ++u)
+                    v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int u = 0; u < kFlatU; ++u) {
-                if (c[u] < 0) continue;
-                float sr, cr, si, ci;
-                ff_mul(sr, cr, a[u].x, a[u].y, v[u].x, v[u].y);
-                ff_mac(sr, cr, -a[u].z, -a[u].w, v[u].z, v[u].w);
-                ff_mul(si, ci, a[u].x, a[u].y, v[u].z, v[u].w);
-                ff_mac(si, ci, a[u].z, a[u].w, v[u].x, v[u].y);
-                prod[lane + 32 * u] = make_float4(sr, cr, si, ci);
+                for (int u = 0; u < kFlatGroup; ++u)
+                    if (c[u] >= 0) prod[lane + 32 * (g + u)] = ff_cprod(a[u], v[u]);
+                if (kc + 32 * (g + kFlatGroup) >= kend) break;
             }
             __syncwarp();
             // phase 2: row sums (rows clipped to this pass's entries)
-            for (int row = r0 + lane; row < r1; row += 32) {
-                const int beg = max(__ldg(A.rowptr + row), kc), end = min(__ldg(A.rowptr + row + 1), kend);
-                float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-                for (int k = beg; k < end; ++k) {
-                    const float4 q = prod[k - kc];
-                    ff_acc(sr, cr, q.x);
-                    cr = __fadd_rn(cr, q.y);
-                    ff_acc(si, ci, q.z);
-                    ci = __fadd_rn(ci, q.w);
-                }
-                if (long_row) {
-                    ff_acc(lsr, lcr, sr); lcr = __fadd_rn(lcr, cr);
-                    ff_acc(lsi, lci, si); lci = __fadd_rn(lci, ci);
-                    if (kend == ke) ff_row_out<Epi, NV>(epi, row, lsr, lcr, lsi, lci, acc);
-                } else {
-                    ff_row_out<Epi, NV>(epi, row, sr, cr, si, ci, acc);
-                }
-            }
+            flat_row_sums<Epi, NV>(A, prod, r0, r1, kc, kend, ke, long_row, LS, LC, epi, acc);
             __syncwarp();
             if (kend >= ke) break;
         }
@@ -335,8 +373,10 @@ __device__ __forceinline__ void flat_rows_ff(const MatView<double2> &A, const fl
 // The same row blocks and arithmetic as flat_rows_ff, but a warp's entries
 // (values and columns) reach shared memory through cp.async.bulk issued one
 // chunk ahead: while the warp gathers x and forms the products of chunk j,
-// the copy engine already moves chunk j+1 into the warp's other stage.  A
-// chunk is a row block, or a kFlatCap-entry piece of a longer single row.
+// the copy engine already moves chunk j+1 into the warp's other stage.  Its
+// row blocks (fblk_t) hold at most kTmaCap entries so that two stages of
+// four warps fit beside each other; a chunk is a row block, or a
+// kTmaCap-entry piece of a longer single row.
 // The products overwrite the values in place (each lane reads and writes its
 // own slots), and phase 2 sums them per row as before.
 //
@@ -344,9 +384,11 @@ __device__ __forceinline__ void flat_rows_ff(const MatView<double2> &A, const fl
 // the warp records the fault in A.fault, waits (bounded again) for its copy
 // still in flight, and stops.  The row outputs are then incomplete and the
 // fault word tells the host so.
+constexpr int kTmaU = 8;
+constexpr int kTmaCap = 32 * kTmaU;   // entries per chunk of the bulk-copy kernel
 struct alignas(16) FlatStage {
-    float4 val[kFlatCap];   // values of the chunk, later its products
-    int col[kFlatCap + 8];  // columns from the 16-byte boundary below the chunk
+    float4 val[kTmaCap];   // values of the chunk, later its products
+    int col[kTmaCap + 8];  // columns from the 16-byte boundary below the chunk
 };
 constexpr int kTmaWarps = kFlatThreads / 32;
 constexpr uint64_t kStageWaitNs = 1000000000ull;
@@ -372,13 +414,13 @@ __device__ __forceinline__ void flat_rows_ff_tma(const MatView<double2> &A, cons
         Chunk c;
         c.b = b;
         c.r0 = c.r1 = c.kb = c.ke = c.kc = c.kend = 0;
-        if (b < A.nfblk) {
-            c.r0 = __ldg(A.fblk + b);
-            c.r1 = __ldg(A.fblk + b + 1);
+        if (b < A.nfblk_t) {
+            c.r0 = __ldg(A.fblk_t + b);
+            c.r1 = __ldg(A.fblk_t + b + 1);
             c.kb = __ldg(A.rowptr + c.r0);
             c.ke = __ldg(A.rowptr + c.r1);
             c.kc = c.kb;
-            c.kend = min(c.ke, c.kb + kFlatCap);
+            c.kend = min(c.ke, c.kb + kTmaCap);
         }
         return c;
     };
@@ -396,21 +438,21 @@ __device__ __forceinline__ void flat_rows_ff_tma(const MatView<double2> &A, cons
         bulk_load(stg[s].col, A.colp + ca, bc, bar + s, pol);
     };
     Chunk cur = block_chunk(blockIdx.x * kTmaWarps + (threadIdx.x >> 5));
-    if (cur.b >= A.nfblk) return;
+    if (cur.b >= A.nfblk_t) return;
     issue(cur, 0);
     unsigned phase = 0;   // bit s: parity of stage s's next completion
     int s = 0;
-    float lsr = 0.f, lcr = 0.f, lsi = 0.f, lci = 0.f;   // long-row carry (lane 0)
+    f32x2 LS = 0ull, LC = 0ull;   // long-row carry (lane 0)
     for (;;) {
         Chunk nxt;
         if (cur.kend < cur.ke) {   // next piece of the same long row
             nxt = cur;
             nxt.kc = cur.kend;
-            nxt.kend = min(cur.ke, cur.kend + kFlatCap);
+            nxt.kend = min(cur.ke, cur.kend + kTmaCap);
         } else {
             nxt = block_chunk(cur.b + nwarps);
         }
-        const bool more = nxt.b < A.nfblk;
+        const bool more = nxt.b < A.nfblk_t;
         if (more) issue(nxt, s ^ 1);
         const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar + s, (phase >> s) & 1u, kStageWaitNs));
         phase ^= 1u << s;
@@ -426,49 +468,25 @@ __device__ __forceinline__ void flat_rows_ff_tma(const MatView<double2> &A, cons
         FlatStage &S = stg[s];
         const int cnt = cur.kend - cur.kc, off = cur.kc & 3;
         // phase 1: products
-        int c[kFlatU];
-        float4 v[kFlatU];
+        int c[kTmaU];
+        float4 v[kTmaU];
 #pragma unroll
-        for (int u = 0; u < kFlatU; ++u) {
+        for (int u = 0; u < kTmaU; ++u) {
             const int k = lane + 32 * u;
             c[u] = k < cnt ? S.col[off + k] : -1;
         }
 #pragma unroll
-        for (int u = 0; u < kFlatU; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = 0; u < kTmaU; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int u = 0; u < kFlatU; ++u) {
-            if (c[u] < 0) continue;
+        for (int u = 0; u < kTmaU; ++u) {
             const int k = lane + 32 * u;
-            const float4 a = S.val[k];
-            float sr, cr, si, ci;
-            ff_mul(sr, cr, a.x, a.y, v[u].x, v[u].y);
-            ff_mac(sr, cr, -a.z, -a.w, v[u].z, v[u].w);
-            ff_mul(si, ci, a.x, a.y, v[u].z, v[u].w);
-            ff_mac(si, ci, a.z, a.w, v[u].x, v[u].y);
-            S.val[k] = make_float4(sr, cr, si, ci);
+            if (c[u] >= 0) S.val[k] = ff_cprod(S.val[k], v[u]);
         }
         __syncwarp();
         // phase 2: row sums (rows clipped to this chunk's entries)
-        const bool long_row = cur.r1 - cur.r0 == 1 && cur.ke - cur.kb > kFlatCap;
-        if (long_row && cur.kc == cur.kb) lsr = lcr = lsi = lci = 0.f;
-        for (int row = cur.r0 + lane; row < cur.r1; row += 32) {
-            const int beg = max(__ldg(A.rowptr + row), cur.kc), end = min(__ldg(A.rowptr + row + 1), cur.kend);
-            float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-            for (int k = beg; k < end; ++k) {
-                const float4 q = S.val[k - cur.kc];
-                ff_acc(sr, cr, q.x);
-                cr = __fadd_rn(cr, q.y);
-                ff_acc(si, ci, q.z);
-                ci = __fadd_rn(ci, q.w);
-            }
-            if (long_row) {
-                ff_acc(lsr, lcr, sr); lcr = __fadd_rn(lcr, cr);
-                ff_acc(lsi, lci, si); lci = __fadd_rn(lci, ci);
-                if (cur.kend == cur.ke) ff_row_out<Epi, NV>(epi, row, lsr, lcr, lsi, lci, acc);
-            } else {
-                ff_row_out<Epi, NV>(epi, row, sr, cr, si, ci, acc);
-            }
-        }
+        const bool long_row = cur.r1 - cur.r0 == 1 && cur.ke - cur.kb > kTmaCap;
+        if (long_row && cur.kc == cur.kb) LS = LC = 0ull;
+        flat_row_sums<Epi, NV>(A, S.val, cur.r0, cur.r1, cur.kc, cur.kend, cur.ke, long_row, LS, LC, epi, acc);
         // the copy issued at the top of the next iteration refills this
         // stage: order this lane's reads and writes of it before that copy
         fence_async_smem();

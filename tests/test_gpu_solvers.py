@@ -39,7 +39,11 @@ def test_bicgstab_c1_vs_oracle_and_history(hz, oracle, ff):
     x, info = hz.zsolve(M, dev(b), tol=1e-10, maxit=2000, hist=hist)
     xo, io = oracle.bicgstab(A, b, tol=1e-10, maxit=2000)
     assert info.converged and io.status == 0
-    assert abs(info.iters - io.iters) <= 5
+    # the residual of BiCGStab is not monotone: near tol it wanders around
+    # 1e-9..1e-10 for several iterations, so the iteration at which it first
+    # drops below tol moves with rounding; the count is compared loosely and
+    # the arithmetic through the early history and the final answer
+    assert abs(info.iters - io.iters) <= max(5, 0.1 * io.iters)
     xg = host(x)
     assert true_relres(oracle, A, xg, b) <= 1e-10
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8

@@ -56,6 +56,18 @@ constexpr int kFlatGroup = HZ_FLAT_GROUP;       // entries per lane whose loads 
 constexpr int kFlatCap = 32 * kFlatU;           // entries per warp row block
 constexpr int kFlatRows = 32;                   // rows per row block (one per lane in phase 2)
 static_assert(kFlatU % kFlatGroup == 0, "kFlatU must be a multiple of kFlatGroup");
+#ifndef HZ_FLAT_CONTIG
+#define HZ_FLAT_CONTIG 0
+#endif
+constexpr bool kFlatContig = HZ_FLAT_CONTIG != 0;   // contiguous block range per CTA
+#ifndef HZ_FLAT_PIPE
+#define HZ_FLAT_PIPE 1
+#endif
+constexpr bool kFlatPipe = HZ_FLAT_PIPE != 0;       // column stream one group ahead
+#ifndef HZ_FLAT_MIN_BLOCKS
+#define HZ_FLAT_MIN_BLOCKS 1
+#endif
+constexpr int kFlatMinBlocks = HZ_FLAT_MIN_BLOCKS;  // resident CTAs per SM asked of the register allocator
 
 template <class T>
 struct MatView {
@@ -331,8 +343,21 @@ __device__ __forceinline__ void flat_rows_ff(const MatView<double2> &A, const fl
     const uint64_t pol = pol_evict_first();
     const int lane = threadIdx.x & 31;
     float4 *prod = slab + (threadIdx.x >> 5) * kFlatCap;
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < A.nfblk; b += nwarps) {
+    int b_first, b_end, b_step;
+    if constexpr (kFlatContig) {
+        // each CTA walks one contiguous range of row blocks, its warps
+        // interleaved, so neighbouring blocks (which gather overlapping x
+        // ranges under a bandwidth-reducing ordering) meet in the same L1
+        const int per = (A.nfblk + gridDim.x - 1) / gridDim.x;
+        b_first = blockIdx.x * per + (threadIdx.x >> 5);
+        b_end = min(A.nfblk, (blockIdx.x + 1) * per);
+        b_step = blockDim.x >> 5;
+    } else {
+        b_first = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        b_end = A.nfblk;
+        b_step = gridDim.x * (blockDim.x >> 5);
+    }
+    for (int b = b_first; b < b_end; b += b_step) {
         const int r0 = __ldg(A.fblk + b), r1 = __ldg(A.fblk + b + 1);
         const int kb = __ldg(A.rowptr + r0), ke = __ldg(A.rowptr + r1);
         const bool long_row = r1 - r0 == 1 && ke - kb > kFlatCap;
@@ -364,6 +389,86 @@ __device__ __forceinline__ void flat_rows_ff(const MatView<double2> &A, const fl
             __syncwarp();
             if (kend >= ke) break;
         }
+    }
+}
+
+// The same kernel with the column stream one group ahead: the columns of the
+// next group (in this chunk, the next chunk of a long row, or the warp's next
+// row block) are loaded while the current group's values and x gathers are in
+// flight, so a group waits for one memory latency instead of a column load
+// followed by a dependent gather.
+template <class Epi, int NV>
+__device__ __forceinline__ void flat_rows_ff_pipe(const MatView<double2> &A, const float4 *__restrict__ x,
+                                                  const Epi &epi, typename Epi::Acc (&acc)[NV], float4 *slab) {
+    const uint64_t pol = pol_evict_first();
+    const int lane = threadIdx.x & 31;
+    float4 *prod = slab + (threadIdx.x >> 5) * kFlatCap;
+    const int step = gridDim.x * (blockDim.x >> 5);
+    // group = entries [kg, kg + 32 * kFlatGroup) of chunk [kc, kend) of
+    // row block b = rows [r0, r1), entries [kb, ke)
+    struct Group {
+        int b, r0, r1, kb, ke, kc, kend, kg;
+    };
+    auto block_group = [&](int b) {
+        Group q;
+        q.b = b;
+        q.r0 = q.r1 = q.kb = q.ke = q.kc = q.kend = q.kg = 0;
+        if (b < A.nfblk) {
+            q.r0 = __ldg(A.fblk + b);
+            q.r1 = __ldg(A.fblk + b + 1);
+            q.kb = __ldg(A.rowptr + q.r0);
+            q.ke = __ldg(A.rowptr + q.r1);
+            q.kc = q.kg = q.kb;
+            q.kend = min(q.ke, q.kb + kFlatCap);
+        }
+        return q;
+    };
+    auto load_cols = [&](const Group &q, int (&c)[kFlatGroup]) {
+#pragma unroll
+        for (int u = 0; u < kFlatGroup; ++u) {
+            const int k = q.kg + lane + 32 * u;
+            c[u] = (q.b < A.nfblk && k < q.kend) ? ld_stream(A.col + k, pol) : -1;
+        }
+    };
+    Group cur = block_group(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    if (cur.b >= A.nfblk) return;
+    int cn[kFlatGroup];
+    load_cols(cur, cn);
+    f32x2 LS = 0ull, LC = 0ull;   // long-row carry (lane 0)
+    for (;;) {
+        int c[kFlatGroup];
+        float4 a[kFlatGroup], v[kFlatGroup];
+#pragma unroll
+        for (int u = 0; u < kFlatGroup; ++u) {
+            c[u] = cn[u];
+            const int k = cur.kg + lane + 32 * u;
+            a[u] = c[u] >= 0 ? ld_stream(A.vff + k, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // the next group, and its columns
+        const bool chunk_done = cur.kg + 32 * kFlatGroup >= cur.kend;
+        Group nxt = cur;
+        if (!chunk_done) {
+            nxt.kg = cur.kg + 32 * kFlatGroup;
+        } else if (cur.kend < cur.ke) {   // next pass over the same long row
+            nxt.kc = nxt.kg = cur.kend;
+            nxt.kend = min(cur.ke, cur.kend + kFlatCap);
+        } else {
+            nxt = block_group(cur.b + step);
+        }
+        load_cols(nxt, cn);
+#pragma unroll
+        for (int u = 0; u < kFlatGroup; ++u)
+            if (c[u] >= 0) prod[cur.kg - cur.kc + lane + 32 * u] = ff_cprod(a[u], v[u]);
+        if (chunk_done) {
+            __syncwarp();
+            const bool long_row = cur.r1 - cur.r0 == 1 && cur.ke - cur.kb > kFlatCap;
+            if (long_row && cur.kc == cur.kb) LS = LC = 0ull;
+            flat_row_sums<Epi, NV>(A, prod, cur.r0, cur.r1, cur.kc, cur.kend, cur.ke, long_row, LS, LC, epi, acc);
+            __syncwarp();
+        }
+        if (nxt.b >= A.nfblk) break;
+        cur = nxt;
     }
 }
 
@@ -542,7 +647,7 @@ __global__ void __launch_bounds__(kSpmvBlock, HZ_FF_MIN_BLOCKS) k_spmv_ff(MatVie
 
 // the block-flat double-float kernel (kFlatThreads threads, row blocks)
 template <class Epi>
-__global__ void __launch_bounds__(kFlatThreads) k_spmv_ffb(MatView<double2> A, const float4 *__restrict__ x, Epi epi,
+__global__ void __launch_bounds__(kFlatThreads, kFlatMinBlocks) k_spmv_ffb(MatView<double2> A, const float4 *__restrict__ x, Epi epi,
                                                            RedScratch red) {
     __shared__ float4 prod[(kFlatThreads / 32) * kFlatCap];   // one slab per warp
     constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
@@ -552,7 +657,8 @@ __global__ void __launch_bounds__(kFlatThreads) k_spmv_ffb(MatView<double2> A, c
     typename Epi::Acc acc[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
-    flat_rows_ff<Epi, NV>(A, x, epi, acc, prod);
+    if constexpr (kFlatPipe) flat_rows_ff_pipe<Epi, NV>(A, x, epi, acc, prod);
+    else flat_rows_ff<Epi, NV>(A, x, epi, acc, prod);
     if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
 }
 

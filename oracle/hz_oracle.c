@@ -173,12 +173,43 @@ typedef struct {
 
 static double z_norm(int64_t n, const oz *x) { return or_dznrm2(n, x); }
 
-int or_bicgstab(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *val,
-                const oz *b, oz *x, double tol, int32_t maxit, double *hist, or_info *info)
+/* z_i = x_i y_i: the element-wise product of Section 5 */
+void or_zmul_elementwise(int64_t n, const oz *x, const oz *y, oz *z)
+{
+    for (int64_t i = 0; i < n; ++i) z[i] = z_mul(x[i], y[i]);
+}
+
+/* Jacobi (diagonal) preconditioner of Section 7's "P-" solvers, stored as
+ * its inverse: dinv_i = 1 / a_ii, where a_ii is the sum of the stored
+ * entries of row i in column i; a row whose diagonal is absent or zero gets
+ * dinv_i = 1 (it is left unscaled). */
+void or_jacobi_dinv(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *val, oz *dinv)
+{
+    for (int32_t i = 0; i < n; ++i) {
+        oz d = {0.0, 0.0};
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            if (col[k] == i) d = z_add(d, val[k]);
+        if (d.re == 0.0 && d.im == 0.0) { dinv[i].re = 1.0; dinv[i].im = 0.0; }
+        else { oz one = {1.0, 0.0}; dinv[i] = z_div(one, d); }
+    }
+}
+
+/* BiCGStab right-preconditioned by M^{-1} = diag(dinv) (dinv = NULL: no
+ * preconditioner, and then every step below is the unpreconditioned
+ * algorithm unchanged).  The textbook right-preconditioned form: the search
+ * directions are mapped through M^{-1} before each product with A,
+ *   p^ = M^{-1} p,  v = A p^,  s^ = M^{-1} s,  t = A s^,  x += alpha p^ + omega s^,
+ * so the residuals r, s are those of the original system A x = b and the
+ * stopping test is unchanged. */
+int or_bicgstab_pc(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *val,
+                   const oz *dinv, const oz *b, oz *x, double tol, int32_t maxit, double *hist,
+                   or_info *info)
 {
     oz *r = calloc((size_t)n, sizeof(oz)), *rh = calloc((size_t)n, sizeof(oz));
     oz *p = calloc((size_t)n, sizeof(oz)), *v = calloc((size_t)n, sizeof(oz));
     oz *s = calloc((size_t)n, sizeof(oz)), *t = calloc((size_t)n, sizeof(oz));
+    oz *ph = dinv ? calloc((size_t)n, sizeof(oz)) : p;   /* M^{-1} p (p itself without M) */
+    oz *sh = dinv ? calloc((size_t)n, sizeof(oz)) : s;   /* M^{-1} s */
     double nb = z_norm(n, b);
     int32_t it = 0, status = OR_NOT_CONVERGED, restarts = 0;
     double rel = 0.0;
@@ -188,6 +219,7 @@ int or_bicgstab(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *
         info->iters = 0; info->status = OR_OK; info->restarts = 0;
         info->relres_rec = 0.0; info->relres_true = 0.0;
         if (hist) hist[0] = 0.0;
+        if (dinv) { free(ph); free(sh); }
         free(r); free(rh); free(p); free(v); free(s); free(t);
         return OR_OK;
     }
@@ -212,7 +244,8 @@ int or_bicgstab(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *
                 beta = z_mul(z_div(rho, rho_old), z_div(alpha, omega));
                 for (int32_t i = 0; i < n; ++i)
                     p[i] = z_add(r[i], z_mul(beta, z_sub(p[i], z_mul(omega, v[i]))));
-                or_zspmv(n, rowptr, col, val, p, v);
+                if (dinv) or_zmul_elementwise(n, dinv, p, ph);
+                or_zspmv(n, rowptr, col, val, ph, v);
                 or_zdotc(n, rh, v, &sig);
                 if (sig.re == 0.0 && sig.im == 0.0) { status = OR_BREAKDOWN; break; }
                 alpha = z_div(rho, sig);
@@ -220,18 +253,19 @@ int or_bicgstab(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *
                 rel = z_norm(n, s) / nb;
                 if (!isfinite(rel)) { status = OR_NAN; break; }
                 if (rel <= tol) {        /* half-step exit */
-                    for (int32_t i = 0; i < n; ++i) x[i] = z_add(x[i], z_mul(alpha, p[i]));
+                    for (int32_t i = 0; i < n; ++i) x[i] = z_add(x[i], z_mul(alpha, ph[i]));
                     if (hist) hist[it] = rel;
                     status = OR_OK;
                     break;
                 }
-                or_zspmv(n, rowptr, col, val, s, t);
+                if (dinv) or_zmul_elementwise(n, dinv, s, sh);
+                or_zspmv(n, rowptr, col, val, sh, t);
                 or_zdotc(n, t, s, &ts);
                 or_zdotc(n, t, t, &tt);
                 if (tt.re == 0.0 && tt.im == 0.0) { status = OR_BREAKDOWN; break; }
                 omega = z_div(ts, tt);
                 for (int32_t i = 0; i < n; ++i) {
-                    x[i] = z_add(x[i], z_add(z_mul(alpha, p[i]), z_mul(omega, s[i])));
+                    x[i] = z_add(x[i], z_add(z_mul(alpha, ph[i]), z_mul(omega, sh[i])));
                     r[i] = z_sub(s[i], z_mul(omega, t[i]));
                 }
                 rho_old = rho;
@@ -257,8 +291,15 @@ int or_bicgstab(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *
     info->iters = it;
     info->status = status;
     info->restarts = restarts;
+    if (dinv) { free(ph); free(sh); }
     free(r); free(rh); free(p); free(v); free(s); free(t);
     return status;
+}
+
+int or_bicgstab(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *val,
+                const oz *b, oz *x, double tol, int32_t maxit, double *hist, or_info *info)
+{
+    return or_bicgstab_pc(n, rowptr, col, val, NULL, b, x, tol, maxit, hist, info);
 }
 
 /* ---------------------------------------------------------------------- */

@@ -47,6 +47,10 @@ def load():
         lib.or_zcopy.argtypes = [i64, P, P]
         lib.or_bicgstab.argtypes = [i32, P, P, P, P, P, f64, i32, P, P]
         lib.or_bicgstab.restype = C.c_int
+        lib.or_bicgstab_pc.argtypes = [i32, P, P, P, P, P, P, f64, i32, P, P]
+        lib.or_bicgstab_pc.restype = C.c_int
+        lib.or_jacobi_dinv.argtypes = [i32, P, P, P, P]
+        lib.or_zmul_elementwise.argtypes = [i64, P, P, P]
         lib.or_cbicgstab.argtypes = [i32, P, P, P, P, P, f32, i32, P]
         lib.or_cbicgstab.restype = i32
         lib.or_refine_mixed.argtypes = [i32, P, P, P, P, P, P, f64, f32, i32, i32, P, P, P]
@@ -147,16 +151,40 @@ def zcopy(x):
     return y
 
 
-def bicgstab(A, b, x0=None, tol=1e-10, maxit=2000, history=True):
-    """Preconditioner-free BiCGStab in binary64; returns (x, OracleInfo)."""
+def jacobi_dinv(A):
+    """Inverse diagonal of A (Section 7's Jacobi preconditioner): 1 / a_ii, or 1
+    where the diagonal is absent or zero."""
+    lib = load()
+    d = np.zeros(A.n, dtype=np.complex128)
+    rp, cl, vl = _i(A.rowptr), _i(A.col), _z(A.val)
+    lib.or_jacobi_dinv(A.n, _p(rp), _p(cl), _p(vl), _p(d))
+    return d
+
+
+def zmul_elementwise(x, y):
+    """z_i = x_i y_i (Section 5's element-wise product)."""
+    lib = load()
+    x, y = _z(x), _z(y)
+    z = np.zeros_like(x)
+    lib.or_zmul_elementwise(x.size, _p(x), _p(y), _p(z))
+    return z
+
+
+def bicgstab(A, b, x0=None, tol=1e-10, maxit=2000, history=True, precond=None):
+    """BiCGStab in binary64; returns (x, OracleInfo).  precond None (the
+    preconditioner-free method) or "jacobi" (right-preconditioned by the
+    inverse diagonal)."""
     lib = load()
     b = _z(b)
     x = np.zeros(A.n, dtype=np.complex128) if x0 is None else _z(x0).copy()
     hist = np.full(maxit + 1, np.nan) if history else None
     info = _OrInfo()
     rp, cl, vl = _i(A.rowptr), _i(A.col), _z(A.val)
-    lib.or_bicgstab(A.n, _p(rp), _p(cl), _p(vl), _p(b), _p(x), float(tol), int(maxit),
-                    _p(hist) if history else None, C.byref(info))
+    if precond not in (None, "none", "jacobi"):
+        raise ValueError("precond must be None or 'jacobi'")
+    dinv = jacobi_dinv(A) if precond == "jacobi" else None
+    lib.or_bicgstab_pc(A.n, _p(rp), _p(cl), _p(vl), _p(dinv) if dinv is not None else None, _p(b), _p(x),
+                       float(tol), int(maxit), _p(hist) if history else None, C.byref(info))
     out = OracleInfo(info.iters, info.status, info.restarts, info.relres_rec, info.relres_true)
     if history:
         out.hist = hist[: info.iters + 1].copy()

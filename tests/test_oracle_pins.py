@@ -205,6 +205,83 @@ def test_bicgstab_special_cases(oracle):
     assert info.status == 6
 
 
+# --------------------------------------------------------------------------- Jacobi
+def test_zmul_elementwise_exact(oracle):
+    """Section 5's element-wise product on small integers: exact."""
+    rng = np.random.default_rng(31)
+    x = rng.integers(-9, 10, 40) + 1j * rng.integers(-9, 10, 40)
+    y = rng.integers(-9, 10, 40) + 1j * rng.integers(-9, 10, 40)
+    assert np.array_equal(oracle.zmul_elementwise(x, y), x * y)
+
+
+def test_jacobi_dinv_rule(oracle):
+    """1 / (sum of the diagonal entries of the row); 1 where there is none or it is 0."""
+    S = sp.lil_matrix((4, 4), dtype=np.complex128)
+    S[0, 0] = 2 + 2j
+    S[0, 1] = 5
+    S[1, 0] = 1            # row 1 has no diagonal
+    S[2, 2] = 0.0          # explicit zero
+    S[3, 3] = 4.0
+    A = W.CSR.from_scipy(S.tocsr())
+    A.col = A.col.copy()
+    d = oracle.jacobi_dinv(A)
+    assert np.allclose(d, [1 / (2 + 2j), 1, 1, 0.25], rtol=1e-15, atol=0)
+    # a diagonal split over two stored entries is summed
+    rp = np.array([0, 2], dtype=np.int32)
+    A2 = W.CSR(1, rp, np.array([0, 0], dtype=np.int32), np.array([1 + 1j, 3 - 1j]))
+    assert oracle.jacobi_dinv(A2)[0] == 0.25
+
+
+def test_jacobi_diagonal_matrix_one_step(oracle):
+    """A = D: the right-preconditioned operator is I, so the first half step
+    exits with x = D^-1 b (closed form)."""
+    rng = np.random.default_rng(32)
+    dvals = rng.uniform(0.5, 4, 60) * np.exp(1j * rng.uniform(0, 2 * np.pi, 60))
+    A = W.CSR.from_scipy(sp.diags(dvals, format="csr").astype(np.complex128))
+    b = K.vectors(60, 33)[0]
+    x, info = oracle.bicgstab(A, b, tol=1e-12, precond="jacobi")
+    assert info.status == 0 and info.iters == 1
+    assert np.allclose(x, b / dvals, rtol=1e-14, atol=0)
+    # without the preconditioner the same system needs many iterations
+    _, info0 = oracle.bicgstab(A, b, tol=1e-12)
+    assert info0.iters > 5
+
+
+def test_jacobi_unit_diagonal_is_unpreconditioned(oracle):
+    """With a_ii = 1 for every row, D^-1 = I and the preconditioned iteration
+    is the plain one: identical histories and solutions."""
+    A = W.fd_helmholtz_box(6, kh=0.5, damping=0.05)
+    S = A.to_scipy()
+    Dinv = sp.diags(1.0 / S.diagonal())
+    A1 = W.CSR.from_scipy((Dinv @ S).tocsr())     # row-scaled: unit diagonal
+    b = K.vectors(A1.n, 34)[0]
+    x0, i0 = oracle.bicgstab(A1, b, tol=1e-10)
+    x1, i1 = oracle.bicgstab(A1, b, tol=1e-10, precond="jacobi")
+    assert i0.iters == i1.iters and np.array_equal(i0.hist, i1.hist) and np.array_equal(x0, x1)
+
+
+def test_jacobi_dense_lu_and_column_scaling_invariance(oracle):
+    """Against dense LU; and scaling the columns of A by S leaves the Jacobi
+    operator A S (D S)^-1 = A D^-1 unchanged, so the iteration matches the
+    unscaled one and the solution maps back as x_scaled = S^-1 x."""
+    A = W.fd_helmholtz_box(8, kh=0.5, damping=0.05)
+    b = K.vectors(A.n, 35)[0]
+    x, info = oracle.bicgstab(A, b, tol=1e-11, precond="jacobi")
+    x_lu = np.linalg.solve(A.to_scipy().toarray(), b)
+    assert info.status == 0 and np.linalg.norm(x - x_lu) <= 1e-8 * np.linalg.norm(x_lu)
+    rng = np.random.default_rng(36)
+    sc = rng.uniform(0.01, 100, A.n) * np.exp(1j * rng.uniform(0, 2 * np.pi, A.n))
+    As = W.CSR.from_scipy((A.to_scipy() @ sp.diags(sc)).tocsr())
+    xs, infs = oracle.bicgstab(As, b, tol=1e-11, precond="jacobi")
+    assert abs(infs.iters - info.iters) <= 1
+    n = min(len(info.hist), len(infs.hist), 10)
+    assert np.allclose(infs.hist[:n], info.hist[:n], rtol=1e-9, atol=0)
+    assert np.linalg.norm(sc * xs - x) <= 1e-8 * np.linalg.norm(x)
+    # the unpreconditioned solver sees the scaling: it needs many more iterations
+    _, i0 = oracle.bicgstab(As, b, tol=1e-11, maxit=3000)
+    assert i0.iters > 2 * infs.iters
+
+
 def test_mixed_refinement(oracle):
     A, b, _ = W.c1_small_fd()
     x, d = oracle.refine_mixed(A, b, tol=1e-10)

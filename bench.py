@@ -242,7 +242,8 @@ def compare_modes(hz, torch, full_c4, maxit):
 
     Every system is solved (x0 = 0) by: the binary64 solver (CSR-vector
     SpMV), the double-float complex128 solver (block-flat SpMV), the mixed
-    solver (complex64 inner BiCGStab, binary64 outer refinement) and, for all
+    solver (complex64 inner BiCGStab, binary64 outer refinement), the
+    double-float solver with Jacobi right preconditioning and, for all
     systems at once, the persistent batched binary64 solver.  Times are CUDA
     events around each call, after one untimed call of each kind (graph
     capture).  Speedups are over the systems every variant solved."""
@@ -265,14 +266,14 @@ def compare_modes(hz, torch, full_c4, maxit):
         e1.synchronize()
         return out, e0.elapsed_time(e1)
 
-    variants = {"fp64_binary64": ("csr", "fp64"), "fp64_double_float": ("ffflat", "fp64"),
-                "mixed": ("csr", "mixed")}
+    variants = {"fp64_binary64": ("csr", "fp64", "none"), "fp64_double_float": ("ffflat", "fp64", "none"),
+                "mixed": ("csr", "mixed", "none"), "fp64_double_float_jacobi": ("ffflat", "fp64", "jacobi")}
     res = {k: [] for k in variants}
     for M, b in zip(mats, bs):
-        for key, (kind, mode) in variants.items():
+        for key, (kind, mode, pc) in variants.items():
             M.set_spmv(kind, M.props()["group"] if kind == "csr" else 0)
-            hz.zsolve(M, b, tol=1e-10, maxit=maxit, mode=mode)          # graph capture
-            (_, info), ms = timed(lambda: hz.zsolve(M, b, tol=1e-10, maxit=maxit, mode=mode))
+            hz.zsolve(M, b, tol=1e-10, maxit=maxit, mode=mode, precond=pc)          # graph capture
+            (_, info), ms = timed(lambda: hz.zsolve(M, b, tol=1e-10, maxit=maxit, mode=mode, precond=pc))
             res[key].append((ms, info))
     hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit)
     (_, binfos), bms = timed(lambda: hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit))
@@ -297,12 +298,9 @@ def compare_modes(hz, torch, full_c4, maxit):
                            "max_relres_true": max(i.relres_true for i in binfos)}
     base = out["fp64_binary64"]["s_on_common"]
     out["speedup_vs_fp64_binary64_on_common"] = {
-        "fp64_double_float": base / max(out["fp64_double_float"]["s_on_common"], 1e-12),
-        "mixed": base / max(out["mixed"]["s_on_common"], 1e-12)}
+        k: base / max(out[k]["s_on_common"], 1e-12) for k in variants if k != "fp64_binary64"}
     out["speedup_vs_fp64_binary64_all_systems"] = {
-        "fp64_double_float": out["fp64_binary64"]["s_total"] / out["fp64_double_float"]["s_total"],
-        "mixed": out["fp64_binary64"]["s_total"] / out["mixed"]["s_total"],
-        "batched_fp64": out["fp64_binary64"]["s_total"] / out["batched_fp64"]["s_total"]}
+        k: out["fp64_binary64"]["s_total"] / out[k]["s_total"] for k in list(variants)[1:] + ["batched_fp64"]}
     for M in mats:
         M.close()
     return out

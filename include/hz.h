@@ -76,6 +76,15 @@ enum {
     HZ_MODE_MIXED = 1u       /* complex64 inner BiCGStab + complex128 iterative refinement */
 };
 
+/* preconditioners (Section 7 names its solvers P-BiCGSTAB etc. without
+ * saying which preconditioner; none is the default reading) */
+enum {
+    HZ_PRECOND_NONE = 0u,
+    HZ_PRECOND_JACOBI = 1u   /* right preconditioning by the inverse diagonal: 1 / a_ii, or 1 where
+                                row i has no (or a zero) diagonal; the stopping test stays on the
+                                residual of A x = b */
+};
+
 /* SpMV kernel variants reported by hz_mat_query */
 enum {
     HZ_SPMV_CSR_VECTOR = 0,  /* a group of `group` lanes per row */
@@ -222,6 +231,13 @@ HZ_API hz_status hz_zscal(int64_t n, const hz_z *d_alpha, hz_z *d_x, void *strea
 /* y_i = x_i (Section 5, assign). */
 HZ_API hz_status hz_zcopy(int64_t n, const hz_z *d_x, hz_z *d_y, void *stream);
 
+/*
+ * z_i = x_i * y_i (Section 5, element-wise product; with y = D^-1 it is the
+ * Jacobi preconditioner step z = D^-1 r).  Vectors of n complex128 entries;
+ * z may equal x or y.
+ */
+HZ_API hz_status hz_zmul_elementwise(int64_t n, const hz_z *d_x, const hz_z *d_y, hz_z *d_z, void *stream);
+
 /* y_i = conj(x_i); y may equal x. */
 HZ_API hz_status hz_zconj(int64_t n, const hz_z *d_x, hz_z *d_y, void *stream);
 
@@ -243,6 +259,7 @@ typedef struct {
     int32_t max_outer;       /* mixed: refinement step cap */
     int32_t x0_is_zero;      /* 1: ignore d_x on entry and start from x0 = 0 */
     double *d_hist;          /* optional device array of maxit+1 doubles: residual history */
+    uint32_t precond;        /* HZ_PRECOND_NONE or HZ_PRECOND_JACOBI */
 } hz_solve_opts;
 
 /*
@@ -267,7 +284,15 @@ typedef struct {
 HZ_API hz_status hz_zsolve(hz_mat *A, const hz_z *d_b, hz_z *d_x, double tol, int32_t maxit,
                            uint32_t mode, hz_info *h_info, void *stream);
 
-/* hz_zsolve with every option explicit (opts must not be NULL). */
+/*
+ * hz_zsolve with every option explicit (opts must not be NULL).
+ * With precond = HZ_PRECOND_JACOBI the handle builds, on first use, the
+ * column-scaled operator A D^-1 (D = diag(A), a second set of values the
+ * handle owns, with the same SpMV copies as A) and solves A D^-1 y = b from
+ * y0 = D x0, returning x = D^-1 y; the residuals and the stopping test are
+ * those of A x = b.  The scaled copy is rebuilt after hz_mat_refresh_values
+ * or hz_mat_set_diag.
+ */
 HZ_API hz_status hz_zsolve_opts(hz_mat *A, const hz_z *d_b, hz_z *d_x,
                                 const hz_solve_opts *opts, hz_info *h_info, void *stream);
 

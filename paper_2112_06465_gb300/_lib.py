@@ -20,6 +20,7 @@ SOLVE_OUTCOMES = (HZ_OK, HZ_NOT_CONVERGED, HZ_BREAKDOWN, HZ_ERR_NAN)
 
 HZ_FLAG_VALIDATE, HZ_FLAG_SELL, HZ_FLAG_C64, HZ_FLAG_AUTOTUNE, HZ_FLAG_FF = 1, 2, 4, 8, 16
 HZ_MODE_FP64, HZ_MODE_MIXED = 0, 1
+HZ_PRECOND_NONE, HZ_PRECOND_JACOBI = 0, 1
 HZ_SPMV_CSR_VECTOR, HZ_SPMV_SELL, HZ_SPMV_FF, HZ_SPMV_SELL_FF, HZ_SPMV_FF_FLAT, HZ_SPMV_FF_TMA = 0, 1, 2, 3, 4, 5
 
 # every symbol include/hz.h declares
@@ -29,7 +30,7 @@ EXPORTS = (
     "hz_cspmv", "hz_zdotc", "hz_zdotu", "hz_dznrm2", "hz_zaxpy", "hz_zscal", "hz_zcopy",
     "hz_zconj", "hz_zsolve", "hz_zsolve_opts", "hz_zsolve_batched", "hz_outer_on_pattern",
     "hz_mat_set_diag", "hz_diag_grad", "hz_last_error", "hz_version", "hz_zdotc_noalloc",
-    "hz_mat_check",
+    "hz_mat_check", "hz_zmul_elementwise",
 )
 
 
@@ -45,7 +46,7 @@ class hz_info(C.Structure):
 class hz_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("mode", C.c_uint32),
                 ("inner_tol", C.c_float), ("inner_maxit", C.c_int32), ("max_outer", C.c_int32),
-                ("x0_is_zero", C.c_int32), ("d_hist", C.c_void_p)]
+                ("x0_is_zero", C.c_int32), ("d_hist", C.c_void_p), ("precond", C.c_uint32)]
 
 
 class hz_mat_props(C.Structure):
@@ -78,6 +79,7 @@ def load():
         "hz_mat_destroy": [P],
         "hz_mat_query": [P, C.POINTER(hz_mat_props)],
         "hz_mat_check": [P, P],
+        "hz_zmul_elementwise": [i64, P, P, P, P],
         "hz_mat_set_spmv": [P, i32, i32],
         "hz_mat_refresh_values": [P, P],
         "hz_zspmv": [P, P, P, P],

@@ -50,6 +50,8 @@ struct Ctl {
     int max_outer;
     float inner_tol;
     int inner_maxit;
+    const double2 *pre_d;      // Jacobi: y0 = D x0 (null without a preconditioner)
+    const double2 *pre_dinv;   // Jacobi: x = D^-1 y
 };
 
 template <class St>
@@ -305,9 +307,9 @@ __global__ void __launch_bounds__(kVecBlock) k_bicg_xr(int n, StateOf<V> *st, co
 template <class V>
 __global__ void __launch_bounds__(kVecBlock) k_init_x(int n, const Ctl *ctl, V *__restrict__ xw) {
     if (ctl->restart) return;
-    const double2 *x0 = ctl->x;
+    const double2 *x0 = ctl->x, *pd = ctl->pre_d;
     const bool zero = ctl->x0_zero != 0;
-    vec_tiles(n, [&](int i) { xw[i] = zero ? Ar<V>::zero() : Ar<V>::from_c128(x0[i]); });
+    vec_tiles(n, [&](int i) { xw[i] = zero ? Ar<V>::zero() : Ar<V>::from_c128(pd ? cmul(x0[i], pd[i]) : x0[i]); });
 }
 
 // init epilogue: r = b - A x, rh = r, p = v = 0, ||r||^2, ||b||^2
@@ -385,10 +387,14 @@ template <class V>
 __global__ void __launch_bounds__(kVecBlock) k_copy_out(int n, const Ctl *ctl, Info *info,
                                                         const V *__restrict__ xw, const int *fault) {
     double2 *x = ctl->x;
+    const double2 *pdi = ctl->pre_dinv;
     const bool zero = info->zero_x != 0;
     // an expired bounded wait in an SpMV of this solve voids the result
     if (fault && blockIdx.x == 0 && threadIdx.x == 0 && *(volatile const int *)fault) info->status = HZ_ERR_TIMEOUT;
-    vec_tiles(n, [&](int i) { x[i] = zero ? make_double2(0.0, 0.0) : Ar<V>::to_c128(xw[i]); });
+    vec_tiles(n, [&](int i) {
+        const double2 y = Ar<V>::to_c128(xw[i]);
+        x[i] = zero ? make_double2(0.0, 0.0) : (pdi ? cmul(y, pdi[i]) : y);
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -470,9 +476,9 @@ __global__ void __launch_bounds__(kVecBlock) k_mixed_start(int n, const Ctl *ctl
         ost->outer = 0; ost->done = 0; ost->status = HZ_NOT_CONVERGED; ost->zero_x = 0;
         *total_inner = 0;
     }
-    const double2 *x0 = ctl->x;
+    const double2 *x0 = ctl->x, *pd = ctl->pre_d;
     const bool zero = ctl->x0_zero != 0;
-    vec_tiles(n, [&](int i) { xw[i] = zero ? Ar<V>::zero() : Ar<V>::from_c128(x0[i]); });
+    vec_tiles(n, [&](int i) { xw[i] = zero ? Ar<V>::zero() : Ar<V>::from_c128(pd ? cmul(x0[i], pd[i]) : x0[i]); });
 }
 
 // x += d (d from the complex64 inner solve)
@@ -772,12 +778,20 @@ extern "C" HZ_API hz_status hz_zsolve_opts(hz_mat *A, const hz_z *d_b, hz_z *d_x
     HZ_CHECK(o->mode == HZ_MODE_FP64 || o->mode == HZ_MODE_MIXED, "hz_zsolve: unknown mode");
     HZ_CHECK(o->maxit >= 0, "hz_zsolve: negative maxit");
     HZ_CHECK(o->tol >= 0.0, "hz_zsolve: negative tol");
+    HZ_CHECK(o->precond == HZ_PRECOND_NONE || o->precond == HZ_PRECOND_JACOBI, "hz_zsolve: unknown preconditioner");
     *h_info = hz_info{};
     if (A->n == 0) { h_info->status = HZ_OK; return HZ_OK; }
     HZ_CHECK(d_b && d_x, "hz_zsolve: null vector");
     cudaStream_t s = (cudaStream_t)stream;
+    hz_mat *op = A;   // the operator the iteration runs on
+    if (o->precond == HZ_PRECOND_JACOBI) {
+        HZ_TRY(ensure_jacobi(A, s));
+        op = A->jac;
+        op->spmv_kind = A->spmv_kind;   // follow the caller's choice of SpMV variant
+        op->group = A->group;
+    }
     Solver *S = nullptr;
-    HZ_TRY(get_solver(A, o->mode, s, &S));
+    HZ_TRY(get_solver(op, o->mode, s, &S));
     Ctl c{};
     c.tol = o->tol;
     c.b = (const double2 *)d_b;
@@ -789,6 +803,8 @@ extern "C" HZ_API hz_status hz_zsolve_opts(hz_mat *A, const hz_z *d_b, hz_z *d_x
     c.max_outer = o->max_outer > 0 ? o->max_outer : 50;
     c.inner_tol = o->inner_tol > 0.f ? o->inner_tol : 1e-5f;
     c.inner_maxit = o->inner_maxit > 0 ? o->inner_maxit : 1000;
+    c.pre_d = op != A ? A->jac_d : nullptr;
+    c.pre_dinv = op != A ? A->jac_dinv : nullptr;
     *S->hctl = c;
     HZ_CUDA(cudaGraphLaunch(S->exec, s));
     HZ_CUDA(cudaStreamSynchronize(s));

@@ -511,4 +511,15 @@ struct hz_mat {
     int32_t *diag_pos = nullptr;
     // solver state (one per mode), created on first solve
     void *solver[2] = {nullptr, nullptr};
+    // Jacobi right preconditioning: the column-scaled operator A D^-1 as a
+    // handle of its own (borrowing rowptr/col), its values, and D, D^-1
+    hz_mat *jac = nullptr;
+    double2 *jac_val = nullptr;
+    double2 *jac_d = nullptr;
+    double2 *jac_dinv = nullptr;
 };
+
+namespace hz {
+hz_status ensure_jacobi(hz_mat *A, cudaStream_t s);   // build A->jac on first use
+void free_jacobi(hz_mat *A);                          // drop it (values changed, destroy)
+}  // namespace hz

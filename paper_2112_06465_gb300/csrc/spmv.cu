@@ -397,6 +397,7 @@ extern "C" HZ_API hz_status hz_mat_destroy(hz_mat *A) {
     if (!A) return HZ_OK;
     cudaDeviceSynchronize();
     free_solvers(A);
+    free_jacobi(A);
     cudaFree(A->own_rowptr);
     cudaFree(A->own_col);
     cudaFree(A->sell_chunk_off);
@@ -449,6 +450,7 @@ extern "C" HZ_API hz_status hz_mat_check(const hz_mat *A, void *stream) {
 
 extern "C" HZ_API hz_status hz_mat_refresh_values(hz_mat *A, void *stream) {
     HZ_CHECK(A, "hz_mat_refresh_values: null handle");
+    free_jacobi(A);   // the scaled copy is rebuilt from the new values on the next use
     return refresh(A, (cudaStream_t)stream);
 }
 

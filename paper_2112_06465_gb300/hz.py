@@ -193,6 +193,14 @@ def zcopy(x, y=None):
     return y
 
 
+def zmul_elementwise(x, y, z=None):
+    """z_i = x_i y_i (z may be x or y)."""
+    x, y = _pair(x, y)
+    z = torch.empty_like(x) if z is None else _vec(z, name="z")
+    check(_L.hz_zmul_elementwise(x.numel(), _ptr(x), _ptr(y), _ptr(z), _stream()))
+    return z
+
+
 def zconj(x, y=None):
     """y = conj(x) (y may be x)."""
     x = _vec(x, name="x")
@@ -224,14 +232,17 @@ def _info(i: hz_info) -> SolveInfo:
 
 
 def zsolve(A: Matrix, b, x=None, tol=1e-10, maxit=2000, mode="fp64", hist=None,
-           inner_tol=1e-5, inner_maxit=1000, max_outer=50):
+           inner_tol=1e-5, inner_maxit=1000, max_outer=50, precond="none"):
     """Solve A x = b with BiCGStab on the device; returns (x, SolveInfo).
 
     x (optional) holds x0 and receives the solution; mode is "fp64" or
-    "mixed"; hist (optional float64 device tensor of maxit+1 entries)
-    receives the residual history.  Non-convergence is reported in the
-    info, not raised.
+    "mixed"; precond is "none" or "jacobi" (right preconditioning by the
+    inverse diagonal); hist (optional float64 device tensor of maxit+1
+    entries) receives the residual history.  Non-convergence is reported in
+    the info, not raised.
     """
+    if precond not in ("none", "jacobi"):
+        raise ValueError("precond must be 'none' or 'jacobi'")
     b = _vec(b, name="b")
     x0_zero = x is None
     if x is None:
@@ -246,6 +257,7 @@ def zsolve(A: Matrix, b, x=None, tol=1e-10, maxit=2000, mode="fp64", hist=None,
     o.max_outer = int(max_outer)
     o.x0_is_zero = 1 if x0_zero else 0
     o.d_hist = hist.data_ptr() if hist is not None else None
+    o.precond = _lib.HZ_PRECOND_JACOBI if precond == "jacobi" else _lib.HZ_PRECOND_NONE
     if hist is not None and (hist.dtype != torch.float64 or hist.numel() < maxit + 1):
         raise ValueError("hist must be a float64 device tensor with maxit+1 entries")
     info = hz_info()

@@ -303,6 +303,149 @@ int or_bicgstab(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *
 }
 
 /* ---------------------------------------------------------------------- */
+/* BiCGStab(l) of Sleijpen and Fokkema (Section 7 lists P-BiCGSTAB(l) among
+ * the paper's solvers; no preconditioner here, as for BiCGStab).  Each outer
+ * iteration takes l BiCG steps that build r_0..r_l and u_0..u_l with
+ * r_{i+1} = A r_i and u_{i+1} = A u_i, then a minimal-residual step: r_0 is
+ * replaced by the residual of the least-squares fit of r_0 by r_1..r_l,
+ * computed by modified Gram-Schmidt on r_1..r_l.  Hermitian inner products
+ * throughout.  The loop stops when ||r_0|| <= tol ||b||, tested after every
+ * BiCG step and after the minimal-residual step; maxit counts BiCG steps and
+ * is checked before each outer iteration.  hist[k] holds ||r_0|| / ||b||
+ * after the k-th BiCG step.  Breakdown: rho_0 = 0, <r^, u_{j+1}> = 0, a
+ * zero Gram-Schmidt norm, or omega = 0.  As for BiCGStab, the true residual
+ * is recomputed at exit and the iteration restarts once if it misses tol. */
+int or_bicgstabl(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *val, int32_t ell,
+                 const oz *b, oz *x, double tol, int32_t maxit, double *hist, or_info *info)
+{
+    const size_t nn = (size_t)n;
+    oz *R = calloc((size_t)(ell + 1) * nn, sizeof(oz)), *U = calloc((size_t)(ell + 1) * nn, sizeof(oz));
+    oz *rh = calloc(nn, sizeof(oz)), *tmp = calloc(nn, sizeof(oz));
+    oz tau[9][9], gp[9], g[9], gpp[9];
+    double sigma[9];
+    double nb = z_norm(n, b), rel = 0.0;
+    int32_t it = 0, status = OR_NOT_CONVERGED, restarts = 0;
+#define RV(i) (R + (size_t)(i) * nn)
+#define UV(i) (U + (size_t)(i) * nn)
+    if (ell < 1 || ell > 8) {
+        free(R); free(U); free(rh); free(tmp);
+        return -1;
+    }
+    if (nb == 0.0) {
+        memset(x, 0, nn * sizeof(oz));
+        info->iters = 0; info->status = OR_OK; info->restarts = 0;
+        info->relres_rec = 0.0; info->relres_true = 0.0;
+        if (hist) hist[0] = 0.0;
+        free(R); free(U); free(rh); free(tmp);
+        return OR_OK;
+    }
+    for (;;) {
+        oz rho0 = {1, 0}, alpha = {0, 0}, omega = {1, 0};
+        or_zspmv(n, rowptr, col, val, x, RV(0));
+        for (int32_t i = 0; i < n; ++i) { RV(0)[i] = z_sub(b[i], RV(0)[i]); rh[i] = RV(0)[i]; }
+        memset(UV(0), 0, nn * sizeof(oz));
+        rel = z_norm(n, RV(0)) / nb;
+        if (hist && it == 0) hist[0] = rel;
+        if (!isfinite(rel)) status = OR_NAN;
+        else if (rel <= tol) status = OR_OK;
+        else status = OR_NOT_CONVERGED;
+        while (status == OR_NOT_CONVERGED && it < maxit) {
+            int done = 0;
+            rho0 = z_mul((oz){-omega.re, -omega.im}, rho0);
+            /* BiCG part */
+            for (int32_t j = 0; j < ell && !done; ++j) {
+                oz rho1, gam, beta;
+                if (rho0.re == 0.0 && rho0.im == 0.0) { status = OR_BREAKDOWN; done = 1; break; }
+                or_zdotc(n, rh, RV(j), &rho1);
+                beta = z_mul(alpha, z_div(rho1, rho0));
+                rho0 = rho1;
+                for (int32_t i = 0; i <= j; ++i)
+                    for (int32_t e = 0; e < n; ++e) UV(i)[e] = z_sub(RV(i)[e], z_mul(beta, UV(i)[e]));
+                or_zspmv(n, rowptr, col, val, UV(j), UV(j + 1));
+                or_zdotc(n, rh, UV(j + 1), &gam);
+                if (gam.re == 0.0 && gam.im == 0.0) { status = OR_BREAKDOWN; done = 1; break; }
+                alpha = z_div(rho0, gam);
+                for (int32_t i = 0; i <= j; ++i)
+                    for (int32_t e = 0; e < n; ++e) RV(i)[e] = z_sub(RV(i)[e], z_mul(alpha, UV(i + 1)[e]));
+                for (int32_t e = 0; e < n; ++e) x[e] = z_add(x[e], z_mul(alpha, UV(0)[e]));
+                ++it;
+                rel = z_norm(n, RV(0)) / nb;
+                if (hist) hist[it] = rel;
+                if (!isfinite(rel)) { status = OR_NAN; done = 1; break; }
+                if (rel <= tol) { status = OR_OK; done = 1; break; }
+                or_zspmv(n, rowptr, col, val, RV(j), RV(j + 1));
+            }
+            if (done) break;
+            /* minimal-residual part: modified Gram-Schmidt on r_1..r_l */
+            for (int32_t j = 1; j <= ell; ++j) {
+                for (int32_t i = 1; i < j; ++i) {
+                    oz d;
+                    or_zdotc(n, RV(i), RV(j), &d);
+                    tau[i][j].re = d.re / sigma[i]; tau[i][j].im = d.im / sigma[i];
+                    for (int32_t e = 0; e < n; ++e) RV(j)[e] = z_sub(RV(j)[e], z_mul(tau[i][j], RV(i)[e]));
+                }
+                sigma[j] = z_norm(n, RV(j));
+                sigma[j] *= sigma[j];
+                if (sigma[j] == 0.0) { status = OR_BREAKDOWN; done = 1; break; }
+                {
+                    oz d;
+                    or_zdotc(n, RV(j), RV(0), &d);
+                    gp[j].re = d.re / sigma[j]; gp[j].im = d.im / sigma[j];
+                }
+            }
+            if (done) break;
+            /* back substitution: g solves the triangular system of the fit */
+            g[ell] = gp[ell];
+            omega = g[ell];
+            for (int32_t j = ell - 1; j >= 1; --j) {
+                oz acc = gp[j];
+                for (int32_t i = j + 1; i <= ell; ++i) acc = z_sub(acc, z_mul(tau[j][i], g[i]));
+                g[j] = acc;
+            }
+            for (int32_t j = 1; j < ell; ++j) {
+                oz acc = g[j + 1];
+                for (int32_t i = j + 1; i < ell; ++i) acc = z_add(acc, z_mul(tau[j][i], g[i + 1]));
+                gpp[j] = acc;
+            }
+            /* updates (the orthogonalised r_1..r_l are what the coefficients refer to) */
+            for (int32_t e = 0; e < n; ++e) {
+                x[e] = z_add(x[e], z_mul(g[1], RV(0)[e]));
+                RV(0)[e] = z_sub(RV(0)[e], z_mul(gp[ell], RV(ell)[e]));
+                UV(0)[e] = z_sub(UV(0)[e], z_mul(g[ell], UV(ell)[e]));
+            }
+            for (int32_t j = 1; j < ell; ++j)
+                for (int32_t e = 0; e < n; ++e) {
+                    UV(0)[e] = z_sub(UV(0)[e], z_mul(g[j], UV(j)[e]));
+                    x[e] = z_add(x[e], z_mul(gpp[j], RV(j)[e]));
+                    RV(0)[e] = z_sub(RV(0)[e], z_mul(gp[j], RV(j)[e]));
+                }
+            rel = z_norm(n, RV(0)) / nb;
+            if (hist) hist[it] = rel;   /* the step's entry now reflects the minimal-residual update */
+            if (!isfinite(rel)) { status = OR_NAN; break; }
+            if (rel <= tol) { status = OR_OK; break; }
+            if (omega.re == 0.0 && omega.im == 0.0) { status = OR_BREAKDOWN; break; }
+        }
+        or_zspmv(n, rowptr, col, val, x, tmp);
+        for (int32_t i = 0; i < n; ++i) tmp[i] = z_sub(b[i], tmp[i]);
+        info->relres_true = z_norm(n, tmp) / nb;
+        info->relres_rec = rel;
+        if (status == OR_OK && info->relres_true > tol && restarts == 0 && it < maxit) {
+            ++restarts;
+            continue;
+        }
+        if (status == OR_OK && info->relres_true > tol) status = OR_NOT_CONVERGED;
+        break;
+    }
+#undef RV
+#undef UV
+    info->iters = it;
+    info->status = status;
+    info->restarts = restarts;
+    free(R); free(U); free(rh); free(tmp);
+    return status;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Same iteration in complex64 with binary32 sums: the inner solver of the
  * mixed-precision refinement.  x0 = 0, stopping on ||r|| <= tol ||b||.
  * Returns the iteration count; *status gets the exit reason. */

@@ -50,6 +50,8 @@ def load():
         lib.or_bicgstab_pc.argtypes = [i32, P, P, P, P, P, P, f64, i32, P, P]
         lib.or_bicgstab_pc.restype = C.c_int
         lib.or_jacobi_dinv.argtypes = [i32, P, P, P, P]
+        lib.or_bicgstabl.argtypes = [i32, P, P, P, i32, P, P, f64, i32, P, P]
+        lib.or_bicgstabl.restype = C.c_int
         lib.or_zmul_elementwise.argtypes = [i64, P, P, P]
         lib.or_cbicgstab.argtypes = [i32, P, P, P, P, P, f32, i32, P]
         lib.or_cbicgstab.restype = i32
@@ -185,6 +187,25 @@ def bicgstab(A, b, x0=None, tol=1e-10, maxit=2000, history=True, precond=None):
     dinv = jacobi_dinv(A) if precond == "jacobi" else None
     lib.or_bicgstab_pc(A.n, _p(rp), _p(cl), _p(vl), _p(dinv) if dinv is not None else None, _p(b), _p(x),
                        float(tol), int(maxit), _p(hist) if history else None, C.byref(info))
+    out = OracleInfo(info.iters, info.status, info.restarts, info.relres_rec, info.relres_true)
+    if history:
+        out.hist = hist[: info.iters + 1].copy()
+    return x, out
+
+
+def bicgstabl(A, b, ell=2, x0=None, tol=1e-10, maxit=2000, history=True):
+    """BiCGStab(l) in binary64 (l BiCG steps + a minimal-residual step per outer
+    iteration); returns (x, OracleInfo) with iters counted in BiCG steps."""
+    lib = load()
+    b = _z(b)
+    x = np.zeros(A.n, dtype=np.complex128) if x0 is None else _z(x0).copy()
+    hist = np.full(maxit + int(ell) + 1, np.nan) if history else None
+    info = _OrInfo()
+    rp, cl, vl = _i(A.rowptr), _i(A.col), _z(A.val)
+    st = lib.or_bicgstabl(A.n, _p(rp), _p(cl), _p(vl), int(ell), _p(b), _p(x), float(tol), int(maxit),
+                          _p(hist) if history else None, C.byref(info))
+    if st < 0:
+        raise ValueError("ell must be in 1..8")
     out = OracleInfo(info.iters, info.status, info.restarts, info.relres_rec, info.relres_true)
     if history:
         out.hist = hist[: info.iters + 1].copy()

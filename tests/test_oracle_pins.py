@@ -282,6 +282,59 @@ def test_jacobi_dense_lu_and_column_scaling_invariance(oracle):
     assert i0.iters > 2 * infs.iters
 
 
+# --------------------------------------------------------------------------- BiCGStab(l)
+def test_bicgstabl_ell1_is_bicgstab(oracle):
+    """BiCGStab(1) is BiCGStab in exact arithmetic (Sleijpen and Fokkema):
+    the same residual history and solution up to rounding."""
+    A = W.fd_helmholtz_box(8, kh=0.5, damping=0.05)
+    b = K.vectors(A.n, 1001)[0]
+    x0, i0 = oracle.bicgstab(A, b, tol=1e-10)
+    x1, i1 = oracle.bicgstabl(A, b, ell=1, tol=1e-10)
+    assert i1.status == 0 and abs(i1.iters - i0.iters) <= 2
+    assert np.allclose(i1.hist[:12], i0.hist[:12], rtol=1e-11, atol=0)
+    assert np.linalg.norm(x1 - x0) <= 1e-8 * np.linalg.norm(x0)
+
+
+@pytest.mark.parametrize("ell", [2, 4, 8])
+def test_bicgstabl_dense_lu(oracle, ell):
+    A = W.fd_helmholtz_box(8, kh=0.5, damping=0.05)
+    b = K.vectors(A.n, 1001)[0]
+    x_lu = np.linalg.solve(A.to_scipy().toarray(), b)
+    x, info = oracle.bicgstabl(A, b, ell=ell, tol=1e-11, maxit=2000)
+    assert info.status == 0 and info.relres_true <= 1e-11
+    assert np.linalg.norm(x - x_lu) <= 1e-8 * np.linalg.norm(x_lu)
+    assert info.hist[0] == 1.0
+
+
+def test_bicgstabl_identity_and_special_cases(oracle):
+    A = W.CSR.from_scipy(sp.identity(50, dtype=np.complex128, format="csr"))
+    b = K.vectors(50, 2)[0]
+    x, info = oracle.bicgstabl(A, b, ell=4, tol=1e-10)
+    assert info.status == 0 and info.iters == 1 and np.array_equal(x, b)
+    A, b, xs = W.c1_small_fd()
+    x, info = oracle.bicgstabl(A, A.to_scipy() @ xs, ell=4, tol=1e-12)
+    assert info.status == 0 and np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+    x, info = oracle.bicgstabl(A, np.zeros(A.n, np.complex128), ell=2, x0=np.ones(A.n))
+    assert info.status == 0 and info.iters == 0 and not x.any()
+    x, info = oracle.bicgstabl(A, b, ell=2, maxit=0)
+    assert info.status == 4 and info.iters == 0 and not x.any()
+    bn = b.copy()
+    bn[0] = np.nan
+    assert oracle.bicgstabl(A, bn, ell=2)[1].status == 6
+    with pytest.raises(ValueError):
+        oracle.bicgstabl(A, b, ell=9)
+
+
+def test_bicgstabl_beats_stagnation(oracle):
+    """On the small jittered cylinder the minimal-residual steps of l = 4
+    converge in fewer BiCG steps than BiCGStab needs iterations."""
+    A, b = K.small_cylinder()
+    _, i0 = oracle.bicgstab(A, b, tol=1e-10, maxit=3000)
+    x4, i4 = oracle.bicgstabl(A, b, ell=4, tol=1e-10, maxit=3000)
+    assert i4.status == 0 and i4.relres_true <= 1e-10
+    assert i4.iters < i0.iters
+
+
 def test_mixed_refinement(oracle):
     A, b, _ = W.c1_small_fd()
     x, d = oracle.refine_mixed(A, b, tol=1e-10)

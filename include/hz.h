@@ -76,6 +76,12 @@ enum {
     HZ_MODE_MIXED = 1u       /* complex64 inner BiCGStab + complex128 iterative refinement */
 };
 
+/* Krylov methods of Section 7 */
+enum {
+    HZ_METHOD_BICGSTAB = 0u,   /* BiCGStab (van der Vorst) */
+    HZ_METHOD_BICGSTABL = 1u   /* BiCGStab(l) (Sleijpen and Fokkema), 1 <= l <= 8 */
+};
+
 /* preconditioners (Section 7 names its solvers P-BiCGSTAB etc. without
  * saying which preconditioner; none is the default reading) */
 enum {
@@ -260,6 +266,8 @@ typedef struct {
     int32_t x0_is_zero;      /* 1: ignore d_x on entry and start from x0 = 0 */
     double *d_hist;          /* optional device array of maxit+1 doubles: residual history */
     uint32_t precond;        /* HZ_PRECOND_NONE or HZ_PRECOND_JACOBI */
+    uint32_t method;         /* HZ_METHOD_BICGSTAB (default 0) or HZ_METHOD_BICGSTABL */
+    int32_t ell;             /* BiCGStab(l): l in 1..8 */
 } hz_solve_opts;
 
 /*

@@ -21,6 +21,7 @@ SOLVE_OUTCOMES = (HZ_OK, HZ_NOT_CONVERGED, HZ_BREAKDOWN, HZ_ERR_NAN)
 HZ_FLAG_VALIDATE, HZ_FLAG_SELL, HZ_FLAG_C64, HZ_FLAG_AUTOTUNE, HZ_FLAG_FF = 1, 2, 4, 8, 16
 HZ_MODE_FP64, HZ_MODE_MIXED = 0, 1
 HZ_PRECOND_NONE, HZ_PRECOND_JACOBI = 0, 1
+HZ_METHOD_BICGSTAB, HZ_METHOD_BICGSTABL = 0, 1
 HZ_SPMV_CSR_VECTOR, HZ_SPMV_SELL, HZ_SPMV_FF, HZ_SPMV_SELL_FF, HZ_SPMV_FF_FLAT, HZ_SPMV_FF_TMA = 0, 1, 2, 3, 4, 5
 
 # every symbol include/hz.h declares
@@ -46,7 +47,8 @@ class hz_info(C.Structure):
 class hz_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("mode", C.c_uint32),
                 ("inner_tol", C.c_float), ("inner_maxit", C.c_int32), ("max_outer", C.c_int32),
-                ("x0_is_zero", C.c_int32), ("d_hist", C.c_void_p), ("precond", C.c_uint32)]
+                ("x0_is_zero", C.c_int32), ("d_hist", C.c_void_p), ("precond", C.c_uint32),
+                ("method", C.c_uint32), ("ell", C.c_int32)]
 
 
 class hz_mat_props(C.Structure):

@@ -29,6 +29,8 @@ template <> struct Ar<double2> {
     __device__ static V zero() { return make_double2(0.0, 0.0); }
     __device__ static V from_c128(double2 a) { return a; }
     __device__ static double2 to_c128(V a) { return a; }
+    // a * s for a power of two s (exact)
+    __device__ static V pow2(V a, double s) { return make_double2(a.x * s, a.y * s); }
     // y + a x
     __device__ static V axpy(V y, S a, V x) { cmac(y, a, x); return y; }
     // y - a x
@@ -90,6 +92,11 @@ template <> struct Ar<float4> {
     __device__ static V from_c128(double2 a) { return split_ff(a); }
     __device__ static double2 to_c128(V a) {
         return make_double2(join_d(a.x, a.y), join_d(a.z, a.w));
+    }
+    // a * s for a power of two s (exact while the parts stay in binary32 range)
+    __device__ static V pow2(V a, double s) {
+        const float f = (float)s;
+        return make_float4(a.x * f, a.y * f, a.z * f, a.w * f);
     }
     // y + a x, each component accumulated exactly from y then rounded once
     __device__ static V axpy(V y, S a, V x) {

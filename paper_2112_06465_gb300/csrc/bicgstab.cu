@@ -26,120 +26,11 @@
 #include <type_traits>
 #include <vector>
 
-#include "spmv.cuh"
+#include "krylov.cuh"
 
 namespace hz {
 
 hz_status ensure_c64(hz_mat *A, cudaStream_t s);
-
-constexpr int kVecBlock = 256;
-#ifndef HZ_VEC_UNROLL
-#define HZ_VEC_UNROLL 8
-#endif
-constexpr int kVecUnroll = HZ_VEC_UNROLL;   // elements per thread per tile of the vector kernels
-
-// host-written controls of one solve (uploaded by the graph itself)
-struct Ctl {
-    double tol;
-    const double2 *b;
-    double2 *x;
-    double *hist;
-    int maxit;
-    int restart;
-    int x0_zero;
-    int max_outer;
-    float inner_tol;
-    int inner_maxit;
-    const double2 *pre_d;      // Jacobi: y0 = D x0 (null without a preconditioner)
-    const double2 *pre_dinv;   // Jacobi: x = D^-1 y
-};
-
-template <class St>
-struct BiState {
-    St rho, rho_old, alpha, omega, beta;
-    double nb;       // ||b|| of this (inner) system
-    double rel;      // last recursive residual ratio
-    double ss;       // ||s||^2
-    float tol32;     // inner tolerance (mixed)
-    int maxit;       // inner iteration cap (mixed)
-    int iter, done, half, status;
-};
-
-template <class V> using StateOf = BiState<typename Ar<V>::St>;
-
-struct OuterState {   // mixed-precision refinement state
-    double nb, rel;
-    int outer, done, status, zero_x;
-};
-
-struct Info {
-    int iters, status, restarts, outer;
-    double relres_rec, relres_true;
-    int zero_x, pad;
-};
-
-template <class F>
-__device__ __forceinline__ void vec_tiles(int n, F f) {
-    const int tile = kVecUnroll * blockDim.x;
-    for (int base = blockIdx.x * tile; base < n; base += gridDim.x * tile) {
-#pragma unroll
-        for (int u = 0; u < kVecUnroll; ++u) {
-            const int i = base + u * blockDim.x + threadIdx.x;
-            if (i < n) f(i);
-        }
-    }
-}
-
-// Tile walker that issues every load of a tile before the first compute:
-// load(i) returns the element's inputs (indices are clamped to n-1, so the
-// loads need no branch), comp(i, in) computes and stores for i < n.
-template <class Ld, class Cp>
-__device__ __forceinline__ void vec_tiles_staged(int n, Ld load, Cp comp) {
-    using In = decltype(load(0));
-    const int tile = kVecUnroll * blockDim.x;
-    for (int base = blockIdx.x * tile; base < n; base += gridDim.x * tile) {
-        In in[kVecUnroll];
-#pragma unroll
-        for (int u = 0; u < kVecUnroll; ++u) in[u] = load(min(base + u * (int)blockDim.x + (int)threadIdx.x, n - 1));
-#pragma unroll
-        for (int u = 0; u < kVecUnroll; ++u) {
-            const int i = base + u * blockDim.x + threadIdx.x;
-            if (i < n) comp(i, in[u]);
-        }
-    }
-}
-
-template <class V> struct In2 { V a, b; };
-template <class V> struct In3 { V a, b, c; };
-template <class V> struct In5 { V a, b, c, d, e; };
-
-__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
-
-// loop condition of the enclosing WHILE node; handle 0 = the graph has no
-// conditional node (the unrolled profiling graph), nothing to set
-__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, unsigned v) {
-    if (h) cudaGraphSetConditional(h, v);
-}
-
-template <class V, int NV>
-__device__ __forceinline__ bool vec_reduce(typename Ar<V>::Acc (&acc)[NV], RedScratch red,
-                                           typename Ar<V>::R (&tot)[NV]) {
-    using R = typename Ar<V>::R;
-    R v[NV];
-#pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] = Ar<V>::total(acc[j]);
-    return grid_reduce_last<R, NV>(v, red, tot);
-}
-
-// base of the solver epilogues: accumulator plumbing for element type V
-template <class V>
-struct EpiBase {
-    using Acc = typename Ar<V>::Acc;
-    using R = typename Ar<V>::R;
-    static constexpr bool kFFRow = Ar<V>::kFF;
-    __device__ static void zero(Acc &a) { Ar<V>::acc_zero(a); }
-    __device__ static R total(const Acc &a) { return Ar<V>::total(a); }
-};
 
 // ---------------------------------------------------------------------------
 // F1: p = r + beta (p - omega v)
@@ -302,16 +193,6 @@ __global__ void __launch_bounds__(kVecBlock) k_bicg_xr(int n, StateOf<V> *st, co
     }
 }
 
-// ---------------------------------------------------------------------------
-// start: x_w from the caller's x0 (or 0); on a restart x_w is kept
-template <class V>
-__global__ void __launch_bounds__(kVecBlock) k_init_x(int n, const Ctl *ctl, V *__restrict__ xw) {
-    if (ctl->restart) return;
-    const double2 *x0 = ctl->x, *pd = ctl->pre_d;
-    const bool zero = ctl->x0_zero != 0;
-    vec_tiles(n, [&](int i) { xw[i] = zero ? Ar<V>::zero() : Ar<V>::from_c128(pd ? cmul(x0[i], pd[i]) : x0[i]); });
-}
-
 // init epilogue: r = b - A x, rh = r, p = v = 0, ||r||^2, ||b||^2
 template <class V>
 struct EpiInit : EpiBase<V> {
@@ -360,42 +241,6 @@ struct EpiInit : EpiBase<V> {
         set_cond(h, st->done ? 0 : 1);
     }
 };
-
-// exit: true residual ||b - A x|| / ||b|| and the info block
-template <class V>
-struct EpiTrue : EpiBase<V> {
-    using typename EpiBase<V>::Acc;
-    using typename EpiBase<V>::R;
-    static constexpr int NV = 1;
-    StateOf<V> *st;
-    Info *info;
-    const Ctl *ctl;
-    __device__ bool skip() const { return false; }
-    template <int N> __device__ void row(int i, V y, Acc (&acc)[N]) const {
-        Ar<V>::nrm2(acc[0], Ar<V>::sub(Ar<V>::from_c128(ctl->b[i]), y));
-    }
-    template <int N> __device__ void finish(R (&tot)[N]) const {
-        info->iters = st->iter;
-        info->status = st->status;
-        info->outer = 0;
-        info->relres_rec = st->rel;
-        info->relres_true = info->zero_x ? 0.0 : sqrt((double)tot[0]) / st->nb;
-    }
-};
-
-template <class V>
-__global__ void __launch_bounds__(kVecBlock) k_copy_out(int n, const Ctl *ctl, Info *info,
-                                                        const V *__restrict__ xw, const int *fault) {
-    double2 *x = ctl->x;
-    const double2 *pdi = ctl->pre_dinv;
-    const bool zero = info->zero_x != 0;
-    // an expired bounded wait in an SpMV of this solve voids the result
-    if (fault && blockIdx.x == 0 && threadIdx.x == 0 && *(volatile const int *)fault) info->status = HZ_ERR_TIMEOUT;
-    vec_tiles(n, [&](int i) {
-        const double2 y = Ar<V>::to_c128(xw[i]);
-        x[i] = zero ? make_double2(0.0, 0.0) : (pdi ? cmul(y, pdi[i]) : y);
-    });
-}
 
 // ---------------------------------------------------------------------------
 // mixed precision: outer residual in complex128 (binary64 or double-float),
@@ -532,6 +377,8 @@ void free_solvers(hz_mat *A) {
         solver_free((Solver *)A->solver[m]);
         A->solver[m] = nullptr;
     }
+    bl_solver_free(A->solver_bl);
+    A->solver_bl = nullptr;
 }
 
 #define HZ_ALLOC(ptr, bytes) HZ_CUDA(cudaMalloc((void **)&(ptr), std::max<size_t>((bytes), 16)))
@@ -574,28 +421,6 @@ static hz_status solver_alloc(Solver *S) {
     memset(S->hinfo, 0, sizeof(Info));
     HZ_CUDA(cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking));
     HZ_CUDA(cudaDeviceSynchronize());
-    return HZ_OK;
-}
-
-// capture helpers -------------------------------------------------------------
-static hz_status capture_leaves(cudaStream_t s, std::vector<cudaGraphNode_t> *leaves) {
-    cudaStreamCaptureStatus cs;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t nd = 0;
-    HZ_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd));
-    leaves->assign(deps, deps + nd);
-    return HZ_OK;
-}
-
-static hz_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
-                           cudaGraphNode_t *node, cudaGraph_t *body) {
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    HZ_CUDA(cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &cp));
-    *body = cp.conditional.phGraph_out[0];
     return HZ_OK;
 }
 
@@ -779,6 +604,10 @@ extern "C" HZ_API hz_status hz_zsolve_opts(hz_mat *A, const hz_z *d_b, hz_z *d_x
     HZ_CHECK(o->maxit >= 0, "hz_zsolve: negative maxit");
     HZ_CHECK(o->tol >= 0.0, "hz_zsolve: negative tol");
     HZ_CHECK(o->precond == HZ_PRECOND_NONE || o->precond == HZ_PRECOND_JACOBI, "hz_zsolve: unknown preconditioner");
+    HZ_CHECK(o->method == HZ_METHOD_BICGSTAB || o->method == HZ_METHOD_BICGSTABL, "hz_zsolve: unknown method");
+    HZ_CHECK(o->method != HZ_METHOD_BICGSTABL || (o->ell >= 1 && o->ell <= 8), "hz_zsolve: ell must be in 1..8");
+    HZ_CHECK(o->method == HZ_METHOD_BICGSTAB || o->mode == HZ_MODE_FP64,
+             "hz_zsolve: the mixed mode runs BiCGStab only");
     *h_info = hz_info{};
     if (A->n == 0) { h_info->status = HZ_OK; return HZ_OK; }
     HZ_CHECK(d_b && d_x, "hz_zsolve: null vector");
@@ -790,8 +619,6 @@ extern "C" HZ_API hz_status hz_zsolve_opts(hz_mat *A, const hz_z *d_b, hz_z *d_x
         op->spmv_kind = A->spmv_kind;   // follow the caller's choice of SpMV variant
         op->group = A->group;
     }
-    Solver *S = nullptr;
-    HZ_TRY(get_solver(op, o->mode, s, &S));
     Ctl c{};
     c.tol = o->tol;
     c.b = (const double2 *)d_b;
@@ -805,6 +632,22 @@ extern "C" HZ_API hz_status hz_zsolve_opts(hz_mat *A, const hz_z *d_b, hz_z *d_x
     c.inner_maxit = o->inner_maxit > 0 ? o->inner_maxit : 1000;
     c.pre_d = op != A ? A->jac_d : nullptr;
     c.pre_dinv = op != A ? A->jac_dinv : nullptr;
+    c.op_scale = 1.0;
+    if (o->method == HZ_METHOD_BICGSTABL) {
+        Info inf{};
+        int restarts = 0;
+        HZ_TRY(bl_solve(op, o->ell, c, &inf, &restarts, s));
+        if (inf.status == HZ_OK && inf.relres_true > o->tol) inf.status = HZ_NOT_CONVERGED;
+        h_info->iters = inf.iters;
+        h_info->status = inf.status;
+        h_info->restarts = restarts;
+        h_info->outer = 0;
+        h_info->relres_rec = inf.relres_rec;
+        h_info->relres_true = inf.relres_true;
+        return (hz_status)inf.status;
+    }
+    Solver *S = nullptr;
+    HZ_TRY(get_solver(op, o->mode, s, &S));
     *S->hctl = c;
     HZ_CUDA(cudaGraphLaunch(S->exec, s));
     HZ_CUDA(cudaStreamSynchronize(s));

@@ -509,8 +509,9 @@ struct hz_mat {
     int *fault = nullptr;
     // diagonal positions (for set_diag), built on demand
     int32_t *diag_pos = nullptr;
-    // solver state (one per mode), created on first solve
+    // solver state (one per mode, and the BiCGStab(l) solver), created on first solve
     void *solver[2] = {nullptr, nullptr};
+    void *solver_bl = nullptr;
     // Jacobi right preconditioning: the column-scaled operator A D^-1 as a
     // handle of its own (borrowing rowptr/col), its values, and D, D^-1
     hz_mat *jac = nullptr;

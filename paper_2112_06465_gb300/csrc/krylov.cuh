@@ -1,0 +1,202 @@
+// krylov.cuh -- pieces shared by the device-resident Krylov solvers
+// (BiCGStab, BiCGStab(l), TFQMR): the host control block uploaded by each
+// solve graph, per-system state and info blocks, the vector-kernel tile
+// walkers, the fused-reduction plumbing, the start / true-residual /
+// copy-out steps and the CUDA-graph capture helpers.
+#pragma once
+
+#include <vector>
+
+#include "spmv.cuh"
+
+namespace hz {
+
+constexpr int kVecBlock = 256;
+#ifndef HZ_VEC_UNROLL
+#define HZ_VEC_UNROLL 8
+#endif
+constexpr int kVecUnroll = HZ_VEC_UNROLL;   // elements per thread per tile of the vector kernels
+
+// host-written controls of one solve (uploaded by the graph itself)
+struct Ctl {
+    double tol;
+    const double2 *b;
+    double2 *x;
+    double *hist;
+    int maxit;
+    int restart;
+    int x0_zero;
+    int max_outer;
+    float inner_tol;
+    int inner_maxit;
+    const double2 *pre_d;      // Jacobi: y0 = D x0 (null without a preconditioner)
+    const double2 *pre_dinv;   // Jacobi: x = D^-1 y
+    double op_scale;           // s = 2^-k: the iteration runs on s A (x0 -> x0 / s, x -> s y); 1 = unscaled
+};
+
+template <class St>
+struct BiState {
+    St rho, rho_old, alpha, omega, beta;
+    double nb;       // ||b|| of this (inner) system
+    double rel;      // last recursive residual ratio
+    double ss;       // ||s||^2
+    float tol32;     // inner tolerance (mixed)
+    int maxit;       // inner iteration cap (mixed)
+    int iter, done, half, status;
+};
+
+template <class V> using StateOf = BiState<typename Ar<V>::St>;
+
+struct OuterState {   // mixed-precision refinement state
+    double nb, rel;
+    int outer, done, status, zero_x;
+};
+
+struct Info {
+    int iters, status, restarts, outer;
+    double relres_rec, relres_true;
+    int zero_x, pad;
+};
+
+template <class F>
+__device__ __forceinline__ void vec_tiles(int n, F f) {
+    const int tile = kVecUnroll * blockDim.x;
+    for (int base = blockIdx.x * tile; base < n; base += gridDim.x * tile) {
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int i = base + u * blockDim.x + threadIdx.x;
+            if (i < n) f(i);
+        }
+    }
+}
+
+// Tile walker that issues every load of a tile before the first compute:
+// load(i) returns the element's inputs (indices are clamped to n-1, so the
+// loads need no branch), comp(i, in) computes and stores for i < n.
+template <class Ld, class Cp>
+__device__ __forceinline__ void vec_tiles_staged(int n, Ld load, Cp comp) {
+    using In = decltype(load(0));
+    const int tile = kVecUnroll * blockDim.x;
+    for (int base = blockIdx.x * tile; base < n; base += gridDim.x * tile) {
+        In in[kVecUnroll];
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) in[u] = load(min(base + u * (int)blockDim.x + (int)threadIdx.x, n - 1));
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int i = base + u * blockDim.x + threadIdx.x;
+            if (i < n) comp(i, in[u]);
+        }
+    }
+}
+
+template <class V> struct In2 { V a, b; };
+template <class V> struct In3 { V a, b, c; };
+template <class V> struct In5 { V a, b, c, d, e; };
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+// loop condition of the enclosing WHILE node; handle 0 = the graph has no
+// conditional node (the unrolled profiling graph), nothing to set
+__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, unsigned v) {
+    if (h) cudaGraphSetConditional(h, v);
+}
+
+template <class V, int NV>
+__device__ __forceinline__ bool vec_reduce(typename Ar<V>::Acc (&acc)[NV], RedScratch red,
+                                           typename Ar<V>::R (&tot)[NV]) {
+    using R = typename Ar<V>::R;
+    R v[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = Ar<V>::total(acc[j]);
+    return grid_reduce_last<R, NV>(v, red, tot);
+}
+
+// base of the solver epilogues: accumulator plumbing for element type V
+template <class V>
+struct EpiBase {
+    using Acc = typename Ar<V>::Acc;
+    using R = typename Ar<V>::R;
+    static constexpr bool kFFRow = Ar<V>::kFF;
+    __device__ static void zero(Acc &a) { Ar<V>::acc_zero(a); }
+    __device__ static R total(const Acc &a) { return Ar<V>::total(a); }
+};
+
+// ---------------------------------------------------------------------------
+// start: x_w from the caller's x0 (or 0); on a restart x_w is kept
+template <class V>
+__global__ void __launch_bounds__(kVecBlock) k_init_x(int n, const Ctl *ctl, V *__restrict__ xw) {
+    if (ctl->restart) return;
+    const double2 *x0 = ctl->x, *pd = ctl->pre_d;
+    const bool zero = ctl->x0_zero != 0;
+    const double inv_s = 1.0 / ctl->op_scale;   // a power of two: exact
+    vec_tiles(n, [&](int i) {
+        const double2 v = pd ? cmul(x0[i], pd[i]) : x0[i];
+        xw[i] = zero ? Ar<V>::zero() : Ar<V>::from_c128(make_double2(v.x * inv_s, v.y * inv_s));
+    });
+}
+
+// exit: true residual ||b - A x|| / ||b|| and the info block
+template <class V>
+struct EpiTrue : EpiBase<V> {
+    using typename EpiBase<V>::Acc;
+    using typename EpiBase<V>::R;
+    static constexpr int NV = 1;
+    StateOf<V> *st;
+    Info *info;
+    const Ctl *ctl;
+    __device__ bool skip() const { return false; }
+    template <int N> __device__ void row(int i, V y, Acc (&acc)[N]) const {
+        Ar<V>::nrm2(acc[0], Ar<V>::sub(Ar<V>::from_c128(ctl->b[i]), Ar<V>::pow2(y, ctl->op_scale)));
+    }
+    template <int N> __device__ void finish(R (&tot)[N]) const {
+        info->iters = st->iter;
+        info->status = st->status;
+        info->outer = 0;
+        info->relres_rec = st->rel;
+        info->relres_true = info->zero_x ? 0.0 : sqrt((double)tot[0]) / st->nb;
+    }
+};
+
+template <class V>
+__global__ void __launch_bounds__(kVecBlock) k_copy_out(int n, const Ctl *ctl, Info *info,
+                                                        const V *__restrict__ xw, const int *fault) {
+    double2 *x = ctl->x;
+    const double2 *pdi = ctl->pre_dinv;
+    const bool zero = info->zero_x != 0;
+    // an expired bounded wait in an SpMV of this solve voids the result
+    if (fault && blockIdx.x == 0 && threadIdx.x == 0 && *(volatile const int *)fault) info->status = HZ_ERR_TIMEOUT;
+    const double s = ctl->op_scale;
+    vec_tiles(n, [&](int i) {
+        const double2 y0 = Ar<V>::to_c128(xw[i]);
+        const double2 y = make_double2(y0.x * s, y0.y * s);
+        x[i] = zero ? make_double2(0.0, 0.0) : (pdi ? cmul(y, pdi[i]) : y);
+    });
+}
+
+// capture helpers -------------------------------------------------------------
+static inline hz_status capture_leaves(cudaStream_t s, std::vector<cudaGraphNode_t> *leaves) {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    HZ_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+    leaves->assign(deps, deps + nd);
+    return HZ_OK;
+}
+
+static inline hz_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
+                           cudaGraphNode_t *node, cudaGraph_t *body) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    HZ_CUDA(cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &cp));
+    *body = cp.conditional.phGraph_out[0];
+    return HZ_OK;
+}
+
+// BiCGStab(l) (bicgstabl.cu): one solve on `op` with controls c, 1 <= l <= 8
+hz_status bl_solve(hz_mat *op, int ell, const Ctl &c, Info *out, int *restarts, cudaStream_t s);
+void bl_solver_free(void *solver);
+
+}  // namespace hz

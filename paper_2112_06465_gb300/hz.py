@@ -232,15 +232,18 @@ def _info(i: hz_info) -> SolveInfo:
 
 
 def zsolve(A: Matrix, b, x=None, tol=1e-10, maxit=2000, mode="fp64", hist=None,
-           inner_tol=1e-5, inner_maxit=1000, max_outer=50, precond="none"):
+           inner_tol=1e-5, inner_maxit=1000, max_outer=50, precond="none", method="bicgstab", ell=4):
     """Solve A x = b with BiCGStab on the device; returns (x, SolveInfo).
 
     x (optional) holds x0 and receives the solution; mode is "fp64" or
     "mixed"; precond is "none" or "jacobi" (right preconditioning by the
-    inverse diagonal); hist (optional float64 device tensor of maxit+1
-    entries) receives the residual history.  Non-convergence is reported in
-    the info, not raised.
+    inverse diagonal); method is "bicgstab" or "bicgstabl" (BiCGStab(ell),
+    iterations counted in BiCG steps); hist (optional float64 device tensor
+    of maxit+1 entries, maxit+ell for BiCGStab(ell)) receives the residual
+    history.  Non-convergence is reported in the info, not raised.
     """
+    if method not in ("bicgstab", "bicgstabl"):
+        raise ValueError("method must be 'bicgstab' or 'bicgstabl'")
     if precond not in ("none", "jacobi"):
         raise ValueError("precond must be 'none' or 'jacobi'")
     b = _vec(b, name="b")
@@ -258,8 +261,11 @@ def zsolve(A: Matrix, b, x=None, tol=1e-10, maxit=2000, mode="fp64", hist=None,
     o.x0_is_zero = 1 if x0_zero else 0
     o.d_hist = hist.data_ptr() if hist is not None else None
     o.precond = _lib.HZ_PRECOND_JACOBI if precond == "jacobi" else _lib.HZ_PRECOND_NONE
-    if hist is not None and (hist.dtype != torch.float64 or hist.numel() < maxit + 1):
-        raise ValueError("hist must be a float64 device tensor with maxit+1 entries")
+    o.method = _lib.HZ_METHOD_BICGSTABL if method == "bicgstabl" else _lib.HZ_METHOD_BICGSTAB
+    o.ell = int(ell)
+    need = maxit + (int(ell) if method == "bicgstabl" else 1)
+    if hist is not None and (hist.dtype != torch.float64 or hist.numel() < need):
+        raise ValueError(f"hist must be a float64 device tensor with {need} entries")
     info = hz_info()
     check(_L.hz_zsolve_opts(A.handle, _ptr(b), _ptr(x), C.byref(o), C.byref(info), _stream()),
           allow=_lib.SOLVE_OUTCOMES)

@@ -446,6 +446,122 @@ int or_bicgstabl(int32_t n, const int32_t *rowptr, const int32_t *col, const oz 
 }
 
 /* ---------------------------------------------------------------------- */
+/* TFQMR, Freund's transpose-free QMR (Section 7 lists P-TFQMR among the
+ * paper's solvers; no preconditioner here).  Iteration j (two products with
+ * A) runs the half steps m = 2j+1 and m = 2j+2:
+ *   alpha = rho / <r^, v>,  u_{2j+2} = u_{2j+1} - alpha v
+ *   per half step m:  w <- w - alpha A u_m  (A u_{2j+1} kept from when
+ *                     u_{2j+1} was formed; A u_{2j+2} is the second product),
+ *     theta_m = ||w|| / tau_{m-1},  c_m = 1/sqrt(1 + theta_m^2),
+ *     tau_m = tau_{m-1} theta_m c_m,  eta_m = c_m^2 alpha,
+ *     d <- u_m + (theta_{m-1}^2 eta_{m-1} / alpha) d,  x <- x + eta_m d
+ *   rho' = <r^, w>,  beta = rho'/rho,  u_{2j+3} = w + beta u_{2j+2},
+ *   v <- A u_{2j+3} + beta (A u_{2j+2} + beta v)   (v is not A u: it is the
+ *   product with the CGS search direction).
+ * The stopping test uses the quasi-residual bound ||r_m|| <= sqrt(m+1) tau_m:
+ * after the second half step of each iteration, stop when
+ * sqrt(m+1) tau_m <= tol ||b||.  hist[j] holds sqrt(m+1) tau_m / ||b|| of
+ * iteration j.  A zero tau_{m-1} (the previous half step reached the exact
+ * solution) gives theta_m = 0.  Breakdown: rho = 0 or <r^, v> = 0.  The true
+ * residual is recomputed at exit; one restart as for BiCGStab. */
+int or_tfqmr(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *val,
+             const oz *b, oz *x, double tol, int32_t maxit, double *hist, or_info *info)
+{
+    const size_t nn = (size_t)n;
+    oz *w = calloc(nn, sizeof(oz)), *u1 = calloc(nn, sizeof(oz)), *u2 = calloc(nn, sizeof(oz));
+    oz *v = calloc(nn, sizeof(oz)), *d = calloc(nn, sizeof(oz)), *au = calloc(nn, sizeof(oz));
+    oz *rh = calloc(nn, sizeof(oz)), *tmp = calloc(nn, sizeof(oz)), *au1 = calloc(nn, sizeof(oz));
+    double nb = z_norm(n, b), rel = 0.0;
+    int32_t it = 0, status = OR_NOT_CONVERGED, restarts = 0;
+    if (nb == 0.0) {
+        memset(x, 0, nn * sizeof(oz));
+        info->iters = 0; info->status = OR_OK; info->restarts = 0;
+        info->relres_rec = 0.0; info->relres_true = 0.0;
+        if (hist) hist[0] = 0.0;
+        free(w); free(u1); free(u2); free(v); free(d); free(au); free(rh); free(tmp); free(au1);
+        return OR_OK;
+    }
+    for (;;) {
+        double tau, theta = 0.0;
+        oz eta = {0, 0}, rho;
+        int32_t m = 0;
+        or_zspmv(n, rowptr, col, val, x, w);
+        for (int32_t i = 0; i < n; ++i) {
+            w[i] = z_sub(b[i], w[i]);
+            u1[i] = w[i];
+            rh[i] = w[i];
+            d[i].re = d[i].im = 0.0;
+        }
+        tau = z_norm(n, w);
+        or_zdotc(n, rh, w, &rho);
+        or_zspmv(n, rowptr, col, val, u1, au1);     /* A u_1 */
+        memcpy(v, au1, nn * sizeof(oz));             /* v_0 = A u_1 */
+        rel = tau / nb;
+        if (hist && it == 0) hist[0] = rel;
+        if (!isfinite(rel)) status = OR_NAN;
+        else if (rel <= tol) status = OR_OK;
+        else status = OR_NOT_CONVERGED;
+        while (status == OR_NOT_CONVERGED && it < maxit) {
+            oz sig, alpha, rho1, beta;
+            if (rho.re == 0.0 && rho.im == 0.0) { status = OR_BREAKDOWN; break; }
+            or_zdotc(n, rh, v, &sig);
+            if (sig.re == 0.0 && sig.im == 0.0) { status = OR_BREAKDOWN; break; }
+            alpha = z_div(rho, sig);
+            for (int32_t i = 0; i < n; ++i) u2[i] = z_sub(u1[i], z_mul(alpha, v[i]));
+            for (int32_t half = 0; half < 2; ++half) {
+                const oz *um = half == 0 ? u1 : u2;
+                oz coef;
+                double th_prev = theta, wn, c;
+                if (half == 0) memcpy(au, au1, nn * sizeof(oz));        /* A u_{2j+1} */
+                else or_zspmv(n, rowptr, col, val, u2, au);            /* A u_{2j+2} */
+                for (int32_t i = 0; i < n; ++i) w[i] = z_sub(w[i], z_mul(alpha, au[i]));
+                ++m;
+                wn = z_norm(n, w);
+                theta = tau == 0.0 ? 0.0 : wn / tau;
+                c = 1.0 / sqrt(1.0 + theta * theta);
+                tau = tau * theta * c;
+                coef = z_div(z_mul((oz){th_prev * th_prev, 0.0}, eta), alpha);
+                eta.re = c * c * alpha.re; eta.im = c * c * alpha.im;
+                for (int32_t i = 0; i < n; ++i) {
+                    d[i] = z_add(um[i], z_mul(coef, d[i]));
+                    x[i] = z_add(x[i], z_mul(eta, d[i]));
+                }
+            }
+            ++it;
+            rel = sqrt((double)m + 1.0) * tau / nb;
+            if (hist) hist[it] = rel;
+            if (!isfinite(rel)) { status = OR_NAN; break; }
+            if (rel <= tol) { status = OR_OK; break; }
+            or_zdotc(n, rh, w, &rho1);
+            beta = z_div(rho1, rho);
+            rho = rho1;
+            /* au holds A u_{2j+2} */
+            for (int32_t i = 0; i < n; ++i) {
+                u1[i] = z_add(w[i], z_mul(beta, u2[i]));
+                tmp[i] = z_add(au[i], z_mul(beta, v[i]));
+            }
+            or_zspmv(n, rowptr, col, val, u1, au1);
+            for (int32_t i = 0; i < n; ++i) v[i] = z_add(au1[i], z_mul(beta, tmp[i]));
+        }
+        or_zspmv(n, rowptr, col, val, x, tmp);
+        for (int32_t i = 0; i < n; ++i) tmp[i] = z_sub(b[i], tmp[i]);
+        info->relres_true = z_norm(n, tmp) / nb;
+        info->relres_rec = rel;
+        if (status == OR_OK && info->relres_true > tol && restarts == 0 && it < maxit) {
+            ++restarts;
+            continue;
+        }
+        if (status == OR_OK && info->relres_true > tol) status = OR_NOT_CONVERGED;
+        break;
+    }
+    info->iters = it;
+    info->status = status;
+    info->restarts = restarts;
+    free(w); free(u1); free(u2); free(v); free(d); free(au); free(rh); free(tmp); free(au1);
+    return status;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Same iteration in complex64 with binary32 sums: the inner solver of the
  * mixed-precision refinement.  x0 = 0, stopping on ||r|| <= tol ||b||.
  * Returns the iteration count; *status gets the exit reason. */

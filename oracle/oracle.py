@@ -52,6 +52,8 @@ def load():
         lib.or_jacobi_dinv.argtypes = [i32, P, P, P, P]
         lib.or_bicgstabl.argtypes = [i32, P, P, P, i32, P, P, f64, i32, P, P]
         lib.or_bicgstabl.restype = C.c_int
+        lib.or_tfqmr.argtypes = [i32, P, P, P, P, P, f64, i32, P, P]
+        lib.or_tfqmr.restype = C.c_int
         lib.or_zmul_elementwise.argtypes = [i64, P, P, P]
         lib.or_cbicgstab.argtypes = [i32, P, P, P, P, P, f32, i32, P]
         lib.or_cbicgstab.restype = i32
@@ -206,6 +208,23 @@ def bicgstabl(A, b, ell=2, x0=None, tol=1e-10, maxit=2000, history=True):
                           _p(hist) if history else None, C.byref(info))
     if st < 0:
         raise ValueError("ell must be in 1..8")
+    out = OracleInfo(info.iters, info.status, info.restarts, info.relres_rec, info.relres_true)
+    if history:
+        out.hist = hist[: info.iters + 1].copy()
+    return x, out
+
+
+def tfqmr(A, b, x0=None, tol=1e-10, maxit=2000, history=True):
+    """TFQMR in binary64, stopping on the quasi-residual bound; returns (x,
+    OracleInfo) with iters counted in iterations (two products with A each)."""
+    lib = load()
+    b = _z(b)
+    x = np.zeros(A.n, dtype=np.complex128) if x0 is None else _z(x0).copy()
+    hist = np.full(maxit + 1, np.nan) if history else None
+    info = _OrInfo()
+    rp, cl, vl = _i(A.rowptr), _i(A.col), _z(A.val)
+    lib.or_tfqmr(A.n, _p(rp), _p(cl), _p(vl), _p(b), _p(x), float(tol), int(maxit),
+                 _p(hist) if history else None, C.byref(info))
     out = OracleInfo(info.iters, info.status, info.restarts, info.relres_rec, info.relres_true)
     if history:
         out.hist = hist[: info.iters + 1].copy()

@@ -335,6 +335,48 @@ def test_bicgstabl_beats_stagnation(oracle):
     assert i4.iters < i0.iters
 
 
+# --------------------------------------------------------------------------- TFQMR
+def test_tfqmr_dense_lu_and_manufactured(oracle):
+    A = W.fd_helmholtz_box(8, kh=0.5, damping=0.05)
+    b = K.vectors(A.n, 1001)[0]
+    x_lu = np.linalg.solve(A.to_scipy().toarray(), b)
+    x, info = oracle.tfqmr(A, b, tol=1e-11, maxit=2000)
+    assert info.status == 0 and info.relres_true <= 1e-11
+    assert np.linalg.norm(x - x_lu) <= 1e-8 * np.linalg.norm(x_lu)
+    # the quasi-residual bound sqrt(m+1) tau_m is never below the true residual
+    assert info.hist[0] == 1.0 and info.relres_true <= info.hist[-1]
+    A, _, xs = W.c1_small_fd()
+    x, info = oracle.tfqmr(A, A.to_scipy() @ xs, tol=1e-12, maxit=2000)
+    assert info.status == 0 and np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
+def test_tfqmr_finite_termination(oracle):
+    """A = I ends after one iteration with x = b; a diagonal matrix with three
+    distinct eigenvalues is solved to rounding level within three iterations
+    (the squared BiCG polynomial of degree 3 annihilates the spectrum)."""
+    I = W.CSR.from_scipy(sp.identity(50, dtype=np.complex128, format="csr"))
+    b = K.vectors(50, 2)[0]
+    x, info = oracle.tfqmr(I, b, tol=1e-10)
+    assert info.status == 0 and info.iters == 1 and np.array_equal(x, b)
+    lam = np.repeat(np.array([1.0 + 0.5j, 3.0 - 1j, 7.0 + 2j]), 20)
+    D = W.CSR.from_scipy(sp.diags(lam, format="csr"))
+    b = K.vectors(60, 3)[0]
+    x, info = oracle.tfqmr(D, b, tol=1e-13, maxit=50)
+    assert info.status == 0 and info.iters <= 3
+    assert np.linalg.norm(x - b / lam) <= 1e-12 * np.linalg.norm(b / lam)
+
+
+def test_tfqmr_special_cases(oracle):
+    A, b, _ = W.c1_small_fd()
+    x, info = oracle.tfqmr(A, np.zeros(A.n, np.complex128), x0=np.ones(A.n))
+    assert info.status == 0 and info.iters == 0 and not x.any()
+    x, info = oracle.tfqmr(A, b, maxit=0)
+    assert info.status == 4 and info.iters == 0 and not x.any()
+    bn = b.copy()
+    bn[0] = np.nan
+    assert oracle.tfqmr(A, bn)[1].status == 6
+
+
 def test_mixed_refinement(oracle):
     A, b, _ = W.c1_small_fd()
     x, d = oracle.refine_mixed(A, b, tol=1e-10)

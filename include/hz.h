@@ -79,7 +79,10 @@ enum {
 /* Krylov methods of Section 7 */
 enum {
     HZ_METHOD_BICGSTAB = 0u,   /* BiCGStab (van der Vorst) */
-    HZ_METHOD_BICGSTABL = 1u   /* BiCGStab(l) (Sleijpen and Fokkema), 1 <= l <= 8 */
+    HZ_METHOD_BICGSTABL = 1u,  /* BiCGStab(l) (Sleijpen and Fokkema), 1 <= l <= 8; iterations are
+                                  counted in BiCG steps (two products with A each) */
+    HZ_METHOD_TFQMR = 2u       /* TFQMR (Freund); stops on the quasi-residual bound
+                                  sqrt(m+1) tau_m <= tol ||b||, which bounds ||b - A x|| */
 };
 
 /* preconditioners (Section 7 names its solvers P-BiCGSTAB etc. without
@@ -266,7 +269,7 @@ typedef struct {
     int32_t x0_is_zero;      /* 1: ignore d_x on entry and start from x0 = 0 */
     double *d_hist;          /* optional device array of maxit+1 doubles: residual history */
     uint32_t precond;        /* HZ_PRECOND_NONE or HZ_PRECOND_JACOBI */
-    uint32_t method;         /* HZ_METHOD_BICGSTAB (default 0) or HZ_METHOD_BICGSTABL */
+    uint32_t method;         /* HZ_METHOD_BICGSTAB (default 0), HZ_METHOD_BICGSTABL or HZ_METHOD_TFQMR */
     int32_t ell;             /* BiCGStab(l): l in 1..8 */
 } hz_solve_opts;
 

@@ -21,7 +21,7 @@ SOLVE_OUTCOMES = (HZ_OK, HZ_NOT_CONVERGED, HZ_BREAKDOWN, HZ_ERR_NAN)
 HZ_FLAG_VALIDATE, HZ_FLAG_SELL, HZ_FLAG_C64, HZ_FLAG_AUTOTUNE, HZ_FLAG_FF = 1, 2, 4, 8, 16
 HZ_MODE_FP64, HZ_MODE_MIXED = 0, 1
 HZ_PRECOND_NONE, HZ_PRECOND_JACOBI = 0, 1
-HZ_METHOD_BICGSTAB, HZ_METHOD_BICGSTABL = 0, 1
+HZ_METHOD_BICGSTAB, HZ_METHOD_BICGSTABL, HZ_METHOD_TFQMR = 0, 1, 2
 HZ_SPMV_CSR_VECTOR, HZ_SPMV_SELL, HZ_SPMV_FF, HZ_SPMV_SELL_FF, HZ_SPMV_FF_FLAT, HZ_SPMV_FF_TMA = 0, 1, 2, 3, 4, 5
 
 # every symbol include/hz.h declares

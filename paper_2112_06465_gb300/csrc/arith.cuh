@@ -40,6 +40,7 @@ template <> struct Ar<double2> {
         return y;
     }
     __device__ static V sub(V a, V b) { return make_double2(a.x - b.x, a.y - b.y); }
+    __device__ static V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
     __device__ static void acc_zero(Acc &a) { a = 0.0; }
     // (re, im) += conj(a) b
     __device__ static void dotc(Acc &re, Acc &im, V a, V b) {
@@ -63,6 +64,7 @@ template <> struct Ar<float2> {
         return y;
     }
     __device__ static V sub(V a, V b) { return make_float2(a.x - b.x, a.y - b.y); }
+    __device__ static V add(V a, V b) { return make_float2(a.x + b.x, a.y + b.y); }
     __device__ static void acc_zero(Acc &a) { a = 0.f; }
     __device__ static void dotc(Acc &re, Acc &im, V a, V b) {
         re = fmaf(a.x, b.x, re); re = fmaf(a.y, b.y, re);
@@ -113,6 +115,13 @@ template <> struct Ar<float4> {
         float sr = a.x, cr = a.y, si = a.z, ci = a.w;
         ff_acc(sr, cr, -b.x); cr = __fsub_rn(cr, b.y);
         ff_acc(si, ci, -b.z); ci = __fsub_rn(ci, b.w);
+        const float2 r = ff_norm(sr, cr), i = ff_norm(si, ci);
+        return make_float4(r.x, r.y, i.x, i.y);
+    }
+    __device__ static V add(V a, V b) {
+        float sr = a.x, cr = a.y, si = a.z, ci = a.w;
+        ff_acc(sr, cr, b.x); cr = __fadd_rn(cr, b.y);
+        ff_acc(si, ci, b.z); ci = __fadd_rn(ci, b.w);
         const float2 r = ff_norm(sr, cr), i = ff_norm(si, ci);
         return make_float4(r.x, r.y, i.x, i.y);
     }

@@ -379,6 +379,8 @@ void free_solvers(hz_mat *A) {
     }
     bl_solver_free(A->solver_bl);
     A->solver_bl = nullptr;
+    tq_solver_free(A->solver_tq);
+    A->solver_tq = nullptr;
 }
 
 #define HZ_ALLOC(ptr, bytes) HZ_CUDA(cudaMalloc((void **)&(ptr), std::max<size_t>((bytes), 16)))
@@ -604,7 +606,8 @@ extern "C" HZ_API hz_status hz_zsolve_opts(hz_mat *A, const hz_z *d_b, hz_z *d_x
     HZ_CHECK(o->maxit >= 0, "hz_zsolve: negative maxit");
     HZ_CHECK(o->tol >= 0.0, "hz_zsolve: negative tol");
     HZ_CHECK(o->precond == HZ_PRECOND_NONE || o->precond == HZ_PRECOND_JACOBI, "hz_zsolve: unknown preconditioner");
-    HZ_CHECK(o->method == HZ_METHOD_BICGSTAB || o->method == HZ_METHOD_BICGSTABL, "hz_zsolve: unknown method");
+    HZ_CHECK(o->method == HZ_METHOD_BICGSTAB || o->method == HZ_METHOD_BICGSTABL || o->method == HZ_METHOD_TFQMR,
+             "hz_zsolve: unknown method");
     HZ_CHECK(o->method != HZ_METHOD_BICGSTABL || (o->ell >= 1 && o->ell <= 8), "hz_zsolve: ell must be in 1..8");
     HZ_CHECK(o->method == HZ_METHOD_BICGSTAB || o->mode == HZ_MODE_FP64,
              "hz_zsolve: the mixed mode runs BiCGStab only");
@@ -633,10 +636,11 @@ extern "C" HZ_API hz_status hz_zsolve_opts(hz_mat *A, const hz_z *d_b, hz_z *d_x
     c.pre_d = op != A ? A->jac_d : nullptr;
     c.pre_dinv = op != A ? A->jac_dinv : nullptr;
     c.op_scale = 1.0;
-    if (o->method == HZ_METHOD_BICGSTABL) {
+    if (o->method == HZ_METHOD_BICGSTABL || o->method == HZ_METHOD_TFQMR) {
         Info inf{};
         int restarts = 0;
-        HZ_TRY(bl_solve(op, o->ell, c, &inf, &restarts, s));
+        if (o->method == HZ_METHOD_BICGSTABL) HZ_TRY(bl_solve(op, o->ell, c, &inf, &restarts, s));
+        else HZ_TRY(tq_solve(op, c, &inf, &restarts, s));
         if (inf.status == HZ_OK && inf.relres_true > o->tol) inf.status = HZ_NOT_CONVERGED;
         h_info->iters = inf.iters;
         h_info->status = inf.status;

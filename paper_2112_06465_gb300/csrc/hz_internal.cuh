@@ -512,6 +512,7 @@ struct hz_mat {
     // solver state (one per mode, and the BiCGStab(l) solver), created on first solve
     void *solver[2] = {nullptr, nullptr};
     void *solver_bl = nullptr;
+    void *solver_tq = nullptr;
     // Jacobi right preconditioning: the column-scaled operator A D^-1 as a
     // handle of its own (borrowing rowptr/col), its values, and D, D^-1
     hz_mat *jac = nullptr;

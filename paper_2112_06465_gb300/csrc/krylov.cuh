@@ -119,6 +119,7 @@ struct EpiBase {
     static constexpr bool kFFRow = Ar<V>::kFF;
     __device__ static void zero(Acc &a) { Ar<V>::acc_zero(a); }
     __device__ static R total(const Acc &a) { return Ar<V>::total(a); }
+    __device__ void on_skip() const {}
 };
 
 // ---------------------------------------------------------------------------
@@ -198,5 +199,8 @@ static inline hz_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode
 // BiCGStab(l) (bicgstabl.cu): one solve on `op` with controls c, 1 <= l <= 8
 hz_status bl_solve(hz_mat *op, int ell, const Ctl &c, Info *out, int *restarts, cudaStream_t s);
 void bl_solver_free(void *solver);
+// TFQMR (tfqmr.cu): one solve on `op` with controls c
+hz_status tq_solve(hz_mat *op, const Ctl &c, Info *out, int *restarts, cudaStream_t s);
+void tq_solver_free(void *solver);
 
 }  // namespace hz

@@ -101,6 +101,7 @@ struct MatView {
 //   using Acc, R;  static constexpr int NV;  static constexpr bool kFFRow;
 //   static void zero(Acc &);  static R total(const Acc &);
 //   bool skip() const;                       grid-uniform early exit
+//   void on_skip() const;                    run by one thread when skip() held
 //   void row(int i, Y y, Acc (&acc)[N]) const;  Y = T, or float4 if kFFRow
 //   void finish(R (&tot)[N]) const;          thread 0 of the last block
 template <int W, class T, class Epi, int NV>
@@ -620,7 +621,10 @@ __global__ void __launch_bounds__(kSpmvBlock) k_spmv(MatView<T> A, const T *__re
     constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
     pdl_wait();
     pdl_release();
-    if (epi.skip()) return;
+    if (epi.skip()) {   // grid-uniform early exit; one thread reports it to the epilogue
+        if (blockIdx.x == 0 && threadIdx.x == 0) epi.on_skip();
+        return;
+    }
     typename Epi::Acc acc[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
@@ -636,7 +640,10 @@ __global__ void __launch_bounds__(kSpmvBlock, HZ_FF_MIN_BLOCKS) k_spmv_ff(MatVie
     constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
     pdl_wait();
     pdl_release();
-    if (epi.skip()) return;
+    if (epi.skip()) {   // grid-uniform early exit; one thread reports it to the epilogue
+        if (blockIdx.x == 0 && threadIdx.x == 0) epi.on_skip();
+        return;
+    }
     typename Epi::Acc acc[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
@@ -653,7 +660,10 @@ __global__ void __launch_bounds__(kFlatThreads, kFlatMinBlocks) k_spmv_ffb(MatVi
     constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
     pdl_wait();
     pdl_release();
-    if (epi.skip()) return;
+    if (epi.skip()) {   // grid-uniform early exit; one thread reports it to the epilogue
+        if (blockIdx.x == 0 && threadIdx.x == 0) epi.on_skip();
+        return;
+    }
     typename Epi::Acc acc[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
@@ -672,7 +682,10 @@ __global__ void __launch_bounds__(kFlatThreads) k_spmv_fft(MatView<double2> A, c
     constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
     pdl_wait();
     pdl_release();
-    if (epi.skip()) return;
+    if (epi.skip()) {   // grid-uniform early exit; one thread reports it to the epilogue
+        if (blockIdx.x == 0 && threadIdx.x == 0) epi.on_skip();
+        return;
+    }
     typename Epi::Acc acc[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
@@ -696,6 +709,7 @@ struct EpiStore {
     __device__ static void zero(Acc &a) { a = Acc(0); }
     __device__ static R total(const Acc &a) { return a; }
     __device__ bool skip() const { return false; }
+    __device__ void on_skip() const {}
     template <int N> __device__ void row(int i, T v, Acc (&)[N]) const { y[i] = v; }
     template <int N> __device__ void finish(R (&)[N]) const {}
 };

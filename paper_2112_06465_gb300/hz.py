@@ -237,13 +237,14 @@ def zsolve(A: Matrix, b, x=None, tol=1e-10, maxit=2000, mode="fp64", hist=None,
 
     x (optional) holds x0 and receives the solution; mode is "fp64" or
     "mixed"; precond is "none" or "jacobi" (right preconditioning by the
-    inverse diagonal); method is "bicgstab" or "bicgstabl" (BiCGStab(ell),
-    iterations counted in BiCG steps); hist (optional float64 device tensor
+    inverse diagonal); method is "bicgstab", "bicgstabl" (BiCGStab(ell),
+    iterations counted in BiCG steps) or "tfqmr" (stopping on the
+    quasi-residual bound, hist holding that bound); hist (optional float64 device tensor
     of maxit+1 entries, maxit+ell for BiCGStab(ell)) receives the residual
     history.  Non-convergence is reported in the info, not raised.
     """
-    if method not in ("bicgstab", "bicgstabl"):
-        raise ValueError("method must be 'bicgstab' or 'bicgstabl'")
+    if method not in ("bicgstab", "bicgstabl", "tfqmr"):
+        raise ValueError("method must be 'bicgstab', 'bicgstabl' or 'tfqmr'")
     if precond not in ("none", "jacobi"):
         raise ValueError("precond must be 'none' or 'jacobi'")
     b = _vec(b, name="b")
@@ -261,7 +262,8 @@ def zsolve(A: Matrix, b, x=None, tol=1e-10, maxit=2000, mode="fp64", hist=None,
     o.x0_is_zero = 1 if x0_zero else 0
     o.d_hist = hist.data_ptr() if hist is not None else None
     o.precond = _lib.HZ_PRECOND_JACOBI if precond == "jacobi" else _lib.HZ_PRECOND_NONE
-    o.method = _lib.HZ_METHOD_BICGSTABL if method == "bicgstabl" else _lib.HZ_METHOD_BICGSTAB
+    o.method = {"bicgstab": _lib.HZ_METHOD_BICGSTAB, "bicgstabl": _lib.HZ_METHOD_BICGSTABL,
+                "tfqmr": _lib.HZ_METHOD_TFQMR}[method]
     o.ell = int(ell)
     need = maxit + (int(ell) if method == "bicgstabl" else 1)
     if hist is not None and (hist.dtype != torch.float64 or hist.numel() < need):

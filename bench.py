@@ -243,8 +243,9 @@ def compare_modes(hz, torch, full_c4, maxit):
     Every system is solved (x0 = 0) by: the binary64 solver (CSR-vector
     SpMV), the double-float complex128 solver (block-flat SpMV), the mixed
     solver (complex64 inner BiCGStab, binary64 outer refinement), the
-    double-float solver with Jacobi right preconditioning and, for all
-    systems at once, the persistent batched binary64 solver.  Times are CUDA
+    double-float solver with Jacobi right preconditioning, double-float
+    BiCGStab(4) and TFQMR (iterations in steps of two products with A) and,
+    for all systems at once, the persistent batched binary64 solver.  Times are CUDA
     events around each call, after one untimed call of each kind (graph
     capture).  Speedups are over the systems every variant solved."""
     import workloads as W
@@ -266,14 +267,20 @@ def compare_modes(hz, torch, full_c4, maxit):
         e1.synchronize()
         return out, e0.elapsed_time(e1)
 
-    variants = {"fp64_binary64": ("csr", "fp64", "none"), "fp64_double_float": ("ffflat", "fp64", "none"),
-                "mixed": ("csr", "mixed", "none"), "fp64_double_float_jacobi": ("ffflat", "fp64", "jacobi")}
+    variants = {
+        "fp64_binary64": ("csr", dict(mode="fp64")),
+        "fp64_double_float": ("ffflat", dict(mode="fp64")),
+        "mixed": ("csr", dict(mode="mixed")),
+        "fp64_double_float_jacobi": ("ffflat", dict(mode="fp64", precond="jacobi")),
+        "bicgstab4_double_float": ("ffflat", dict(method="bicgstabl", ell=4)),
+        "tfqmr_double_float": ("ffflat", dict(method="tfqmr")),
+    }
     res = {k: [] for k in variants}
     for M, b in zip(mats, bs):
-        for key, (kind, mode, pc) in variants.items():
+        for key, (kind, kw) in variants.items():
             M.set_spmv(kind, M.props()["group"] if kind == "csr" else 0)
-            hz.zsolve(M, b, tol=1e-10, maxit=maxit, mode=mode, precond=pc)          # graph capture
-            (_, info), ms = timed(lambda: hz.zsolve(M, b, tol=1e-10, maxit=maxit, mode=mode, precond=pc))
+            hz.zsolve(M, b, tol=1e-10, maxit=maxit, **kw)          # graph capture
+            (_, info), ms = timed(lambda: hz.zsolve(M, b, tol=1e-10, maxit=maxit, **kw))
             res[key].append((ms, info))
     hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit)
     (_, binfos), bms = timed(lambda: hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit))

@@ -14,6 +14,15 @@
 // per half step: theta = ||w|| / tau, c = 1/sqrt(1 + theta^2), tau *= theta c,
 // coef = theta_prev^2 eta_prev / alpha, eta = c^2 alpha.  The d/x update of
 // a half step needs that step's reduction, so it rides on the next kernel.
+//
+// Range guard.  In a stagnating or erratic run u, v and w (squared-BiCG
+// vectors) can grow without bound while x stays sensible; on the
+// double-float path their squares leave the binary32 exponent range long
+// before binary64 would notice.  The iteration is invariant under scaling
+// u, v, w, d, A u and rho, tau by the same factor if x is updated with
+// eta / G (G the accumulated factor) and the bound uses tau / G.  When
+// ||v||^2 or tau^2 passes 2^120 the next iteration first scales those
+// vectors by 2^-64 (exact) and the scalars with them.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -27,9 +36,15 @@ struct TqExtra {
     double2 eta;       // eta of the last half step
     double2 coef1, eta1, coef2, eta2;   // d/x coefficients of the two half steps of this iteration
     double tau, theta;
+    double xs;         // 1 / G: x moves by eta * xs * d (vectors held scaled by G <= 1)
+    double2 eta1x, eta2x;   // eta1 * xs, eta2 * xs
     int m;             // half steps since the (re)start
     int stop;          // the stopping test fired: finish the pending x update, then stop
+    int pend;          // rescale by 2^-64 at the start of the next iteration
 };
+
+constexpr double kTqBig = 1.329227995784916e36;     // 2^120: rescale threshold for squared norms
+constexpr double kTqShrink = 5.421010862427522e-20;  // 2^-64
 
 // one half step's scalars from ||w||^2 (single thread)
 __device__ __forceinline__ void tq_half_step(StateOf<double2> *st, TqExtra *q, double ww, double2 &coef,
@@ -79,6 +94,8 @@ struct EpiTqInit : EpiBase<V> {
         q->eta = make_double2(0.0, 0.0);
         q->m = 0;
         q->stop = 0;
+        q->pend = 0;
+        q->xs = 1.0;
         st->rho = make_double2(rr, 0.0);
         if (nb == 0.0) {
             st->rel = 0.0; st->status = HZ_OK; st->done = 1; info->zero_x = 1;
@@ -103,8 +120,9 @@ template <class V>
 struct EpiTqV : EpiBase<V> {
     using typename EpiBase<V>::Acc;
     using typename EpiBase<V>::R;
-    static constexpr int NV = 2;
+    static constexpr int NV = 3;
     StateOf<V> *st;
+    TqExtra *q;
     const Ctl *ctl;
     V *au1, *v;
     const V *rh;
@@ -117,9 +135,11 @@ struct EpiTqV : EpiBase<V> {
         const V vi = Ar<V>::add(y, v[i]);
         v[i] = vi;
         Ar<V>::dotc(acc[0], acc[1], rh[i], vi);
+        Ar<V>::nrm2(acc[2], vi);
     }
     template <int N> __device__ void finish(R (&tot)[N]) const {
         const double2 sig = make_double2((double)tot[0], (double)tot[1]);
+        if (!((double)tot[2] < kTqBig) || !(q->tau * q->tau < kTqBig)) q->pend = 1;
         if (cis_zero(st->rho) || cis_zero(sig)) { st->status = HZ_BREAKDOWN; st->done = 1; }
         else if (st->iter >= ctl->maxit) { st->status = HZ_NOT_CONVERGED; st->done = 1; }
         else st->alpha = cdiv(st->rho, sig);
@@ -145,7 +165,31 @@ __global__ void __launch_bounds__(kVecBlock) k_tq_half1(int n, StateOf<V> *st, T
         A::nrm2(acc[0], wi);
     });
     typename A::R tot[1];
-    if (vec_reduce<V, 1>(acc, red, tot) && threadIdx.x == 0) tq_half_step(st, q, (double)tot[0], q->coef1, q->eta1);
+    if (vec_reduce<V, 1>(acc, red, tot) && threadIdx.x == 0) {
+        if (q->pend) {   // the vectors were scaled by k_tq_rescale before this kernel
+            q->pend = 0;
+            q->tau *= kTqShrink;
+            st->rho = make_double2(st->rho.x * kTqShrink, st->rho.y * kTqShrink);
+            q->xs /= kTqShrink;
+        }
+        tq_half_step(st, q, (double)tot[0], q->coef1, q->eta1);
+        q->eta1x = make_double2(q->eta1.x * q->xs, q->eta1.y * q->xs);
+    }
+}
+
+// range guard: scale u1, v, w, d and A u1 by 2^-64 (exact) when flagged
+template <class V>
+__global__ void __launch_bounds__(kVecBlock) k_tq_rescale(int n, const StateOf<V> *st, const TqExtra *q,
+                                                          V *__restrict__ u1, V *__restrict__ v, V *__restrict__ w,
+                                                          V *__restrict__ d, V *__restrict__ au1) {
+    if (st->done || !q->pend) return;
+    vec_tiles(n, [&](int i) {
+        u1[i] = Ar<V>::pow2(u1[i], kTqShrink);
+        v[i] = Ar<V>::pow2(v[i], kTqShrink);
+        w[i] = Ar<V>::pow2(w[i], kTqShrink);
+        d[i] = Ar<V>::pow2(d[i], kTqShrink);
+        au1[i] = Ar<V>::pow2(au1[i], kTqShrink);
+    });
 }
 
 // Q2 epilogue: au = A u2; d/x update of half step 2j+1; w -= alpha au;
@@ -166,7 +210,7 @@ struct EpiTqW : EpiBase<V> {
         au[i] = y;
         const V di = A::axpy(u1[i], A::scal(q->coef1), d[i]);
         d[i] = di;
-        x[i] = A::axpy(x[i], A::scal(q->eta1), di);
+        x[i] = A::axpy(x[i], A::scal(q->eta1x), di);
         const V wi = A::axmy(w[i], A::scal(st->alpha), y);
         w[i] = wi;
         A::nrm2(acc[0], wi);
@@ -174,9 +218,10 @@ struct EpiTqW : EpiBase<V> {
     }
     template <int N> __device__ void finish(R (&tot)[N]) const {
         tq_half_step(st, q, (double)tot[0], q->coef2, q->eta2);
+        q->eta2x = make_double2(q->eta2.x * q->xs, q->eta2.y * q->xs);
         const int it = st->iter + 1;
         st->iter = it;
-        const double rel = sqrt((double)q->m + 1.0) * q->tau / st->nb;
+        const double rel = sqrt((double)q->m + 1.0) * q->tau * q->xs / st->nb;
         st->rel = rel;
         if (ctl->hist) ctl->hist[it] = rel;
         if (!finite_d(rel)) { st->status = HZ_ERR_NAN; q->stop = 1; }
@@ -199,7 +244,7 @@ __global__ void __launch_bounds__(kVecBlock) k_tq_update(int n, StateOf<V> *st, 
                                                          cudaGraphConditionalHandle h) {
     using A = Ar<V>;
     if (st->done) return;
-    const typename A::S coef = A::scal(q->coef2), eta = A::scal(q->eta2), beta = A::scal(st->beta);
+    const typename A::S coef = A::scal(q->coef2), eta = A::scal(q->eta2x), beta = A::scal(st->beta);
     const bool stop = q->stop != 0;
     vec_tiles(n, [&](int i) {
         const V di = A::axpy(u2[i], coef, d[i]);
@@ -278,7 +323,7 @@ static hz_status tq_build_graph(TqSolver *S, const hz_mat *A, cudaGraph_t g) {
     ei.v = v; ei.h = h;
     tq_spmv<V>(S, A, x, ei, cs);
     EpiTqV<V> ev;
-    ev.st = st; ev.ctl = S->dctl; ev.au1 = au1; ev.v = v; ev.rh = rh; ev.h = h;
+    ev.st = st; ev.q = S->q; ev.ctl = S->dctl; ev.au1 = au1; ev.v = v; ev.rh = rh; ev.h = h;
     tq_spmv<V>(S, A, u1, ev, cs);   // v_0 = A u_1, alpha; sets the loop condition
     HZ_TRY(capture_leaves(cs, &leaves));
     HZ_CUDA(cudaStreamEndCapture(cs, &g));
@@ -286,6 +331,7 @@ static hz_status tq_build_graph(TqSolver *S, const hz_mat *A, cudaGraph_t g) {
     cudaGraph_t body;
     HZ_TRY(add_while(g, leaves, h, &wn, &body));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
+    k_tq_rescale<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->q, u1, v, w, d, au1);
     k_tq_half1<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->q, u2, u1, v, w, au1, S->red);
     EpiTqW<V> ew;
     ew.st = st; ew.q = S->q; ew.ctl = S->dctl; ew.au = au; ew.d = d; ew.x = x; ew.w = w; ew.u1 = u1; ew.rh = rh;

@@ -97,3 +97,28 @@ def test_tfqmr_edge_cases(hz, oracle):
     assert np.linalg.norm(host(x) - bd / lam) <= 1e-12 * np.linalg.norm(bd / lam)
     with pytest.raises(hz.HzError):
         hz.zsolve(M, dev(b), method="tfqmr", mode="mixed")
+
+
+def test_tfqmr_range_guard_c2(hz, oracle):
+    """On the C2 cylinder TFQMR stagnates and its squared-BiCG vectors u, v
+    grow geometrically against w.  The binary64 run follows the oracle's
+    history; the double-float run follows it too, past the point where its
+    vectors leave the binary32 range without the power-of-two rescaling
+    (about 70 iterations), and ends cleanly (no NaN) once the spread between
+    u and w exceeds what binary32 exponents can hold."""
+    A, b = W.c2_cylinder()
+    _, io = oracle.tfqmr(A, b, tol=1e-10, maxit=40)
+    hists, infos = {}, {}
+    for ff, kind in ((False, "csr"), (True, "ffflat")):
+        M = hz.Matrix.from_csr(A, ff=ff)
+        M.set_spmv(kind, 4)
+        hist = torch.zeros(151, dtype=torch.float64, device="cuda")
+        x, info = hz.zsolve(M, dev(b), tol=1e-10, maxit=150, method="tfqmr", hist=hist)
+        assert info.status in (4, 5) and np.isfinite(info.relres_true) and np.isfinite(host(x)).all(), (kind, info)
+        hists[kind], infos[kind] = host(hist), info
+        M.close()
+    assert infos["csr"].status == 4 and infos["csr"].iters == 150
+    assert np.allclose(hists["csr"][:41], io.hist[:41], rtol=1e-9, atol=0)
+    k = infos["ffflat"].iters
+    assert k > 75
+    assert np.allclose(hists["ffflat"][:k + 1], hists["csr"][:k + 1], rtol=1e-6, atol=0)

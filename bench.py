@@ -313,6 +313,47 @@ def compare_modes(hz, torch, full_c4, maxit):
     return out
 
 
+def time_spmv(hz, torch, M, n, stream, reps=20):
+    """Average device time (ms) of one hz_zspmv launch.  Every launch is
+    preceded by a 1 GiB write (flushes the 129 MB L2 and keeps the GPU busy
+    while the host enqueues the next launch, so host launch latency never
+    lands between the events); all launches are enqueued before the one
+    synchronisation."""
+    x = torch.randn(n, dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    flush = torch.empty(8 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        hz.zspmv(M, x, y)
+    ev = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hz.zspmv(M, x, y)
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    return sum(e0.elapsed_time(e1) for e0, e1 in ev) / reps
+
+
+def spmv_h1(hz, torch, stream):
+    """The SpMV on the H1 car-cabin stand-in (Q1 hexahedra, 27-entry rows),
+    double-float block-flat and binary64 CSR-vector, L2 flushed."""
+    import workloads as W
+    A, _ = W.h1_hexcar()
+    peak, _ = peaks()
+    out = {"workload": "H1 Q1 hexahedral car cabin nx=192 kh=0.5 (27-entry rows)", "n": A.n, "nnz": A.nnz,
+           "algorithmic_bytes_per_launch": spmv_bytes(A.n, A.nnz)}
+    for key, ff, kind in (("double_float", True, None), ("binary64", False, None)):
+        M = hz.Matrix.from_csr(A, ff=ff)
+        ms = time_spmv(hz, torch, M, A.n, stream)
+        gbs = spmv_bytes(A.n, A.nnz) / (ms / 1e3) / 1e9
+        out[key] = {"launch_ms": ms, "achieved_gbs": gbs, "frac": gbs / peak,
+                    "kind": M.props()["spmv_kind"], "group": M.props()["group"]}
+        M.close()
+    return out
+
+
 def workload_config(A, maxit, arith="fp64"):
     return {"workload": "C2 jittered P1-FEM cylinder nr=40 ntheta=96 nz=160 k=20 impedance ends, "
                         f"complex128 BiCGStab x0=0 tol=1e-10 maxit={maxit}",
@@ -437,23 +478,7 @@ def main():
     # keeps the GPU busy while the host enqueues the next launch, so host
     # launch latency never lands between the events); all launches are
     # enqueued before the one synchronisation.
-    x_r = torch.randn(A.n, dtype=torch.complex128, device=dev)
-    y_r = torch.empty_like(x_r)
-    flush = torch.empty(8 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    for _ in range(3):
-        hz.zspmv(M, x_r, y_r)
-    ev_sp = []
-    for k in range(20):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        hz.zspmv(M, x_r, y_r)
-        e1.record(stream)
-        ev_sp.append((e0, e1))
-    torch.cuda.synchronize()
-    sp_ms = [e0.elapsed_time(e1) for e0, e1 in ev_sp]
-    sp_avg = sum(sp_ms) / len(sp_ms)
-    del flush
+    sp_avg = time_spmv(hz, torch, M, A.n, stream)
     peak, peak_src = peaks()
     achieved = spmv_bytes(A.n, A.nnz) / (sp_avg / 1e3) / 1e9
     traffic = recorded_traffic()
@@ -480,6 +505,7 @@ def main():
     }
     if rank == 0 and not args.no_compare:
         line["compare"] = compare_modes(hz, torch, args.c4_full, args.compare_maxit)
+        line["spmv_h1"] = spmv_h1(hz, torch, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, dt, it = cpu_oracle_rate(A, b, args.cpu_iters)
         line["cpu_baseline"] = {"value": r, "unit": "GB/s", "cores": 1, "kind": "oracle",

@@ -90,6 +90,21 @@ def test_spmv_fd_and_cylinder(hz, oracle):
     check_spmv(hz, oracle, Ac, K.vectors(Ac.n, 11)[0], ALL_VARIANTS)
 
 
+def test_spmv_hexcar(hz, oracle):
+    """27-entry rows of the Q1 car cabin (a small mesh on every variant, and
+    the full H1 size sampled in the benchmark's configuration)."""
+    A, b = W.hexcar_helmholtz(nx=40)
+    check_spmv(hz, oracle, A, K.vectors(A.n, 71)[0], ALL_VARIANTS)
+    A, b = W.h1_hexcar()
+    x = K.vectors(A.n, 72)[0]
+    ref = oracle.zspmv(A, x)
+    scale = K.row_abs_scale(A, x)
+    M = hz.Matrix.from_csr(A, ff=True)
+    y = host(hz.zspmv(M, dev(x)))
+    assert (np.abs(y - ref) / scale).max() <= TOL
+    M.close()
+
+
 def test_spmv_empty_matrix(hz):
     for ff in (False, True):
         M = hz.Matrix(dev(np.zeros(1, np.int32)), dev(np.zeros(0, np.int32)), dev(np.zeros(0, np.complex128)),

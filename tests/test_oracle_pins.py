@@ -123,6 +123,32 @@ def test_cylinder_fem_invariants():
     assert r.max() <= R + 1e-12
 
 
+def test_hexcar_q1_invariants():
+    """The Q1 car-cabin generator: rigid-body and volume identities of the
+    stiffness and mass, the impedance area, symmetry, 27-entry rows, and the
+    Q1 discrete Laplacian reproducing linear fields in the interior."""
+    from workloads import hexcar as H
+    Kr, Mr = H.q1_reference()
+    assert np.allclose(Kr.sum(axis=1), 0, atol=1e-15) and abs(Mr.sum() - 1.0) < 1e-15
+    assert np.sum(np.linalg.eigvalsh(Kr) < 1e-12) == 1                       # only constants in the null space
+    A, b, P = H.hexcar_helmholtz(nx=40, rcm=False, return_parts=True)
+    K, M, B, xyz, h = P["K"], P["M"], P["B"], P["xyz"], A.meta["h"]
+    one = np.ones(K.shape[0])
+    assert np.abs(K @ one).max() < 1e-12 * abs(K).max()
+    assert abs(one @ (M @ one) - P["volume"]) < 1e-12 * P["volume"]
+    faces = (one @ (B @ one)) / (h * h)
+    assert faces > 0 and abs(faces - round(faces)) < 1e-9                       # whole seat faces
+    S = A.to_scipy()
+    assert abs(S - S.T).max() == 0
+    lens = A.row_lengths()
+    assert lens.max() == 27 and np.mean(lens == 27) > 0.5
+    u = 0.3 * xyz[:, 0] - 1.1 * xyz[:, 1] + 0.7 * xyz[:, 2]
+    full = lens == 27                                                       # nodes with all 8 cubes present
+    assert np.abs((K @ u)[full]).max() < 1e-10 * abs(K).max()
+    # the cut-outs: the cabin holds less air than its bounding box
+    assert P["volume"] < 0.9 * (40 * h) * (round(1.8 / h) * h) * (round(1.3 / h) * h)
+
+
 # --------------------------------------------------------------------------- BLAS-1
 def test_blas1_closed_forms(oracle):
     n = 4096

@@ -14,7 +14,8 @@ structure: complex-symmetric, CSR, 7 to 300 nonzeros per row, RCM-ordered.
 from .csr import CSR, complex_normal  # noqa: F401
 from .fd import fd_helmholtz_box, fd_laplacian_eig  # noqa: F401
 from .cylinder import cylinder_helmholtz  # noqa: F401
+from .hexcar import hexcar_helmholtz  # noqa: F401
 from .configs import (  # noqa: F401
-    c1_small_fd, c2_cylinder, c3_cylinder_large, c4_sweep_systems, c5_inverse_problem,
+    c1_small_fd, c2_cylinder, c3_cylinder_large, c4_sweep_systems, c5_inverse_problem, h1_hexcar,
     c5_directions, blas_sweep_sizes, blas_vectors,
 )

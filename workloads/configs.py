@@ -5,6 +5,7 @@ C2  P1 FEM cylinder    nr=40, ntheta=96, nz=160, k=20, impedance ends (~618k unk
 C3  large cylinder     nr=60, ntheta=128, nz=256, k=20 (~1.97M unknowns)
 C4  frequency sweep    8 geometries x 8 wavenumbers (64 systems of uneven size)
 C5  inverse problem    64^3 FD operator A(theta) = -Lap_h - kappa^2 diag(theta)
+H1  car cabin          Q1 hexahedra, 27-entry rows (stand-in for the car-cavity matrices)
 
 Seeds (numpy PCG64): C1 b 1001, x* 1002; C2 jitter 2001; C3 jitter 3001;
 C4 system s uses 4000 + s; C5 theta field 5001, sample points 5002, data 5003,
@@ -16,6 +17,7 @@ import numpy as np
 from .csr import CSR, complex_normal
 from .fd import fd_helmholtz_box
 from .cylinder import cylinder_helmholtz
+from .hexcar import hexcar_helmholtz
 
 
 def c1_small_fd(m: int = 16):
@@ -65,6 +67,13 @@ def c4_sweep_systems(boxes=C4_BOXES, cylinders=C4_CYLINDERS, kh_list=C4_KH, damp
             out.append((f"cyl{nr}x{nth}x{nz}_kh{kh:.3f}", A, b))
             s += 1
     return out
+
+
+def h1_hexcar(nx: int = 192):
+    """H1: Q1 hexahedral car-cabin cavity, kh = 0.5, 0.05 damping; nx = 192
+    gives about 684k nodes and 17.8M nonzeros with 27-entry rows, the size of
+    the paper's largest car-cavity matrix (649k rows, 15.4M nonzeros)."""
+    return hexcar_helmholtz(nx=nx, kh=0.5, damping=0.05)
 
 
 def smooth_field(m: int, rng: np.random.Generator, sigma: float = 4.0) -> np.ndarray:

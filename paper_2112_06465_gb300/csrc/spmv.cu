@@ -36,6 +36,7 @@ __global__ void k_sell_gather(int64_t slots, const int *__restrict__ src, const 
 }
 
 __global__ void k_split_ff(int64_t n, const double2 *__restrict__ x, float4 *__restrict__ xff) {
+    pdl_release();   // a programmatic dependent (the SpMV) may start streaming the matrix
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         xff[i] = split_ff(x[i]);
 }
@@ -463,6 +464,13 @@ extern "C" HZ_API hz_status hz_zspmv(const hz_mat *A, const hz_z *d_x, hz_z *d_y
     EpiStore<double2> epi{(double2 *)d_y};
     if (is_ff_kind(A->spmv_kind)) {
         HZ_CUDA(split_ff_vec(A->n, (const double2 *)d_x, A->x_ff, (cudaStream_t)stream));
+        if (A->spmv_kind == HZ_SPMV_FF_FLAT && kFlatPipe) {
+            // programmatic dependent of the split: the matrix stream starts
+            // while the split drains; x is gathered after griddepcontrol.wait
+            HZ_CUDA(launch_pdl(k_spmv_ffb<EpiStore<double2>, true>, grid, kFlatThreads, (cudaStream_t)stream,
+                               mat_view<double2>(A), (const float4 *)A->x_ff, epi, RedScratch{}));
+            return HZ_OK;
+        }
         HZ_CUDA(launch_spmv_ff(A->spmv_kind, A->group, mat_view<double2>(A), A->x_ff, epi,
                                RedScratch{}, grid, (cudaStream_t)stream));
         return HZ_OK;

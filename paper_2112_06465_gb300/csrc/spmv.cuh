@@ -397,8 +397,11 @@ __device__ __forceinline__ void flat_rows_ff(const MatView<double2> &A, const fl
 // next group (in this chunk, the next chunk of a long row, or the warp's next
 // row block) are loaded while the current group's values and x gathers are in
 // flight, so a group waits for one memory latency instead of a column load
-// followed by a dependent gather.
-template <class Epi, int NV>
+// followed by a dependent gather.  With kLateX the kernel was launched as a
+// programmatic dependent of the kernel that writes x: it streams its first
+// columns and values before waiting for that kernel (griddepcontrol.wait)
+// and only then gathers x.
+template <class Epi, int NV, bool kLateX = false>
 __device__ __forceinline__ void flat_rows_ff_pipe(const MatView<double2> &A, const float4 *__restrict__ x,
                                                   const Epi &epi, typename Epi::Acc (&acc)[NV], float4 *slab) {
     const uint64_t pol = pol_evict_first();
@@ -436,6 +439,7 @@ __device__ __forceinline__ void flat_rows_ff_pipe(const MatView<double2> &A, con
     int cn[kFlatGroup];
     load_cols(cur, cn);
     f32x2 LS = 0ull, LC = 0ull;   // long-row carry (lane 0)
+    bool x_ready = !kLateX;
     for (;;) {
         int c[kFlatGroup];
         float4 a[kFlatGroup], v[kFlatGroup];
@@ -444,8 +448,15 @@ __device__ __forceinline__ void flat_rows_ff_pipe(const MatView<double2> &A, con
             c[u] = cn[u];
             const int k = cur.kg + lane + 32 * u;
             a[u] = c[u] >= 0 ? ld_stream(A.vff + k, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
-            v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        if constexpr (kLateX) {
+            if (!x_ready) {
+                pdl_wait();
+                x_ready = true;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kFlatGroup; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
         // the next group, and its columns
         const bool chunk_done = cur.kg + 32 * kFlatGroup >= cur.kend;
         Group nxt = cur;
@@ -652,13 +663,16 @@ __global__ void __launch_bounds__(kSpmvBlock, HZ_FF_MIN_BLOCKS) k_spmv_ff(MatVie
     if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
 }
 
-// the block-flat double-float kernel (kFlatThreads threads, row blocks)
-template <class Epi>
+// the block-flat double-float kernel (kFlatThreads threads, row blocks);
+// kLateX: see flat_rows_ff_pipe (only for epilogues that read nothing the
+// preceding kernel writes, and skip() == false)
+template <class Epi, bool kLateX = false>
 __global__ void __launch_bounds__(kFlatThreads, kFlatMinBlocks) k_spmv_ffb(MatView<double2> A, const float4 *__restrict__ x, Epi epi,
                                                            RedScratch red) {
     __shared__ float4 prod[(kFlatThreads / 32) * kFlatCap];   // one slab per warp
     constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
-    pdl_wait();
+    static_assert(!kLateX || kFlatPipe, "the late wait needs the pipelined core");
+    if constexpr (!kLateX) pdl_wait();
     pdl_release();
     if (epi.skip()) {   // grid-uniform early exit; one thread reports it to the epilogue
         if (blockIdx.x == 0 && threadIdx.x == 0) epi.on_skip();
@@ -667,8 +681,9 @@ __global__ void __launch_bounds__(kFlatThreads, kFlatMinBlocks) k_spmv_ffb(MatVi
     typename Epi::Acc acc[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
-    if constexpr (kFlatPipe) flat_rows_ff_pipe<Epi, NV>(A, x, epi, acc, prod);
+    if constexpr (kFlatPipe) flat_rows_ff_pipe<Epi, NV, kLateX>(A, x, epi, acc, prod);
     else flat_rows_ff<Epi, NV>(A, x, epi, acc, prod);
+    if constexpr (kLateX) pdl_wait();   // a warp without row blocks still waits before leaving
     if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
 }
 

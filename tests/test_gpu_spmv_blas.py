@@ -7,6 +7,7 @@ relative to itself.  Integer/structural work (pattern, index base) is exact.
 """
 
 import numpy as np
+import scipy.sparse as sp
 import pytest
 import torch
 
@@ -103,6 +104,29 @@ def test_spmv_hexcar(hz, oracle):
     y = host(hz.zspmv(M, dev(x)))
     assert (np.abs(y - ref) / scale).max() <= TOL
     M.close()
+
+
+def test_spmv_wide_band_fallback(hz, oracle):
+    """Wide bands: random columns anywhere in a 70000-row matrix, and a band
+    whose entries sit 32768 columns left of the diagonal."""
+    n = 70000
+    rng = np.random.default_rng(73)
+    rows, cols = [], []
+    for r in range(0, n, 7):
+        rows += [r, r, r]
+        cols += [r, int(rng.integers(0, n)), min(n - 1, r + 32767 - (r % 32))]
+    S = sp.coo_matrix((K.vectors(len(rows), 74)[0], (rows, cols)), shape=(n, n)).tocsr()
+    S = S + sp.identity(n, dtype=np.complex128, format="csr")
+    A = W.CSR.from_scipy(S.tocsr())
+    check_spmv(hz, oracle, A, K.vectors(n, 75)[0], [("ffflat", 0), ("fftma", 0), ("ff", 4)])
+    # a banded matrix whose offsets reach exactly -32768 and +32767
+    n = 40000
+    rows = np.arange(n)
+    lo = np.maximum(rows - 32768 - (rows % 32) * 0, 0)
+    S = sp.coo_matrix((np.ones(2 * n, np.complex128) * (1 + 1j), (np.r_[rows, rows], np.r_[rows, lo])),
+                      shape=(n, n)).tocsr()
+    A = W.CSR.from_scipy(S)
+    check_spmv(hz, oracle, A, K.vectors(n, 76)[0], [("ffflat", 0)])
 
 
 def test_spmv_empty_matrix(hz):

@@ -12,10 +12,18 @@
 // order and does its scalar update.  Phases are separated by a grid barrier
 // whose wait is bounded in time (it reports HZ_ERR_TIMEOUT instead of
 // hanging if a CTA never arrives).
+//
+// The kernel is written once over the vector format V: complex128 in
+// binary64 (double2), or complex128 in double-float on the binary32 pipes
+// (float4, when every handle of the batch was created with HZ_FLAG_FF): the
+// products then read the handles' split values, the iterate lives in a
+// double-float workspace loaded from and stored to the caller's x, and the
+// per-item reductions are folded in binary64 as before.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
-#include "hz_internal.cuh"
+#include "arith.cuh"
 
 namespace hz {
 
@@ -30,10 +38,24 @@ struct BSys {
     const int *rowptr;
     const int *col;
     const double2 *val;
+    const float4 *vff;           // double-float split of val (double-float batches)
     const double2 *b;
-    double2 *x;
-    double2 *r, *rh, *p, *v, *s, *t;
+    double2 *x;                  // the caller's x0 / solution
+    void *xw;                    // the iterate (double-float batches; else x itself)
+    void *r, *rh, *p, *v, *s, *t;
 };
+
+// the system's vectors in format V
+template <class V> struct BVecs {
+    V *x, *r, *rh, *p, *v, *s, *t;
+};
+template <class V>
+__device__ __forceinline__ BVecs<V> bvecs(const BSys &sy) {
+    BVecs<V> o;
+    o.x = std::is_same<V, double2>::value ? (V *)sy.x : (V *)sy.xw;
+    o.r = (V *)sy.r; o.rh = (V *)sy.rh; o.p = (V *)sy.p; o.v = (V *)sy.v; o.s = (V *)sy.s; o.t = (V *)sy.t;
+    return o;
+}
 
 struct BState {
     double2 rho, rho_old, alpha, omega, beta;
@@ -52,7 +74,7 @@ struct BCtl {
     int err;
 };
 
-enum Phase { P_INIT = 0, P_F1, P_F2, P_F3, P_F4, P_F5, P_TRUE };
+enum Phase { P_INIT = 0, P_F1, P_F2, P_F3, P_F4, P_F5, P_TRUE, P_LOAD, P_STORE };
 
 // bounded grid barrier: gives up after ~1 s and flags the error
 __device__ bool bgrid_sync(BCtl *c) {
@@ -198,90 +220,107 @@ __device__ void item_done(int phase, const BCtl *c, const BSys &sy, BState *S, d
     __syncthreads();
 }
 
-// SpMV rows [r0, r1) of one system with W lanes per row and the phase epilogue
-template <int W>
-__device__ void spmv_item(int phase, const BSys &sy, const BState *S, int r0, int r1, double (&acc)[3]) {
-    const int lane = threadIdx.x & (W - 1);
-    const unsigned gmask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << ((threadIdx.x & 31) & ~(W - 1)));
-    const double2 *x = phase == P_F2 ? sy.p : phase == P_F4 ? sy.s : sy.x;
-    for (int row = r0 + (int)threadIdx.x / W; row < r1; row += kBBlock / W) {
-        const int beg = __ldg(sy.rowptr + row), end = __ldg(sy.rowptr + row + 1);
-        double2 y = make_double2(0.0, 0.0);
-        for (int k = beg + lane; k < end; k += W) cmac(y, ld_stream(sy.val + k), __ldg(x + ld_stream(sy.col + k)));
-#pragma unroll
-        for (int off = W / 2; off > 0; off >>= 1) {
-            y.x += __shfl_xor_sync(gmask, y.x, off, W);
-            y.y += __shfl_xor_sync(gmask, y.y, off, W);
-        }
-        if (lane != 0) continue;
-        if (phase == P_INIT) {
-            const double2 bi = sy.b[row];
-            const double2 ri = make_double2(bi.x - y.x, bi.y - y.y);
-            sy.r[row] = ri; sy.rh[row] = ri;
-            sy.p[row] = make_double2(0.0, 0.0); sy.v[row] = make_double2(0.0, 0.0);
-            acc[0] = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[0]));
-            acc[1] = fma(bi.x, bi.x, fma(bi.y, bi.y, acc[1]));
-        } else if (phase == P_F2) {
-            sy.v[row] = y;
-            const double2 h = sy.rh[row];
-            acc[0] = fma(h.x, y.x, fma(h.y, y.y, acc[0]));
-            acc[1] = fma(h.x, y.y, fma(-h.y, y.x, acc[1]));
-        } else if (phase == P_F4) {
-            sy.t[row] = y;
-            const double2 q = sy.s[row];
-            acc[0] = fma(y.x, q.x, fma(y.y, q.y, acc[0]));
-            acc[1] = fma(y.x, q.y, fma(-y.y, q.x, acc[1]));
-            acc[2] = fma(y.x, y.x, fma(y.y, y.y, acc[2]));
-        } else {   // P_TRUE
-            const double2 bi = sy.b[row];
-            const double rx = bi.x - y.x, ry = bi.y - y.y;
-            acc[0] = fma(rx, rx, fma(ry, ry, acc[0]));
-        }
+// the phase epilogue of one finished row y (lane 0 of the row's group)
+template <class V, class Acc>
+__device__ __forceinline__ void row_epilogue(int phase, const BSys &sy, int row, V y, Acc (&acc)[3]) {
+    using A = Ar<V>;
+    const BVecs<V> w = bvecs<V>(sy);
+    if (phase == P_INIT) {
+        const V bi = A::from_c128(sy.b[row]);
+        const V ri = A::sub(bi, y);
+        w.r[row] = ri; w.rh[row] = ri;
+        w.p[row] = A::zero(); w.v[row] = A::zero();
+        A::nrm2(acc[0], ri);
+        A::nrm2(acc[1], bi);
+    } else if (phase == P_F2) {
+        w.v[row] = y;
+        A::dotc(acc[0], acc[1], w.rh[row], y);
+    } else if (phase == P_F4) {
+        w.t[row] = y;
+        A::dotc(acc[0], acc[1], y, w.s[row]);
+        A::nrm2(acc[2], y);
+    } else {   // P_TRUE
+        A::nrm2(acc[0], A::sub(A::from_c128(sy.b[row]), y));
     }
 }
 
-__device__ void vec_item(int phase, const BSys &sy, const BState *S, int e0, int e1, double (&acc)[3]) {
-    const double2 alpha = S->alpha, omega = S->omega, beta = S->beta;
+// SpMV rows [r0, r1) of one system with W lanes per row and the phase epilogue
+template <int W, class V>
+__device__ void spmv_item(int phase, const BSys &sy, int r0, int r1, typename Ar<V>::Acc (&acc)[3]) {
+    const int lane = threadIdx.x & (W - 1);
+    const unsigned gmask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << ((threadIdx.x & 31) & ~(W - 1)));
+    const BVecs<V> w = bvecs<V>(sy);
+    const V *x = phase == P_F2 ? w.p : phase == P_F4 ? w.s : w.x;
+    for (int row = r0 + (int)threadIdx.x / W; row < r1; row += kBBlock / W) {
+        const int beg = __ldg(sy.rowptr + row), end = __ldg(sy.rowptr + row + 1);
+        V y;
+        if constexpr (std::is_same<V, double2>::value) {
+            y = make_double2(0.0, 0.0);
+            for (int k = beg + lane; k < end; k += W) cmac(y, ld_stream(sy.val + k), __ldg(x + ld_stream(sy.col + k)));
+#pragma unroll
+            for (int off = W / 2; off > 0; off >>= 1) {
+                y.x += __shfl_xor_sync(gmask, y.x, off, W);
+                y.y += __shfl_xor_sync(gmask, y.y, off, W);
+            }
+        } else {
+            // packed double-float sums (re, im) per lane, folded over the group
+            f32x2 S = 0ull, C = 0ull;
+            for (int k = beg + lane; k < end; k += W) ff_cacc(S, C, ff_cprod(ld_stream(sy.vff + k), __ldg(x + ld_stream(sy.col + k))));
+#pragma unroll
+            for (int off = W / 2; off > 0; off >>= 1) {
+                const f32x2 S2 = __shfl_xor_sync(gmask, S, off, W), C2 = __shfl_xor_sync(gmask, C, off, W);
+                f32x2 t, e;
+                two_sum2(S, S2, t, e);
+                S = t;
+                C = add2(C, add2(C2, e));
+            }
+            f32x2 h, l;
+            two_sum2(S, C, h, l);
+            float hr, hi, lr, li;
+            upk2(h, hr, hi);
+            upk2(l, lr, li);
+            y = make_float4(hr, lr, hi, li);
+        }
+        if (lane != 0) continue;
+        row_epilogue<V>(phase, sy, row, y, acc);
+    }
+}
+
+template <class V>
+__device__ void vec_item(int phase, const BSys &sy, const BState *S, int e0, int e1, typename Ar<V>::Acc (&acc)[3]) {
+    using A = Ar<V>;
+    const BVecs<V> w = bvecs<V>(sy);
+    const typename A::S alpha = A::scal(S->alpha), omega = A::scal(S->omega), beta = A::scal(S->beta);
     const bool half = S->half;
     for (int i = e0 + threadIdx.x; i < e1; i += kBBlock) {
         if (phase == P_F1) {
-            double2 q = sy.p[i];
-            const double2 w = sy.v[i];
-            q.x = fma(-omega.x, w.x, q.x); q.x = fma(omega.y, w.y, q.x);
-            q.y = fma(-omega.x, w.y, q.y); q.y = fma(-omega.y, w.x, q.y);
-            double2 o = sy.r[i];
-            cmac(o, beta, q);
-            sy.p[i] = o;
+            w.p[i] = A::axpy(w.r[i], beta, A::axmy(w.p[i], omega, w.v[i]));
         } else if (phase == P_F3) {
-            const double2 w = sy.v[i];
-            double2 o = sy.r[i];
-            o.x = fma(-alpha.x, w.x, o.x); o.x = fma(alpha.y, w.y, o.x);
-            o.y = fma(-alpha.x, w.y, o.y); o.y = fma(-alpha.y, w.x, o.y);
-            sy.s[i] = o;
-            acc[0] = fma(o.x, o.x, fma(o.y, o.y, acc[0]));
-        } else {   // P_F5
-            double2 xi = sy.x[i];
-            cmac(xi, alpha, sy.p[i]);
+            const V o = A::axmy(w.r[i], alpha, w.v[i]);
+            w.s[i] = o;
+            A::nrm2(acc[0], o);
+        } else if (phase == P_F5) {
+            V xi = A::axpy(w.x[i], alpha, w.p[i]);
             if (half) {
-                sy.x[i] = xi;
+                w.x[i] = xi;
                 continue;
             }
-            const double2 si = sy.s[i], ti = sy.t[i];
-            cmac(xi, omega, si);
-            sy.x[i] = xi;
-            double2 ri = si;
-            ri.x = fma(-omega.x, ti.x, ri.x); ri.x = fma(omega.y, ti.y, ri.x);
-            ri.y = fma(-omega.x, ti.y, ri.y); ri.y = fma(-omega.y, ti.x, ri.y);
-            sy.r[i] = ri;
-            const double2 h = sy.rh[i];
-            acc[0] = fma(h.x, ri.x, fma(h.y, ri.y, acc[0]));
-            acc[1] = fma(h.x, ri.y, fma(-h.y, ri.x, acc[1]));
-            acc[2] = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[2]));
+            const V si = w.s[i];
+            w.x[i] = A::axpy(xi, omega, si);
+            const V ri = A::axmy(si, omega, w.t[i]);
+            w.r[i] = ri;
+            A::dotc(acc[0], acc[1], w.rh[i], ri);
+            A::nrm2(acc[2], ri);
+        } else if (phase == P_LOAD) {
+            w.x[i] = A::from_c128(sy.x[i]);
+        } else {   // P_STORE
+            sy.x[i] = A::to_c128(w.x[i]);
         }
     }
 }
 
 // one phase over the systems in the block's active table
+template <class V>
 __device__ void run_phase(int phase, const BCtl *c, const BSys *sys, BState *st, double *partials, const int *act,
                           const int *pref, int nact) {
     const bool spmv = phase == P_INIT || phase == P_F2 || phase == P_F4 || phase == P_TRUE;
@@ -299,20 +338,26 @@ __device__ void run_phase(int phase, const BCtl *c, const BSys *sys, BState *st,
         __shared__ int skip;
         if (threadIdx.x == 0) {
             const int done = *(volatile int *)&S->done, half = *(volatile int *)&S->half;
-            skip = (phase != P_INIT && phase != P_TRUE && done) || (phase == P_F4 && half);
+            skip = (phase != P_INIT && phase != P_TRUE && phase != P_LOAD && phase != P_STORE && done) ||
+                   (phase == P_F4 && half);
         }
         __syncthreads();
         if (skip) continue;
-        double acc[3] = {0.0, 0.0, 0.0};
+        typename Ar<V>::Acc va[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Ar<V>::acc_zero(va[q]);
+        double acc[3];
         if (spmv) {
             const int r0 = local * sy.rows_per_item, r1 = min(sy.n, r0 + sy.rows_per_item);
             switch (sy.W) {
-                case 2: spmv_item<2>(phase, sy, S, r0, r1, acc); break;
-                case 4: spmv_item<4>(phase, sy, S, r0, r1, acc); break;
-                case 8: spmv_item<8>(phase, sy, S, r0, r1, acc); break;
-                case 16: spmv_item<16>(phase, sy, S, r0, r1, acc); break;
-                default: spmv_item<32>(phase, sy, S, r0, r1, acc); break;
+                case 2: spmv_item<2, V>(phase, sy, r0, r1, va); break;
+                case 4: spmv_item<4, V>(phase, sy, r0, r1, va); break;
+                case 8: spmv_item<8, V>(phase, sy, r0, r1, va); break;
+                case 16: spmv_item<16, V>(phase, sy, r0, r1, va); break;
+                default: spmv_item<32, V>(phase, sy, r0, r1, va); break;
             }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc[q] = (double)Ar<V>::total(va[q]);
             const int nit = sy.sp_items;
             if (phase == P_F4) item_done<3>(phase, c, sy, S, partials, sy.sp_item0 + local, sy.sp_item0, nit, acc);
             else if (phase == P_TRUE) {
@@ -324,7 +369,9 @@ __device__ void run_phase(int phase, const BCtl *c, const BSys *sys, BState *st,
             }
         } else {
             const int e0 = local * kBVecItem, e1 = min(sy.n, e0 + kBVecItem);
-            vec_item(phase, sy, S, e0, e1, acc);
+            vec_item<V>(phase, sy, S, e0, e1, va);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc[q] = (double)Ar<V>::total(va[q]);
             const int nit = sy.vc_items;
             const int g = sy.vc_item0 + local;
             if (phase == P_F3) {
@@ -366,30 +413,43 @@ __device__ int build_active(int spmv_items, const BCtl *c, const BSys *sys, cons
     return nact;
 }
 
+template <class V>
 __global__ void __launch_bounds__(kBBlock) k_batched(BCtl *c, const BSys *sys, BState *st, double *partials) {
     __shared__ int act[kBMaxSys];
     __shared__ int pref_sp[kBMaxSys + 1];
     __shared__ int pref_vc[kBMaxSys + 1];
-    int nact = build_active(1, c, sys, st, act, pref_sp, false);
-    run_phase(P_INIT, c, sys, st, partials, act, pref_sp, nact);
+    constexpr bool kFF = !std::is_same<V, double2>::value;
+    int nact;
+    if constexpr (kFF) {   // the iterate into the double-float workspace
+        nact = build_active(0, c, sys, st, act, pref_vc, false);
+        run_phase<V>(P_LOAD, c, sys, st, partials, act, pref_vc, nact);
+        if (!bgrid_sync(c)) return;
+    }
+    nact = build_active(1, c, sys, st, act, pref_sp, false);
+    run_phase<V>(P_INIT, c, sys, st, partials, act, pref_sp, nact);
     if (!bgrid_sync(c)) return;
     for (int guard = 0; guard <= c->maxit + 1; ++guard) {
         nact = build_active(1, c, sys, st, act, pref_sp, true);
         if (nact == 0) break;
         build_active(0, c, sys, st, act, pref_vc, true);
-        run_phase(P_F1, c, sys, st, partials, act, pref_vc, nact);
+        run_phase<V>(P_F1, c, sys, st, partials, act, pref_vc, nact);
         if (!bgrid_sync(c)) return;
-        run_phase(P_F2, c, sys, st, partials, act, pref_sp, nact);
+        run_phase<V>(P_F2, c, sys, st, partials, act, pref_sp, nact);
         if (!bgrid_sync(c)) return;
-        run_phase(P_F3, c, sys, st, partials, act, pref_vc, nact);
+        run_phase<V>(P_F3, c, sys, st, partials, act, pref_vc, nact);
         if (!bgrid_sync(c)) return;
-        run_phase(P_F4, c, sys, st, partials, act, pref_sp, nact);
+        run_phase<V>(P_F4, c, sys, st, partials, act, pref_sp, nact);
         if (!bgrid_sync(c)) return;
-        run_phase(P_F5, c, sys, st, partials, act, pref_vc, nact);
+        run_phase<V>(P_F5, c, sys, st, partials, act, pref_vc, nact);
         if (!bgrid_sync(c)) return;
     }
     nact = build_active(1, c, sys, st, act, pref_sp, false);
-    run_phase(P_TRUE, c, sys, st, partials, act, pref_sp, nact);
+    run_phase<V>(P_TRUE, c, sys, st, partials, act, pref_sp, nact);
+    if constexpr (kFF) {   // the solution back to the caller's x
+        if (!bgrid_sync(c)) return;
+        nact = build_active(0, c, sys, st, act, pref_vc, false);
+        run_phase<V>(P_STORE, c, sys, st, partials, act, pref_vc, nact);
+    }
 }
 
 }  // namespace hz
@@ -407,8 +467,15 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<BSys> hs(nsys);
     int64_t sp = 0, vc = 0, vec_elems = 0;
+    // double-float when every handle carries the split values and runs a
+    // double-float SpMV kind; binary64 otherwise
+    bool ff = true;
     for (int k = 0; k < nsys; ++k) {
         HZ_CHECK(A[k], "hz_zsolve_batched: null matrix handle");
+        if (A[k]->n > 0 && !(A[k]->val_ff && is_ff_kind(A[k]->spmv_kind))) ff = false;
+    }
+    const int nvec = ff ? 7 : 6;
+    for (int k = 0; k < nsys; ++k) {
         HZ_CHECK(A[k]->n == 0 || (d_b[k] && d_x[k]), "hz_zsolve_batched: null vector");
         BSys &y = hs[k];
         y.n = A[k]->n;
@@ -418,8 +485,8 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
         y.sp_items = (y.n + y.rows_per_item - 1) / y.rows_per_item;
         y.vc_item0 = (int)vc;
         y.vc_items = (y.n + kBVecItem - 1) / kBVecItem;
-        y.rowptr = A[k]->rowptr; y.col = A[k]->col; y.val = A[k]->val;
-        y.b = (const double2 *)d_b[k]; y.x = (double2 *)d_x[k];
+        y.rowptr = A[k]->rowptr; y.col = A[k]->col; y.val = A[k]->val; y.vff = A[k]->val_ff;
+        y.b = (const double2 *)d_b[k]; y.x = (double2 *)d_x[k]; y.xw = nullptr;
         sp += y.sp_items;
         vc += y.vc_items;
         vec_elems += y.n;
@@ -432,7 +499,7 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
     BSys *dsys = nullptr;
     BCtl *ctl = nullptr;
     auto cleanup = [&]() { cudaFree(work); cudaFree(partials); cudaFree(st); cudaFree(dsys); cudaFree(ctl); };
-    if (cudaMalloc(&work, sizeof(double2) * std::max<int64_t>(6 * vec_elems, 1)) != cudaSuccess ||
+    if (cudaMalloc(&work, sizeof(double2) * std::max<int64_t>(nvec * vec_elems, 1)) != cudaSuccess ||
         cudaMalloc(&partials, sizeof(double) * 4 * std::max<int64_t>(std::max(sp, vc), 1)) != cudaSuccess ||
         cudaMalloc(&st, sizeof(BState) * nsys) != cudaSuccess || cudaMalloc(&dsys, sizeof(BSys) * nsys) != cudaSuccess ||
         cudaMalloc(&ctl, sizeof(BCtl)) != cudaSuccess) {
@@ -441,9 +508,9 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
         return HZ_ERR_ALLOC;
     }
     int64_t off = 0;
-    for (auto &y : hs) {
-        double2 **vecs[6] = {&y.r, &y.rh, &y.p, &y.v, &y.s, &y.t};
-        for (auto v : vecs) { *v = work + off; off += y.n; }
+    for (auto &y : hs) {   // 16-byte elements in either format
+        void **vecs[7] = {&y.r, &y.rh, &y.p, &y.v, &y.s, &y.t, &y.xw};
+        for (int q = 0; q < nvec; ++q) { *vecs[q] = work + off; off += y.n; }
     }
     BCtl hc{};
     hc.tol = tol; hc.maxit = maxit; hc.nsys = nsys;
@@ -458,13 +525,14 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     DevInfo d;
     int occ = 0;
+    void *kern = ff ? (void *)k_batched<float4> : (void *)k_batched<double2>;
     if (e == cudaSuccess && dev_info(&d) == HZ_OK)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched, kBBlock, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBBlock, 0);
     if (e == cudaSuccess && occ < 1) e = cudaErrorInvalidConfiguration;
     if (e == cudaSuccess) {
         dim3 grid(d.num_sms * std::min(occ, 4)), block(kBBlock);
         void *args[] = {&ctl, &dsys, &st, &partials};
-        e = cudaLaunchCooperativeKernel((void *)k_batched, grid, block, args, 0, s);
+        e = cudaLaunchCooperativeKernel(kern, grid, block, args, 0, s);
     }
     BCtl hc2{};
     if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), st, sizeof(BState) * nsys, cudaMemcpyDeviceToHost, s);

@@ -245,7 +245,8 @@ def compare_modes(hz, torch, full_c4, maxit):
     solver (complex64 inner BiCGStab, binary64 outer refinement), the
     double-float solver with Jacobi right preconditioning, double-float
     BiCGStab(4) and TFQMR (iterations in steps of two products with A) and,
-    for all systems at once, the persistent batched binary64 solver.  Times are CUDA
+    for all systems at once, the persistent batched solver in binary64 and
+    in double-float.  Times are CUDA
     events around each call, after one untimed call of each kind (graph
     capture).  Speedups are over the systems every variant solved."""
     import workloads as W
@@ -282,8 +283,13 @@ def compare_modes(hz, torch, full_c4, maxit):
             hz.zsolve(M, b, tol=1e-10, maxit=maxit, **kw)          # graph capture
             (_, info), ms = timed(lambda: hz.zsolve(M, b, tol=1e-10, maxit=maxit, **kw))
             res[key].append((ms, info))
-    hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit)
-    (_, binfos), bms = timed(lambda: hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit))
+    batched = {}
+    for key, kind in (("batched_fp64", "csr"), ("batched_double_float", "ffflat")):
+        for M in mats:   # the batch runs double-float when every handle's kind is
+            M.set_spmv(kind, M.props()["group"] if kind == "csr" else 0)
+        hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit)
+        batched[key] = timed(lambda: hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit))
+    binfos = batched["batched_fp64"][0][1]
     ok_all = [all(res[k][i][1].converged for k in variants) and binfos[i].converged
               for i in range(len(mats))]
 
@@ -300,14 +306,15 @@ def compare_modes(hz, torch, full_c4, maxit):
     for key in variants:
         out[key] = summary(res[key])
     out["mixed"]["outer"] = sum(i.outer for _, i in res["mixed"])
-    out["batched_fp64"] = {"s_total": bms / 1e3, "converged": sum(1 for i in binfos if i.converged),
-                           "iters": sum(i.iters for i in binfos),
-                           "max_relres_true": max(i.relres_true for i in binfos)}
+    for key, ((_, infs), ms) in batched.items():
+        out[key] = {"s_total": ms / 1e3, "converged": sum(1 for i in infs if i.converged),
+                    "iters": sum(i.iters for i in infs), "max_relres_true": max(i.relres_true for i in infs)}
     base = out["fp64_binary64"]["s_on_common"]
     out["speedup_vs_fp64_binary64_on_common"] = {
         k: base / max(out[k]["s_on_common"], 1e-12) for k in variants if k != "fp64_binary64"}
     out["speedup_vs_fp64_binary64_all_systems"] = {
-        k: out["fp64_binary64"]["s_total"] / out[k]["s_total"] for k in list(variants)[1:] + ["batched_fp64"]}
+        k: out["fp64_binary64"]["s_total"] / out[k]["s_total"]
+        for k in list(variants)[1:] + ["batched_fp64", "batched_double_float"]}
     for M in mats:
         M.close()
     return out

@@ -313,6 +313,9 @@ HZ_API hz_status hz_zsolve_opts(hz_mat *A, const hz_z *d_b, hz_z *d_x,
  * on the device; all systems advance together through the phases of the
  * iteration and leave the batch as they converge.  Same algorithm,
  * stopping rule and status semantics as hz_zsolve (no restart), per system.
+ * The batch runs in double-float arithmetic when every handle (with n > 0)
+ * was created with HZ_FLAG_FF and its SpMV kind is a double-float one, in
+ * binary64 otherwise.  d_x[s] holds x0 on entry and the solution on exit.
  * h_info has nsys entries.  Synchronises `stream`.
  */
 HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, const hz_z *const *d_b,

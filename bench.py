@@ -272,6 +272,7 @@ def compare_modes(hz, torch, full_c4, maxit):
         "fp64_binary64": ("csr", dict(mode="fp64")),
         "fp64_double_float": ("ffflat", dict(mode="fp64")),
         "mixed": ("csr", dict(mode="mixed")),
+        "mixed_double_float": ("ffflat", dict(mode="mixed")),
         "fp64_double_float_jacobi": ("ffflat", dict(mode="fp64", precond="jacobi")),
         "bicgstab4_double_float": ("ffflat", dict(method="bicgstabl", ell=4)),
         "tfqmr_double_float": ("ffflat", dict(method="tfqmr")),

@@ -341,6 +341,7 @@ struct Solver {
     int kind = 0, group = 4;
     int grid_spmv = 1, grid_vec = 1;
     int grid_spmv_cv = 1;   // grid of the binary64/complex64 CSR or SELL kernels
+    int grid_c64 = 1;       // grid of the block-flat complex64 kernel
     bool pdl = false;       // programmatic dependent launches inside the iteration
     void *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
     float2 *r32 = nullptr, *rh32 = nullptr, *p32 = nullptr, *v32 = nullptr, *s32 = nullptr, *t32 = nullptr,
@@ -433,6 +434,13 @@ static void spmv_on(const Solver *S, const hz_mat *A, const V *x, const Epi &e, 
     const bool sell = S->kind == HZ_SPMV_SELL || S->kind == HZ_SPMV_SELL_FF;
     if constexpr (std::is_same<V, float4>::value) {
         launch_spmv_ff(S->kind, S->group, mat_view<double2>(A), x, e, S->red, S->grid_spmv, cs, pdl);
+    } else if constexpr (std::is_same<V, float2>::value) {
+        // complex64 inner operator: block-flat when the handle runs a block-flat kind
+        if (A->fblk && (S->kind == HZ_SPMV_FF_FLAT || S->kind == HZ_SPMV_FF_TMA))
+            launch_k(pdl, k_spmv_c64b<Epi>, S->grid_c64, kFlatThreads, cs, mat_view<float2>(A), x, e, S->red);
+        else
+            launch_spmv<V>(S->kind == HZ_SPMV_SELL || S->kind == HZ_SPMV_SELL_FF ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR,
+                           S->group, mat_view<V>(A), x, e, S->red, S->grid_spmv_cv, cs, pdl);
     } else {
         launch_spmv<V>(sell ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR, S->group, mat_view<V>(A), x, e, S->red,
                        S->grid_spmv_cv, cs, pdl);
@@ -580,6 +588,7 @@ static hz_status get_solver(hz_mat *A, uint32_t mode, cudaStream_t s, Solver **o
         S->grid_spmv = spmv_grid(A, S->kind, S->group);
         const bool sell = S->kind == HZ_SPMV_SELL || S->kind == HZ_SPMV_SELL_FF;
         S->grid_spmv_cv = spmv_grid(A, sell ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR, S->group);
+        S->grid_c64 = A->fblk ? c64_flat_grid(A) : 1;
         // HZ_PDL=1 (environment) captures F2..F5 as programmatic dependent
         // launches; measured slower on the C2 solve (185 vs 175 us per
         // iteration), so plain launches are the default

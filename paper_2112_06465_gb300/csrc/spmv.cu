@@ -62,6 +62,7 @@ template <>
 MatView<float2> mat_view<float2>(const hz_mat *A) {
     MatView<float2> v{};
     v.n = A->n; v.rowptr = A->rowptr; v.col = A->col; v.val = A->val32;
+    v.nfblk = A->nfblk; v.fblk = A->fblk;
     v.nchunks = A->sell_nchunks; v.chunk_off = A->sell_chunk_off; v.chunk_w = A->sell_chunk_w;
     v.perm = A->sell_perm; v.scol = A->sell_col; v.sval = A->sell_val32;
     return v;
@@ -92,6 +93,18 @@ int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap) {
     const bool sell = kind == HZ_SPMV_SELL || kind == HZ_SPMV_SELL_FF;
     int64_t threads = sell ? (int64_t)A->sell_nchunks * 32 : (int64_t)A->n * group;
     return stream_grid(d, threads, kSpmvBlock, blocks_per_sm_cap);
+}
+
+int c64_flat_grid(const hz_mat *A) {
+    DevInfo d;
+    if (dev_info(&d) != HZ_OK) return 1;
+    static int occ = 0;
+    if (occ == 0 &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_c64b<EpiStore<float2>>, kFlatThreads, 0) !=
+             cudaSuccess || occ < 1))
+        occ = 1;
+    const int64_t g = std::min<int64_t>(A->nfblk, (int64_t)d.num_sms * occ);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
 }
 
 // lanes per row from the row-length histogram: about four entries per lane,
@@ -486,6 +499,13 @@ extern "C" HZ_API hz_status hz_cspmv(hz_mat *A, const hz_c *d_x, hz_c *d_y, void
     HZ_CHECK(d_x && d_y, "hz_cspmv: null vector");
     HZ_CHECK((const void *)d_x != (const void *)d_y, "hz_cspmv: x and y must not alias");
     HZ_TRY(ensure_c64(A, (cudaStream_t)stream));
+    if (A->fblk && (A->spmv_kind == HZ_SPMV_FF_FLAT || A->spmv_kind == HZ_SPMV_FF_TMA)) {
+        // the row blocks exist: the block-flat complex64 kernel
+        EpiStore<float2> epi{(float2 *)d_y};
+        HZ_CUDA(launch_k(false, k_spmv_c64b<EpiStore<float2>>, c64_flat_grid(A), kFlatThreads, (cudaStream_t)stream,
+                         mat_view<float2>(A), (const float2 *)d_x, epi, RedScratch{}));
+        return HZ_OK;
+    }
     const int kind = (A->spmv_kind == HZ_SPMV_SELL || A->spmv_kind == HZ_SPMV_SELL_FF) ? HZ_SPMV_SELL
                                                                                      : HZ_SPMV_CSR_VECTOR;
     const int grid = spmv_grid(A, kind, A->group);

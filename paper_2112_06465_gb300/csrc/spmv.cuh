@@ -709,6 +709,87 @@ __global__ void __launch_bounds__(kFlatThreads) k_spmv_fft(MatView<double2> A, c
     if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
 }
 
+// ---------------------------------------------------------------------------
+// Block-flat complex64 kernel: the row blocks and two phases of the
+// double-float kernel with complex64 values (the mixed solver's inner
+// operator) and plain binary32 arithmetic: phase 1 forms a_k x_col(k) (four
+// FMA-pipe operations) into the warp's slab, phase 2 sums each row in
+// storage order.
+template <class Epi, int NV>
+__device__ __forceinline__ void flat_rows_c64(const MatView<float2> &A, const float2 *__restrict__ x, const Epi &epi,
+                                              typename Epi::Acc (&acc)[NV], float2 *slab) {
+    const uint64_t pol = pol_evict_first();
+    const int lane = threadIdx.x & 31;
+    float2 *prod = slab + (threadIdx.x >> 5) * kFlatCap;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < A.nfblk; b += nwarps) {
+        const int r0 = __ldg(A.fblk + b), r1 = __ldg(A.fblk + b + 1);
+        const int kb = __ldg(A.rowptr + r0), ke = __ldg(A.rowptr + r1);
+        const bool long_row = r1 - r0 == 1 && ke - kb > kFlatCap;
+        float2 carry = make_float2(0.f, 0.f);   // long-row carry (lane 0)
+        for (int kc = kb;; kc += kFlatCap) {
+            const int kend = min(ke, kc + kFlatCap);
+#pragma unroll 1
+            for (int g = 0; g < kFlatU; g += kFlatGroup) {
+                int c[kFlatGroup];
+                float2 a[kFlatGroup], v[kFlatGroup];
+#pragma unroll
+                for (int u = 0; u < kFlatGroup; ++u) {
+                    const int k = kc + lane + 32 * (g + u);
+                    c[u] = k < kend ? ld_stream(A.col + k, pol) : -1;
+                    a[u] = k < kend ? ld_stream(A.val + k) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < kFlatGroup; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < kFlatGroup; ++u)
+                    if (c[u] >= 0) prod[lane + 32 * (g + u)] = cmul(a[u], v[u]);
+                if (kc + 32 * (g + kFlatGroup) >= kend) break;
+            }
+            __syncwarp();
+            for (int row = r0 + lane; row < r1; row += 32) {
+                const int beg = max(__ldg(A.rowptr + row), kc), end = min(__ldg(A.rowptr + row + 1), kend);
+                float2 y = make_float2(0.f, 0.f);
+                for (int k = beg; k < end; ++k) {
+                    const float2 q = prod[k - kc];
+                    y.x += q.x;
+                    y.y += q.y;
+                }
+                if (long_row) {
+                    carry.x += y.x;
+                    carry.y += y.y;
+                    if (kend == ke) epi.row(row, carry, acc);
+                } else {
+                    epi.row(row, y, acc);
+                }
+            }
+            __syncwarp();
+            if (kend >= ke) break;
+        }
+    }
+}
+
+template <class Epi>
+__global__ void __launch_bounds__(kFlatThreads) k_spmv_c64b(MatView<float2> A, const float2 *__restrict__ x, Epi epi,
+                                                            RedScratch red) {
+    __shared__ float2 prod[(kFlatThreads / 32) * kFlatCap];   // one slab per warp
+    constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
+    pdl_wait();
+    pdl_release();
+    if (epi.skip()) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) epi.on_skip();
+        return;
+    }
+    typename Epi::Acc acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
+    flat_rows_c64<Epi, NV>(A, x, epi, acc, prod);
+    if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
+}
+
+// grid of k_spmv_c64b: the CTAs that fit at once
+int c64_flat_grid(const hz_mat *A);
+
 // binary64 -> double-float split of a vector (xff[i] = split_ff(x[i])), on stream s
 cudaError_t split_ff_vec(int n, const double2 *x, float4 *xff, cudaStream_t s);
 

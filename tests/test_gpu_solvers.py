@@ -151,8 +151,10 @@ def test_mixed_precision_fd_boxes(hz, oracle):
         A = W.fd_helmholtz_box(m, kh=kh, damping=0.05)
         b = K.vectors(A.n, 300 + m)[0]
         xm, dm = oracle.refine_mixed(A, b, tol=1e-10)
-        for sell in (False, True):
-            M = hz.Matrix.from_csr(A, c64=True, sell=sell)
+        for sell, ff in ((False, False), (True, False), (False, True)):
+            # the double-float handle runs a double-float outer residual and
+            # the block-flat complex64 inner product
+            M = hz.Matrix.from_csr(A, c64=True, sell=sell, ff=ff)
             x, info = hz.zsolve(M, dev(b), tol=1e-10, maxit=20000, mode="mixed")
             if dm["status"] == 0:
                 assert info.converged, info

@@ -180,14 +180,17 @@ def test_spmv_c2_full_size_sampled(hz, oracle):
         M.close()
 
 
-def test_cspmv_complex64(hz, oracle):
-    A, b = K.small_cylinder()
-    x = K.vectors(A.n, 5)[0].astype(np.complex64)
-    M = hz.Matrix.from_csr(A, c64=True)
-    y = host(hz.cspmv(M, dev(x)))
-    ref = oracle.cspmv(A, x)
-    scale = K.row_abs_scale(A, x.astype(np.complex128))
-    assert np.all(np.abs(y - ref) <= 4e-6 * scale)
+@pytest.mark.parametrize("ff", [False, True])
+def test_cspmv_complex64(hz, oracle, ff):
+    """CSR-vector (plain handle) and block-flat (double-float handle) complex64
+    products, including rows longer than one 512-entry block."""
+    for A, x in ((K.small_cylinder()[0], None), (K.random_csr(3000, 6, max_row=12, long_rows=(2500, 1300)), None)):
+        x = K.vectors(A.n, 5)[0].astype(np.complex64)
+        M = hz.Matrix.from_csr(A, c64=True, ff=ff)
+        y = host(hz.cspmv(M, dev(x)))
+        ref = oracle.cspmv(A, x)
+        scale = K.row_abs_scale(A, x.astype(np.complex128))
+        assert np.all(np.abs(y - ref) <= 4e-6 * scale)
 
 
 # --------------------------------------------------------------------------- BLAS-1

@@ -344,6 +344,45 @@ def time_spmv(hz, torch, M, n, stream, reps=20):
     return sum(e0.elapsed_time(e1) for e0, e1 in ev) / reps
 
 
+def blas_sweep(hz, torch, stream, reps=10):
+    """The complex128 BLAS-1 sweep of the C2 configuration: zdotc, zaxpy,
+    zscal and dznrm2 over lengths 1e3 .. 1e8 in half decades.  Each call is
+    preceded by a 1 GiB write (cold L2, GPU busy while the host enqueues),
+    timed with CUDA events; median of `reps`.  Bytes: zdotc 32n, zaxpy 48n,
+    zscal 32n, dznrm2 16n.  Working sets under the 129 MB L2 are marked."""
+    import workloads as W
+    import statistics as st_
+    flush = torch.empty(8 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    alpha = torch.tensor([0.5 - 0.25j], dtype=torch.complex128, device="cuda")
+    out = {"sizes": [], "zdotc": [], "zaxpy": [], "zscal": [], "dznrm2": []}
+    nbytes = {"zdotc": 32, "zaxpy": 48, "zscal": 32, "dznrm2": 16}
+    for n in W.blas_sweep_sizes():
+        x = torch.randn(n, dtype=torch.complex128, device="cuda")
+        y = torch.randn(n, dtype=torch.complex128, device="cuda")
+        d = torch.empty(1, dtype=torch.complex128, device="cuda")
+        r = torch.empty(1, dtype=torch.float64, device="cuda")
+        calls = {"zdotc": lambda: hz.zdotc(x, y, out=d), "zaxpy": lambda: hz.zaxpy(alpha, x, y),
+                 "zscal": lambda: hz.zscal(alpha, x), "dznrm2": lambda: hz.dznrm2(x, out=r)}
+        out["sizes"].append(n)
+        for op, fn in calls.items():
+            fn()
+            ev = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                ev.append((e0, e1))
+            torch.cuda.synchronize()
+            us = 1e3 * st_.median(a.elapsed_time(b) for a, b in ev)
+            gbs = nbytes[op] * n / (us * 1e-6) / 1e9
+            out[op].append({"us": round(us, 2), "gbs": round(gbs, 1),
+                            "l2_resident": nbytes[op] * n < L2_BYTES})
+        del x, y
+    return out
+
+
 def spmv_h1(hz, torch, stream):
     """The SpMV on the H1 car-cabin stand-in (Q1 hexahedra, 27-entry rows),
     double-float block-flat and binary64 CSR-vector, L2 flushed."""
@@ -514,6 +553,7 @@ def main():
     if rank == 0 and not args.no_compare:
         line["compare"] = compare_modes(hz, torch, args.c4_full, args.compare_maxit)
         line["spmv_h1"] = spmv_h1(hz, torch, stream)
+        line["blas_sweep"] = blas_sweep(hz, torch, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, dt, it = cpu_oracle_rate(A, b, args.cpu_iters)
         line["cpu_baseline"] = {"value": r, "unit": "GB/s", "cores": 1, "kind": "oracle",

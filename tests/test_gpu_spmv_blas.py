@@ -129,6 +129,27 @@ def test_spmv_wide_band_fallback(hz, oracle):
     check_spmv(hz, oracle, A, K.vectors(n, 76)[0], [("ffflat", 0)])
 
 
+def test_spmv_autotune(hz, oracle):
+    """HZ_FLAG_AUTOTUNE times every variant the handle has copies for and keeps
+    the fastest; the kept variant computes the same product, and a solve and
+    a batched sweep run on the tuned handles."""
+    A, b = K.small_cylinder()
+    x = K.vectors(A.n, 77)[0]
+    ref = oracle.zspmv(A, x)
+    scale = K.row_abs_scale(A, x)
+    for ff in (False, True):
+        M = hz.Matrix.from_csr(A, ff=ff, sell=True, autotune=True)
+        props = M.props()
+        assert props["spmv_kind"] in ((0, 1) if not ff else (0, 1, 2, 3, 4, 5))
+        y = host(hz.zspmv(M, dev(x)))
+        assert (np.abs(y - ref) / scale).max() <= TOL, props
+        xs, info = hz.zsolve(M, dev(b), tol=1e-10, maxit=3000)
+        assert info.converged
+        xb, infos = hz.zsolve_batched([M, M], [dev(b), dev(b)], tol=1e-10, maxit=3000)
+        assert all(i.converged for i in infos)
+        M.close()
+
+
 def test_spmv_empty_matrix(hz):
     for ff in (False, True):
         M = hz.Matrix(dev(np.zeros(1, np.int32)), dev(np.zeros(0, np.int32)), dev(np.zeros(0, np.complex128)),

@@ -201,6 +201,32 @@ def test_spmv_c2_full_size_sampled(hz, oracle):
         M.close()
 
 
+def test_spmv_c3_full_size(hz, oracle):
+    """C3 cylinder (1,974,017 rows, 29,414,401 nonzeros; axis rows of 387
+    entries, so the long-row passes of the block-flat kernel run) in the
+    complex128 kinds the solvers use, and the complex64 block-flat product of
+    the mixed solver's inner iteration, every entry against the oracle."""
+    A, _ = W.c3_cylinder_large()
+    assert int(np.diff(A.rowptr).max()) > 256
+    x = K.vectors(A.n, 3002)[0]
+    ref = oracle.zspmv(A, x)
+    scale = K.row_abs_scale(A, x)
+    xd = dev(x)
+    for ff in (False, True):
+        M = hz.Matrix.from_csr(A, ff=ff, c64=ff)
+        y = host(hz.zspmv(M, xd))
+        rel = np.abs(y - ref) / scale
+        assert rel.max() <= TOL, (ff, float(rel.max()))
+        if ff:
+            x32 = x.astype(np.complex64)
+            y32 = host(hz.cspmv(M, dev(x32)))
+            ref32 = oracle.cspmv(A, x32)
+            scale32 = K.row_abs_scale(A, x32.astype(np.complex128))
+            assert np.all(np.abs(y32 - ref32) <= 4e-6 * scale32)
+        M.check()
+        M.close()
+
+
 @pytest.mark.parametrize("ff", [False, True])
 def test_cspmv_complex64(hz, oracle, ff):
     """CSR-vector (plain handle) and block-flat (double-float handle) complex64

@@ -321,23 +321,24 @@ def compare_modes(hz, torch, full_c4, maxit):
     return out
 
 
-def time_spmv(hz, torch, M, n, stream, reps=20):
-    """Average device time (ms) of one hz_zspmv launch.  Every launch is
-    preceded by a 1 GiB write (flushes the 129 MB L2 and keeps the GPU busy
-    while the host enqueues the next launch, so host launch latency never
-    lands between the events); all launches are enqueued before the one
-    synchronisation."""
-    x = torch.randn(n, dtype=torch.complex128, device="cuda")
+def time_spmv(hz, torch, M, n, stream, reps=20, c64=False):
+    """Average device time (ms) of one hz_zspmv launch (hz_cspmv with c64).
+    Every launch is preceded by a 1 GiB write (flushes the 129 MB L2 and
+    keeps the GPU busy while the host enqueues the next launch, so host
+    launch latency never lands between the events); all launches are
+    enqueued before the one synchronisation."""
+    x = torch.randn(n, dtype=torch.complex64 if c64 else torch.complex128, device="cuda")
     y = torch.empty_like(x)
+    spmv = hz.cspmv if c64 else hz.zspmv
     flush = torch.empty(8 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     for _ in range(3):
-        hz.zspmv(M, x, y)
+        spmv(M, x, y)
     ev = []
     for _ in range(reps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        hz.zspmv(M, x, y)
+        spmv(M, x, y)
         e1.record(stream)
         ev.append((e0, e1))
     torch.cuda.synchronize()
@@ -399,6 +400,98 @@ def spmv_h1(hz, torch, stream):
                     "kind": M.props()["spmv_kind"], "group": M.props()["group"]}
         M.close()
     return out
+
+
+def spmv_c64_c2(hz, torch, A, stream):
+    """The complex64 SpMV of the mixed solver's inner iteration (block-flat
+    complex64 kernel on a double-float handle) on C2, L2 flushed; algorithmic
+    bytes 12 nnz + 20 n (8-byte values, 4-byte columns, x read once and y
+    written once in complex64, row pointers)."""
+    peak, _ = peaks()
+    rp = torch.as_tensor(A.rowptr).cuda()
+    cl = torch.as_tensor(A.col).cuda()
+    vl = torch.as_tensor(A.val).cuda()
+    M = hz.Matrix(rp, cl, vl, ff=True, c64=True)
+    ms = time_spmv(hz, torch, M, A.n, stream, c64=True)
+    nbytes = 12 * A.nnz + 20 * A.n + 4
+    gbs = nbytes / (ms / 1e3) / 1e9
+    M.close()
+    return {"kernel": "complex64 block-flat SpMV through hz_cspmv, L2 flushed", "launch_ms": ms,
+            "algorithmic_bytes_per_launch": nbytes, "achieved_gbs": gbs, "frac": gbs / peak}
+
+
+def adjoint_c5(hz, torch, stream, iters=300, reps=10):
+    """The adjoint step of the C5 inverse problem (64^3 FD, n = 262,144,
+    A(theta) = L - kappa^2 diag(theta)): the forward solve A x = b and the
+    adjoint solve A^T mu = conj(g) (g = the data misfit at the 512 sample
+    points) with the double-float solver for a fixed number of iterations
+    (the undamped 64^3 operator does not reach 1e-12 without a
+    preconditioner), then the two gradient kernels, each timed alone with
+    the L2 flushed (median of `reps`): the outer product on A's pattern
+    (16 nnz bytes written; 4 nnz + 4 (n + 1) of pattern and 32 n of mu and x
+    read) and the diagonal gradient (48 n)."""
+    import numpy as np
+    import statistics as st_
+    import workloads as W
+    prob = W.c5_inverse_problem()
+    A = prob["A"]
+    n, nnz = A.n, A.nnz
+    M = hz.Matrix.from_csr(A, ff=True)
+    base = torch.as_tensor(prob["L"].to_scipy().diagonal().astype(np.complex128)).cuda()
+    theta = torch.as_tensor(prob["theta"].astype(np.complex128)).cuda()
+    b = torch.as_tensor(prob["b"]).cuda()
+    idx = torch.as_tensor(prob["sample_idx"]).cuda()
+    d = torch.as_tensor(prob["data"]).cuda()
+    scale = -prob["kappa2"]
+    flush = torch.empty(8 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    def cold(fn):
+        fn()
+        ev = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        return st_.median(a.elapsed_time(z) for a, z in ev)
+
+    hz.mat_set_diag(M, base, scale, theta)
+    hz.zsolve(M, b, tol=1e-12, maxit=iters)                      # graph capture
+    (x, inf_f), ms_f = timed(lambda: hz.zsolve(M, b, tol=1e-12, maxit=iters))
+    g = torch.zeros_like(x)
+    g[idx] = x[idx] - d
+    rhs = hz.zconj(g)
+    (mu, inf_a), ms_a = timed(lambda: hz.zsolve(M, rhs, tol=1e-12, maxit=iters))
+    gval = torch.empty(nnz, dtype=torch.complex128, device="cuda")
+    gth = torch.empty_like(x)
+    ms_outer = cold(lambda: hz.outer_on_pattern(M, mu, x, out=gval))
+    ms_diag = cold(lambda: hz.diag_grad(M, mu, x, scale, out=gth))
+    peak, _ = peaks()
+    ob = 20 * nnz + 36 * n + 4
+    M.close()
+    return {"workload": "C5 64^3 FD inverse problem, A(theta) = L - kappa^2 diag(theta), kh = 0.5",
+            "n": n, "nnz": nnz, "iters": iters,
+            "forward": {"ms": ms_f, "iters": inf_f.iters, "status": inf_f.status_name,
+                        "relres_true": inf_f.relres_true, "iter_us": 1e3 * ms_f / max(inf_f.iters, 1)},
+            "adjoint": {"ms": ms_a, "iters": inf_a.iters, "status": inf_a.status_name,
+                        "relres_true": inf_a.relres_true, "iter_us": 1e3 * ms_a / max(inf_a.iters, 1)},
+            "outer_on_pattern": {"us": 1e3 * ms_outer, "algorithmic_bytes": ob,
+                                 "gbs": ob / (ms_outer / 1e3) / 1e9,
+                                 "frac": ob / (ms_outer / 1e3) / 1e9 / peak,
+                                 "note": "L2 flushed before each launch; the 29 MB it writes fits in L2"},
+            "diag_grad": {"us": 1e3 * ms_diag, "gbs": 48 * n / (ms_diag / 1e3) / 1e9,
+                          "l2_resident": True}}
 
 
 def workload_config(A, maxit, arith="fp64"):
@@ -553,6 +646,8 @@ def main():
     if rank == 0 and not args.no_compare:
         line["compare"] = compare_modes(hz, torch, args.c4_full, args.compare_maxit)
         line["spmv_h1"] = spmv_h1(hz, torch, stream)
+        line["spmv_c64_c2"] = spmv_c64_c2(hz, torch, A, stream)
+        line["adjoint_c5"] = adjoint_c5(hz, torch, stream)
         line["blas_sweep"] = blas_sweep(hz, torch, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, dt, it = cpu_oracle_rate(A, b, args.cpu_iters)

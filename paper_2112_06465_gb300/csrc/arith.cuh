@@ -15,6 +15,8 @@
 // and the operations the BiCGStab kernels need.
 #pragma once
 
+#include <type_traits>
+
 #include "hz_internal.cuh"
 
 namespace hz {
@@ -138,5 +140,108 @@ template <> struct Ar<float4> {
     }
     __device__ static R total(Acc a) { return (double)a.s + (double)a.c; }
 };
+
+// ------------------------------------------------------------------ reductions
+// Grid reduction of double-float accumulators.  The block and grid sums stay
+// in (s, c) pairs added with binary32 TwoSums and are widened to binary64
+// once, by thread 0 of the last block: on this GPU the binary64 pipe runs at
+// about 1/60 of the binary32 rate, so a binary64 block sum (and the two
+// conversions per thread before it) cost microseconds per reduction.  The
+// order of the additions is fixed, so the result is bitwise reproducible for
+// a fixed grid.  Partials are float2 pairs in red.partials.
+__device__ __forceinline__ void ff_pair_add(float &s, float &c, float bs, float bc) {
+    ff_acc(s, c, bs);
+    c = __fadd_rn(c, bc);
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum_ff(float (&s)[NV], float (&c)[NV], float2 (*sh)[NV]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, s[j], off);
+            const float oc = __shfl_xor_sync(0xffffffffu, c[j], off);
+            ff_pair_add(s[j], c[j], os, oc);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) sh[warp][j] = make_float2(s[j], c[j]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            const float2 t = lane < nwarps ? sh[lane][j] : make_float2(0.f, 0.f);
+            float ts = t.x, tc = t.y;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const float os = __shfl_xor_sync(0xffffffffu, ts, off);
+                const float oc = __shfl_xor_sync(0xffffffffu, tc, off);
+                ff_pair_add(ts, tc, os, oc);
+            }
+            s[j] = ts;
+            c[j] = tc;
+        }
+    }
+    __syncthreads();
+}
+
+// as grid_reduce_last; tot[] is valid in thread 0 of the last block only
+template <int NV>
+__device__ __forceinline__ bool grid_reduce_last_ff(const FFAcc (&v)[NV], RedScratch red, double (&tot)[NV]) {
+    __shared__ float2 sh[32][NV];
+    __shared__ int am_last;
+    float2 *partials = reinterpret_cast<float2 *>(red.partials);
+    float s[NV], c[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        s[j] = v[j].s;
+        c[j] = v[j].c;
+    }
+    block_sum_ff<NV>(s, c, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) partials[blockIdx.x * NV + j] = make_float2(s[j], c[j]);
+        __threadfence();
+        const unsigned int t = atomicAdd(red.counter, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) s[j] = c[j] = 0.f;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            const float2 p = __ldcg(&partials[b * NV + j]);
+            ff_pair_add(s[j], c[j], p.x, p.y);
+        }
+    }
+    block_sum_ff<NV>(s, c, sh);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) tot[j] = threadIdx.x == 0 ? (double)s[j] + (double)c[j] : 0.0;
+    if (threadIdx.x == 0) *red.counter = 0u;
+    return true;
+}
+
+// grid reduction of per-thread accumulators of any element type: pairs for
+// double-float, otherwise the accumulator's own type through grid_reduce_last
+template <class Acc, class R, int NV, class Total>
+__device__ __forceinline__ bool grid_reduce_acc(const Acc (&acc)[NV], RedScratch red, R (&tot)[NV], Total total) {
+    if constexpr (std::is_same<Acc, FFAcc>::value) {
+        static_assert(std::is_same<R, double>::value, "double-float totals are binary64");
+        return grid_reduce_last_ff<NV>(acc, red, tot);
+    } else {
+        R v[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = total(acc[j]);
+        return grid_reduce_last<R, NV>(v, red, tot);
+    }
+}
 
 }  // namespace hz

@@ -104,11 +104,7 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, unsigned 
 template <class V, int NV>
 __device__ __forceinline__ bool vec_reduce(typename Ar<V>::Acc (&acc)[NV], RedScratch red,
                                            typename Ar<V>::R (&tot)[NV]) {
-    using R = typename Ar<V>::R;
-    R v[NV];
-#pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] = Ar<V>::total(acc[j]);
-    return grid_reduce_last<R, NV>(v, red, tot);
+    return grid_reduce_acc(acc, red, tot, [](const typename Ar<V>::Acc &a) { return Ar<V>::total(a); });
 }
 
 // base of the solver epilogues: accumulator plumbing for element type V

@@ -618,10 +618,8 @@ __device__ __forceinline__ void flat_rows_ff_tma(const MatView<double2> &A, cons
 template <class Epi, int NV>
 __device__ __forceinline__ void spmv_reduce(const Epi &epi, typename Epi::Acc (&acc)[NV], RedScratch red) {
     using R = typename Epi::R;
-    R v[NV], tot[NV];
-#pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] = Epi::total(acc[j]);
-    if (grid_reduce_last<R, NV>(v, red, tot)) {
+    R tot[NV];
+    if (grid_reduce_acc(acc, red, tot, [](const typename Epi::Acc &a) { return Epi::total(a); })) {
         if (threadIdx.x == 0) epi.finish(tot);
     }
 }

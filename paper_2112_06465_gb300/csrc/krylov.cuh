@@ -73,16 +73,16 @@ __device__ __forceinline__ void vec_tiles(int n, F f) {
 // Tile walker that issues every load of a tile before the first compute:
 // load(i) returns the element's inputs (indices are clamped to n-1, so the
 // loads need no branch), comp(i, in) computes and stores for i < n.
-template <class Ld, class Cp>
+template <int U = kVecUnroll, class Ld, class Cp>
 __device__ __forceinline__ void vec_tiles_staged(int n, Ld load, Cp comp) {
     using In = decltype(load(0));
-    const int tile = kVecUnroll * blockDim.x;
+    const int tile = U * blockDim.x;
     for (int base = blockIdx.x * tile; base < n; base += gridDim.x * tile) {
-        In in[kVecUnroll];
+        In in[U];
 #pragma unroll
-        for (int u = 0; u < kVecUnroll; ++u) in[u] = load(min(base + u * (int)blockDim.x + (int)threadIdx.x, n - 1));
+        for (int u = 0; u < U; ++u) in[u] = load(min(base + u * (int)blockDim.x + (int)threadIdx.x, n - 1));
 #pragma unroll
-        for (int u = 0; u < kVecUnroll; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int i = base + u * blockDim.x + threadIdx.x;
             if (i < n) comp(i, in[u]);
         }

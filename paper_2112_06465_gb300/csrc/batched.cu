@@ -221,6 +221,53 @@ __device__ void item_done(int phase, const BCtl *c, const BSys &sy, BState *S, d
 }
 
 // the phase epilogue of one finished row y (lane 0 of the row's group)
+// item_done for double-float accumulators: the block sum and the fold over
+// a system's items stay in binary32 (s, c) pairs (float2 in the partials
+// slots) and are widened once for finalize; the binary64 pipe is far slower
+// than the binary32 one on this GPU
+template <int NV>
+__device__ void item_done_ff(int phase, const BCtl *c, const BSys &sy, BState *S, double *partials,
+                             int item_global, int item0, int nitems, const FFAcc *acc) {
+    __shared__ float2 sh[32][NV];
+    __shared__ int last;
+    float2 *pp = reinterpret_cast<float2 *>(partials);
+    float hs[NV], lc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        hs[j] = acc[j].s;
+        lc[j] = acc[j].c;
+    }
+    block_sum_ff<NV>(hs, lc, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) pp[(size_t)item_global * 4 + j] = make_float2(hs[j], lc[j]);
+        __threadfence();
+        const unsigned int k = atomicAdd(&S->cnt, 1u);
+        last = (k == (unsigned int)nitems - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) hs[j] = lc[j] = 0.f;
+    for (int it = threadIdx.x; it < nitems; it += kBBlock)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            const float2 q = __ldcg(&pp[(size_t)(item0 + it) * 4 + j]);
+            ff_pair_add(hs[j], lc[j], q.x, q.y);
+        }
+    block_sum_ff<NV>(hs, lc, sh);
+    if (threadIdx.x == 0) {
+        double tot[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) tot[j] = (double)hs[j] + (double)lc[j];
+        S->cnt = 0u;
+        finalize(phase, c, S, tot);
+        __threadfence();
+    }
+    __syncthreads();
+}
+
 template <class V, class Acc>
 __device__ __forceinline__ void row_epilogue(int phase, const BSys &sy, int row, V y, Acc (&acc)[3]) {
     using A = Ar<V>;
@@ -356,29 +403,41 @@ __device__ void run_phase(int phase, const BCtl *c, const BSys *sys, BState *st,
                 case 16: spmv_item<16, V>(phase, sy, r0, r1, va); break;
                 default: spmv_item<32, V>(phase, sy, r0, r1, va); break;
             }
-#pragma unroll
-            for (int q = 0; q < 3; ++q) acc[q] = (double)Ar<V>::total(va[q]);
             const int nit = sy.sp_items;
-            if (phase == P_F4) item_done<3>(phase, c, sy, S, partials, sy.sp_item0 + local, sy.sp_item0, nit, acc);
-            else if (phase == P_TRUE) {
-                double a1[1] = {acc[0]};
-                item_done<1>(phase, c, sy, S, partials, sy.sp_item0 + local, sy.sp_item0, nit, a1);
+            const int g = sy.sp_item0 + local;
+            if constexpr (Ar<V>::kFF) {
+                if (phase == P_F4) item_done_ff<3>(phase, c, sy, S, partials, g, sy.sp_item0, nit, va);
+                else if (phase == P_TRUE) item_done_ff<1>(phase, c, sy, S, partials, g, sy.sp_item0, nit, va);
+                else item_done_ff<2>(phase, c, sy, S, partials, g, sy.sp_item0, nit, va);
             } else {
-                double a2[2] = {acc[0], acc[1]};
-                item_done<2>(phase, c, sy, S, partials, sy.sp_item0 + local, sy.sp_item0, nit, a2);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) acc[q] = (double)Ar<V>::total(va[q]);
+                if (phase == P_F4) item_done<3>(phase, c, sy, S, partials, g, sy.sp_item0, nit, acc);
+                else if (phase == P_TRUE) {
+                    double a1[1] = {acc[0]};
+                    item_done<1>(phase, c, sy, S, partials, g, sy.sp_item0, nit, a1);
+                } else {
+                    double a2[2] = {acc[0], acc[1]};
+                    item_done<2>(phase, c, sy, S, partials, g, sy.sp_item0, nit, a2);
+                }
             }
         } else {
             const int e0 = local * kBVecItem, e1 = min(sy.n, e0 + kBVecItem);
             vec_item<V>(phase, sy, S, e0, e1, va);
-#pragma unroll
-            for (int q = 0; q < 3; ++q) acc[q] = (double)Ar<V>::total(va[q]);
             const int nit = sy.vc_items;
             const int g = sy.vc_item0 + local;
-            if (phase == P_F3) {
-                double a1[1] = {acc[0]};
-                item_done<1>(phase, c, sy, S, partials, g, sy.vc_item0, nit, a1);
-            } else if (phase == P_F5) {
-                item_done<3>(phase, c, sy, S, partials, g, sy.vc_item0, nit, acc);
+            if constexpr (Ar<V>::kFF) {
+                if (phase == P_F3) item_done_ff<1>(phase, c, sy, S, partials, g, sy.vc_item0, nit, va);
+                else if (phase == P_F5) item_done_ff<3>(phase, c, sy, S, partials, g, sy.vc_item0, nit, va);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) acc[q] = (double)Ar<V>::total(va[q]);
+                if (phase == P_F3) {
+                    double a1[1] = {acc[0]};
+                    item_done<1>(phase, c, sy, S, partials, g, sy.vc_item0, nit, a1);
+                } else if (phase == P_F5) {
+                    item_done<3>(phase, c, sy, S, partials, g, sy.vc_item0, nit, acc);
+                }
             }
         }
         __syncthreads();   // `skip` is rewritten by the next item

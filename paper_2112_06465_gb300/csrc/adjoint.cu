@@ -14,17 +14,20 @@
 
 namespace hz {
 
-// one warp per row: every stored entry (i, j) gets -conj(mu_i x_j)
+// W lanes per row (W near the mean row length, so short rows do not leave
+// most of a warp idle): every stored entry (i, j) gets -conj(mu_i x_j); the
+// row's entries are read and written contiguously by its W lanes
+template <int W>
 __global__ void __launch_bounds__(256) k_outer_pattern(int n, const int *__restrict__ rowptr,
                                                        const int *__restrict__ col, const double2 *__restrict__ mu,
                                                        const double2 *__restrict__ x, double2 *__restrict__ g) {
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
-        const double2 m = mu[i];
-        const int beg = rowptr[i], end = rowptr[i + 1];
-        for (int k = beg + lane; k < end; k += 32) {
-            const double2 xj = __ldg(x + col[k]);
+    const int lane = threadIdx.x & (W - 1);
+    const int groups = (gridDim.x * blockDim.x) / W;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / W; i < n; i += groups) {
+        const double2 m = __ldg(mu + i);
+        const int beg = __ldg(rowptr + i), end = __ldg(rowptr + i + 1);
+        for (int k = beg + lane; k < end; k += W) {
+            const double2 xj = __ldg(x + __ldg(col + k));
             const double2 p = cmul(m, xj);
             g[k] = make_double2(-p.x, p.y);
         }
@@ -92,8 +95,20 @@ extern "C" HZ_API hz_status hz_outer_on_pattern(const hz_mat *A, const hz_z *d_m
     HZ_CHECK(A, "hz_outer_on_pattern: null handle");
     if (A->n == 0 || A->nnz == 0) return HZ_OK;
     HZ_CHECK(d_mu && d_x && d_gradval, "hz_outer_on_pattern: null vector");
-    k_outer_pattern<<<grid_for((int64_t)A->n * 32), 256, 0, (cudaStream_t)stream>>>(
-        A->n, A->rowptr, A->col, (const double2 *)d_mu, (const double2 *)d_x, (double2 *)d_gradval);
+    int w = 2;
+    while (w < 32 && w < A->mean_row) w *= 2;
+    const int grid = grid_for((int64_t)A->n * w);
+    auto launch = [&](auto kern) {
+        kern<<<grid, 256, 0, (cudaStream_t)stream>>>(A->n, A->rowptr, A->col, (const double2 *)d_mu,
+                                                      (const double2 *)d_x, (double2 *)d_gradval);
+    };
+    switch (w) {
+        case 2: launch(k_outer_pattern<2>); break;
+        case 4: launch(k_outer_pattern<4>); break;
+        case 8: launch(k_outer_pattern<8>); break;
+        case 16: launch(k_outer_pattern<16>); break;
+        default: launch(k_outer_pattern<32>); break;
+    }
     HZ_CUDA(cudaGetLastError());
     return HZ_OK;
 }

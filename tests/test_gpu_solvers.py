@@ -228,6 +228,32 @@ def _loss_and_grad_dense(L, kappa2, theta, b, idx, d):
     return loss, grad_theta
 
 
+def test_outer_on_pattern_and_diag_grad(hz, oracle):
+    """The adjoint's gradient kernels against the oracle: -conj(mu_i x_j) on
+    every stored entry (ragged rows: empty, short, longer than a warp; FD
+    rows of 7) and the diagonal gradient conj(c) (-conj(mu_i x_i)).  One
+    binary64 complex product per entry, so each entry agrees to a few units
+    of its rounding (|mu_i| |x_j| 2^-52)."""
+    cases = [K.random_csr(3000, 11, max_row=12, long_rows=(2500, 1300)),
+             W.fd_helmholtz_box(12, kh=0.5, damping=0.05),
+             K.random_csr(500, 12, max_row=70, empty_frac=0.3)]
+    for A in cases:
+        mu, x = K.vectors(A.n, 13)
+        M = hz.Matrix.from_csr(A)
+        g = host(hz.outer_on_pattern(M, dev(mu), dev(x)))
+        ref = oracle.outer_on_pattern(A, mu, x)
+        rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+        scale = np.abs(mu[rows]) * np.abs(x[A.col])
+        assert np.all(np.abs(g - ref) <= 4.0 * 2.0 ** -52 * scale)
+    A = W.fd_helmholtz_box(10, kh=0.5, damping=0.05)
+    mu, x = K.vectors(A.n, 14)
+    c = -3.25 + 0.5j
+    M = hz.Matrix.from_csr(A)
+    gt = host(hz.diag_grad(M, dev(mu), dev(x), c))
+    ref = np.conj(c) * (-np.conj(mu * x))
+    assert np.all(np.abs(gt - ref) <= 8.0 * 2.0 ** -52 * abs(c) * np.abs(mu) * np.abs(x))
+
+
 def test_adjoint_gradient_dense_lu_and_fd(hz):
     m = 10
     prob = W.c5_inverse_problem(m=m, nsample=64)

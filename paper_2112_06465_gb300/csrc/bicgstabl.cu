@@ -236,6 +236,23 @@ __device__ bool chol_solve(int ell, const double2 (*G)[kMaxEll + 1], const doubl
     return true;
 }
 
+// accumulator pairs of the Gram reduction: binary64 sums on the binary64
+// path, (s, c) pairs with binary32 TwoSums on the double-float path (the
+// binary64 pipe is far slower than the binary32 one on this GPU)
+__device__ __forceinline__ void pacc(double &a, double b) { a += b; }
+__device__ __forceinline__ void pacc(FFAcc &a, FFAcc b) { ff_pair_add(a.s, a.c, b.s, b.c); }
+__device__ __forceinline__ double pshfl(double a, int off) { return __shfl_xor_sync(0xffffffffu, a, off); }
+__device__ __forceinline__ FFAcc pshfl(FFAcc a, int off) {
+    return FFAcc{__shfl_xor_sync(0xffffffffu, a.s, off), __shfl_xor_sync(0xffffffffu, a.c, off)};
+}
+__device__ __forceinline__ double pld(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ FFAcc pld(const FFAcc *p) {   // 8-byte slots of the scratch buffer
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return FFAcc{v.x, v.y};
+}
+__device__ __forceinline__ double pwiden(double a) { return a; }
+__device__ __forceinline__ double pwiden(FFAcc a) { return (double)a.s + (double)a.c; }
+
 // M1: Gram matrix of r_1..r_l and their products with r_0, reduced
 // deterministically (fixed-order sums within and across blocks); the last
 // block solves the normal equations for the minimal-residual coefficients
@@ -245,7 +262,7 @@ __global__ void __launch_bounds__(kVecBlock) k_bl_gram(int n, int ell, StateOf<V
     using A = Ar<V>;
     if (st->done) return;
     __shared__ V tile[kMaxEll + 1][kGramTile];
-    __shared__ double part[kVecBlock][2];
+    __shared__ typename Ar<V>::Acc part[kVecBlock][2];
     __shared__ double tot[kMaxPairs][2];
     __shared__ int am_last;
     const int np = ell + ell * (ell + 1) / 2;
@@ -266,15 +283,17 @@ __global__ void __launch_bounds__(kVecBlock) k_bl_gram(int n, int ell, StateOf<V
             for (int e = sub; e < kGramTile; e += tpp) A::dotc(ar, ai, tile[pi][e], tile[pk][e]);
         __syncthreads();
     }
-    part[threadIdx.x][0] = p < np ? (double)A::total(ar) : 0.0;
-    part[threadIdx.x][1] = p < np ? (double)A::total(ai) : 0.0;
+    // block partial of each pair: its tpp threads folded in order
+    using P = typename A::Acc;
+    part[threadIdx.x][0] = ar;
+    part[threadIdx.x][1] = ai;
     __syncthreads();
-    double *partials = reinterpret_cast<double *>(red.partials);
+    P *partials = reinterpret_cast<P *>(red.partials);
     if (threadIdx.x < np) {
-        double sr = 0.0, si = 0.0;
-        for (int t = 0; t < tpp; ++t) {
-            sr += part[threadIdx.x * tpp + t][0];
-            si += part[threadIdx.x * tpp + t][1];
+        P sr = part[threadIdx.x * tpp][0], si = part[threadIdx.x * tpp][1];
+        for (int t = 1; t < tpp; ++t) {
+            pacc(sr, part[threadIdx.x * tpp + t][0]);
+            pacc(si, part[threadIdx.x * tpp + t][1]);
         }
         partials[((size_t)blockIdx.x * np + threadIdx.x) * 2] = sr;
         partials[((size_t)blockIdx.x * np + threadIdx.x) * 2 + 1] = si;
@@ -285,14 +304,26 @@ __global__ void __launch_bounds__(kVecBlock) k_bl_gram(int n, int ell, StateOf<V
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    if (threadIdx.x < np) {
-        double sr = 0.0, si = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) {
-            sr += __ldcg(&partials[((size_t)b * np + threadIdx.x) * 2]);
-            si += __ldcg(&partials[((size_t)b * np + threadIdx.x) * 2 + 1]);
+    // last block: one warp per pair, lane l folds blocks l, l + 32, ... and
+    // the lanes are combined by a fixed shuffle tree
+    const int lane = threadIdx.x & 31;
+    for (int q = threadIdx.x >> 5; q < np; q += blockDim.x >> 5) {
+        P sr, si;
+        A::acc_zero(sr);
+        A::acc_zero(si);
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
+            pacc(sr, pld(&partials[((size_t)b * np + q) * 2]));
+            pacc(si, pld(&partials[((size_t)b * np + q) * 2 + 1]));
         }
-        tot[threadIdx.x][0] = sr;
-        tot[threadIdx.x][1] = si;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            pacc(sr, pshfl(sr, off));
+            pacc(si, pshfl(si, off));
+        }
+        if (lane == 0) {
+            tot[q][0] = pwiden(sr);
+            tot[q][1] = pwiden(si);
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {

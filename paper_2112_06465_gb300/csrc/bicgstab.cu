@@ -63,10 +63,13 @@ struct EpiSigma : EpiBase<V> {
     V *v;
     const V *rh;
     __device__ bool skip() const { return st->done; }
-    template <int N> __device__ void row(int i, V y, Acc (&acc)[N]) const {
+    using Pre = V;   // rh[i], fetched ahead by the block-flat kernel
+    __device__ V pre(int i) const { return rh[i]; }
+    template <int N> __device__ void row(int i, V y, Acc (&acc)[N], const V &rhi) const {
         v[i] = y;
-        Ar<V>::dotc(acc[0], acc[1], rh[i], y);
+        Ar<V>::dotc(acc[0], acc[1], rhi, y);
     }
+    template <int N> __device__ void row(int i, V y, Acc (&acc)[N]) const { row(i, y, acc, rh[i]); }
     template <int N> __device__ void finish(R (&tot)[N]) const {
         const auto sig = cmk(tot[0], tot[1]);
         if (cis_zero(sig)) { st->status = HZ_BREAKDOWN; st->done = 1; return; }
@@ -116,11 +119,14 @@ struct EpiOmega : EpiBase<V> {
     V *t;
     const V *s;
     __device__ bool skip() const { return st->done || st->half; }
-    template <int N> __device__ void row(int i, V y, Acc (&acc)[N]) const {
+    using Pre = V;   // s[i], fetched ahead by the block-flat kernel
+    __device__ V pre(int i) const { return s[i]; }
+    template <int N> __device__ void row(int i, V y, Acc (&acc)[N], const V &si) const {
         t[i] = y;
-        Ar<V>::dotc(acc[0], acc[1], y, s[i]);
+        Ar<V>::dotc(acc[0], acc[1], y, si);
         Ar<V>::nrm2(acc[2], y);
     }
+    template <int N> __device__ void row(int i, V y, Acc (&acc)[N]) const { row(i, y, acc, s[i]); }
     template <int N> __device__ void finish(R (&tot)[N]) const {
         if (tot[2] == R(0)) { st->status = HZ_BREAKDOWN; st->done = 1; return; }
         st->omega = cmk(tot[0] / tot[2], tot[1] / tot[2]);

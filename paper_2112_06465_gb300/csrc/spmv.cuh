@@ -18,6 +18,8 @@
 // kernel folds into one grid total (single pass, deterministic order).
 #pragma once
 
+#include <type_traits>
+
 #include "arith.cuh"
 
 namespace hz {
@@ -65,9 +67,12 @@ constexpr bool kFlatContig = HZ_FLAT_CONTIG != 0;   // contiguous block range pe
 #endif
 constexpr bool kFlatPipe = HZ_FLAT_PIPE != 0;       // column stream one group ahead
 #ifndef HZ_FLAT_MIN_BLOCKS
-#define HZ_FLAT_MIN_BLOCKS 1
+#define HZ_FLAT_MIN_BLOCKS 4
 #endif
-constexpr int kFlatMinBlocks = HZ_FLAT_MIN_BLOCKS;  // resident CTAs per SM asked of the register allocator
+// resident CTAs per SM asked of the register allocator: four (<= 128
+// registers) is what the 32 KB slabs allow anyway, and it keeps the solver
+// epilogues with a prefetched operand from dropping to three
+constexpr int kFlatMinBlocks = HZ_FLAT_MIN_BLOCKS;
 
 template <class T>
 struct MatView {
@@ -282,21 +287,50 @@ __device__ __forceinline__ void sell_rows_ff(const MatView<double2> &A, const fl
 
 // row result from packed accumulators S = (re_hi, im_hi), C = (re_lo, im_lo):
 // normalised ff pair (kFFRow, both halves by one packed TwoSum) or binary64
+// Optional prefetch of an epilogue's per-row operand: an epilogue that reads
+// one vector entry per row may declare `using Pre`, `Pre pre(int row) const`
+// and a row() that takes the loaded value as a fourth argument.  The
+// pipelined block-flat core issues those loads (and the row bounds) together
+// with the last group of a row block's entries, so they arrive while that
+// group's values and gathers are in flight instead of after the row sums.
+struct NoPre {};
+template <class E, class = void>
+struct PreOf {
+    using T = NoPre;
+    static constexpr bool kHas = false;
+};
+template <class E>
+struct PreOf<E, std::void_t<typename E::Pre>> {
+    using T = typename E::Pre;
+    static constexpr bool kHas = true;
+};
+template <class Epi>
+__device__ __forceinline__ typename PreOf<Epi>::T epi_pre(const Epi &epi, int row) {
+    if constexpr (PreOf<Epi>::kHas) return epi.pre(row);
+    else return NoPre{};
+}
+template <class Epi, class Y, int NV>
+__device__ __forceinline__ void epi_row(const Epi &epi, int row, Y y, typename Epi::Acc (&acc)[NV],
+                                        const typename PreOf<Epi>::T &pf) {
+    if constexpr (PreOf<Epi>::kHas) epi.row(row, y, acc, pf);
+    else epi.row(row, y, acc);
+}
+
 template <class Epi, int NV>
 __device__ __forceinline__ void ff_row_out2(const Epi &epi, int row, f32x2 S, f32x2 C,
-                                            typename Epi::Acc (&acc)[NV]) {
+                                            typename Epi::Acc (&acc)[NV], const typename PreOf<Epi>::T &pf) {
     if constexpr (Epi::kFFRow) {
         f32x2 h, l;
         two_sum2(S, C, h, l);
         float hr, hi, lr, li;
         upk2(h, hr, hi);
         upk2(l, lr, li);
-        epi.row(row, make_float4(hr, lr, hi, li), acc);
+        epi_row(epi, row, make_float4(hr, lr, hi, li), acc, pf);
     } else {
         float sr, si, cr, ci;
         upk2(S, sr, si);
         upk2(C, cr, ci);
-        epi.row(row, make_double2(join_d(sr, cr), join_d(si, ci)), acc);
+        epi_row(epi, row, make_double2(join_d(sr, cr), join_d(si, ci)), acc, pf);
     }
 }
 
@@ -304,24 +338,44 @@ __device__ __forceinline__ void ff_row_out2(const Epi &epi, int row, f32x2 S, f3
 // (+32, ...) held in prod[] for entries [kc, kend) and hands finished rows to
 // the epilogue.  A single row longer than one chunk is summed over several
 // chunks, lane 0 carrying (LS, LC) until the chunk that ends at ke.
+// phase 2 of a row block: lane j sums row r0 + j (a block has at most 32
+// rows) over entries [rb, re) clipped to the chunk [kc, kend); rb, re and the
+// epilogue operand pf were loaded for that row by the caller
+template <class Epi, int NV>
+__device__ __forceinline__ void flat_row_sums(const float4 *prod, int r0, int r1, int kc, int kend, int ke,
+                                              bool long_row, f32x2 &LS, f32x2 &LC, const Epi &epi,
+                                              typename Epi::Acc (&acc)[NV], int rb, int re,
+                                              const typename PreOf<Epi>::T &pf) {
+    const int row = r0 + (threadIdx.x & 31);
+    if (row >= r1) return;
+    const int beg = max(rb, kc), end = min(re, kend);
+    f32x2 S = 0ull, C = 0ull;   // +0.0f in both lanes
+    for (int k = beg; k < end; ++k) ff_cacc(S, C, prod[k - kc]);
+    if (long_row) {
+        f32x2 t, e;
+        two_sum2(LS, S, t, e);
+        LS = t;
+        LC = add2(LC, add2(e, C));
+        if (kend == ke) ff_row_out2<Epi, NV>(epi, row, LS, LC, acc, pf);
+    } else {
+        ff_row_out2<Epi, NV>(epi, row, S, C, acc, pf);
+    }
+}
+
+// the same, loading the row bounds and the epilogue operand itself
 template <class Epi, int NV>
 __device__ __forceinline__ void flat_row_sums(const MatView<double2> &A, const float4 *prod, int r0, int r1,
                                               int kc, int kend, int ke, bool long_row, f32x2 &LS, f32x2 &LC,
                                               const Epi &epi, typename Epi::Acc (&acc)[NV]) {
-    for (int row = r0 + (threadIdx.x & 31); row < r1; row += 32) {
-        const int beg = max(__ldg(A.rowptr + row), kc), end = min(__ldg(A.rowptr + row + 1), kend);
-        f32x2 S = 0ull, C = 0ull;   // +0.0f in both lanes
-        for (int k = beg; k < end; ++k) ff_cacc(S, C, prod[k - kc]);
-        if (long_row) {
-            f32x2 t, e;
-            two_sum2(LS, S, t, e);
-            LS = t;
-            LC = add2(LC, add2(e, C));
-            if (kend == ke) ff_row_out2<Epi, NV>(epi, row, LS, LC, acc);
-        } else {
-            ff_row_out2<Epi, NV>(epi, row, S, C, acc);
-        }
+    const int row = r0 + (threadIdx.x & 31);
+    int rb = 0, re = 0;
+    typename PreOf<Epi>::T pf{};
+    if (row < r1) {
+        rb = __ldg(A.rowptr + row);
+        re = __ldg(A.rowptr + row + 1);
+        pf = epi_pre(epi, row);
     }
+    flat_row_sums<Epi, NV>(prod, r0, r1, kc, kend, ke, long_row, LS, LC, epi, acc, rb, re, pf);
 }
 
 // Block-flat double-float core, one warp per row block (complete rows: at
@@ -457,8 +511,17 @@ __device__ __forceinline__ void flat_rows_ff_pipe(const MatView<double2> &A, con
         }
 #pragma unroll
         for (int u = 0; u < kFlatGroup; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        // the next group, and its columns
+        // the last group of a chunk also fetches what its row sums need: this
+        // lane's row bounds and the epilogue's operand for that row
         const bool chunk_done = cur.kg + 32 * kFlatGroup >= cur.kend;
+        int rb = 0, re = 0;
+        typename PreOf<Epi>::T pf{};
+        if (chunk_done && cur.r0 + lane < cur.r1) {
+            rb = __ldg(A.rowptr + cur.r0 + lane);
+            re = __ldg(A.rowptr + cur.r0 + lane + 1);
+            pf = epi_pre(epi, cur.r0 + lane);
+        }
+        // the next group, and its columns
         Group nxt = cur;
         if (!chunk_done) {
             nxt.kg = cur.kg + 32 * kFlatGroup;
@@ -476,7 +539,8 @@ __device__ __forceinline__ void flat_rows_ff_pipe(const MatView<double2> &A, con
             __syncwarp();
             const bool long_row = cur.r1 - cur.r0 == 1 && cur.ke - cur.kb > kFlatCap;
             if (long_row && cur.kc == cur.kb) LS = LC = 0ull;
-            flat_row_sums<Epi, NV>(A, prod, cur.r0, cur.r1, cur.kc, cur.kend, cur.ke, long_row, LS, LC, epi, acc);
+            flat_row_sums<Epi, NV>(prod, cur.r0, cur.r1, cur.kc, cur.kend, cur.ke, long_row, LS, LC, epi, acc, rb, re,
+                                   pf);
             __syncwarp();
         }
         if (nxt.b >= A.nfblk) break;

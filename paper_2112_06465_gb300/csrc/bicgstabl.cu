@@ -113,11 +113,14 @@ struct EpiBlU : EpiBase<V> {
     const V *rh;
     double s;   // operator scale
     __device__ bool skip() const { return st->done; }
-    template <int N> __device__ void row(int i, V y, Acc (&acc)[N]) const {
+    using Pre = V;   // rh[i], fetched ahead by the block-flat kernel
+    __device__ V pre(int i) const { return rh[i]; }
+    template <int N> __device__ void row(int i, V y, Acc (&acc)[N], const V &rhi) const {
         y = Ar<V>::pow2(y, s);
         u_next[i] = y;
-        Ar<V>::dotc(acc[0], acc[1], rh[i], y);
+        Ar<V>::dotc(acc[0], acc[1], rhi, y);
     }
+    template <int N> __device__ void row(int i, V y, Acc (&acc)[N]) const { row(i, y, acc, rh[i]); }
     template <int N> __device__ void finish(R (&tot)[N]) const {
         const double2 g = make_double2((double)tot[0], (double)tot[1]);
         if (cis_zero(g)) { st->status = HZ_BREAKDOWN; st->done = 1; return; }

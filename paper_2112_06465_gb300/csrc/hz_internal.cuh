@@ -500,6 +500,7 @@ struct hz_mat {
     // row blocks of the block-flat double-float kernel (complete rows)
     int32_t nfblk = 0;
     int32_t *fblk = nullptr;
+    int32_t *fblk_k = nullptr;   // rowptr[fblk[b]] for b = 0 .. nfblk
     int32_t nfblk_t = 0;       // the same for the bulk-copy kernel's smaller chunks
     int32_t *fblk_t = nullptr;
     // owned copy of col, 16-byte aligned and padded by 8 entries, that the

@@ -52,7 +52,7 @@ template <>
 MatView<double2> mat_view<double2>(const hz_mat *A) {
     MatView<double2> v{};
     v.n = A->n; v.rowptr = A->rowptr; v.col = A->col; v.val = A->val; v.vff = A->val_ff; v.svff = A->sell_vff;
-    v.nfblk = A->nfblk; v.fblk = A->fblk; v.nfblk_t = A->nfblk_t; v.fblk_t = A->fblk_t; v.colp = A->col_pad; v.fault = A->fault;
+    v.nfblk = A->nfblk; v.fblk = A->fblk; v.fblk_k = A->fblk_k; v.nfblk_t = A->nfblk_t; v.fblk_t = A->fblk_t; v.colp = A->col_pad; v.fault = A->fault;
     v.nchunks = A->sell_nchunks; v.chunk_off = A->sell_chunk_off; v.chunk_w = A->sell_chunk_w;
     v.perm = A->sell_perm; v.scol = A->sell_col; v.sval = A->sell_val;
     return v;
@@ -62,7 +62,7 @@ template <>
 MatView<float2> mat_view<float2>(const hz_mat *A) {
     MatView<float2> v{};
     v.n = A->n; v.rowptr = A->rowptr; v.col = A->col; v.val = A->val32;
-    v.nfblk = A->nfblk; v.fblk = A->fblk;
+    v.nfblk = A->nfblk; v.fblk = A->fblk; v.fblk_k = A->fblk_k;
     v.nchunks = A->sell_nchunks; v.chunk_off = A->sell_chunk_off; v.chunk_w = A->sell_chunk_w;
     v.perm = A->sell_perm; v.scol = A->sell_col; v.sval = A->sell_val32;
     return v;
@@ -367,7 +367,8 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
         // row blocks for the block-flat kernels: greedy runs of at most
         // kFlatRows complete rows with at most `cap` entries; a longer row is
         // a block of its own
-        auto row_blocks = [&](int cap, int32_t **dev, int32_t *count) {
+        // (and, for dev_k, the first entry of every block boundary row)
+        auto row_blocks = [&](int cap, int32_t **dev, int32_t *count, int32_t **dev_k) {
             std::vector<int> fb{0};
             for (int r = 0; r < n;) {
                 int r1 = r + 1;
@@ -376,10 +377,17 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
                 r = r1;
             }
             *count = (int32_t)fb.size() - 1;
-            return cudaMalloc(dev, sizeof(int) * fb.size()) == cudaSuccess &&
-                   cudaMemcpy(*dev, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+            if (cudaMalloc(dev, sizeof(int) * fb.size()) != cudaSuccess ||
+                cudaMemcpy(*dev, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                return false;
+            if (!dev_k) return true;
+            std::vector<int> fk(fb.size());
+            for (size_t b = 0; b < fb.size(); ++b) fk[b] = rp[fb[b]];
+            return cudaMalloc(dev_k, sizeof(int) * fk.size()) == cudaSuccess &&
+                   cudaMemcpy(*dev_k, fk.data(), sizeof(int) * fk.size(), cudaMemcpyHostToDevice) == cudaSuccess;
         };
-        if (!row_blocks(kFlatCap, &A->fblk, &A->nfblk) || !row_blocks(kTmaCap, &A->fblk_t, &A->nfblk_t)) {
+        if (!row_blocks(kFlatCap, &A->fblk, &A->nfblk, &A->fblk_k) ||
+            !row_blocks(kTmaCap, &A->fblk_t, &A->nfblk_t, nullptr)) {
             set_error("hz_csr_create: allocation failed");
             return fail(HZ_ERR_ALLOC);
         }
@@ -422,6 +430,7 @@ extern "C" HZ_API hz_status hz_mat_destroy(hz_mat *A) {
     cudaFree(A->sell_val);
     cudaFree(A->sell_vff);
     cudaFree(A->fblk);
+    cudaFree(A->fblk_k);
     cudaFree(A->fblk_t);
     cudaFree(A->col_pad);
     cudaFree(A->fault);

@@ -95,6 +95,7 @@ struct MatView {
     // one longer row); fblk_t the same with kTmaCap for the bulk-copy kernel
     int nfblk;
     const int *fblk;
+    const int *fblk_k;   // rowptr[fblk[b]]: a block's entry range without a dependent load
     int nfblk_t;
     const int *fblk_t;
     // padded copy of col read by the bulk-copy kernel, and its fault word
@@ -467,18 +468,31 @@ __device__ __forceinline__ void flat_rows_ff_pipe(const MatView<double2> &A, con
     struct Group {
         int b, r0, r1, kb, ke, kc, kend, kg;
     };
-    auto block_group = [&](int b) {
-        Group q;
-        q.b = b;
-        q.r0 = q.r1 = q.kb = q.ke = q.kc = q.kend = q.kg = 0;
+    // a block's bounds come from four independent loads (fblk_k holds the
+    // rowptr entries of the block boundaries) issued one block ahead, so the
+    // switch to the next block never waits on them
+    struct Meta {
+        int b, r0, r1, kb, ke;
+    };
+    auto block_meta = [&](int b) {
+        Meta m{b, 0, 0, 0, 0};
         if (b < A.nfblk) {
-            q.r0 = __ldg(A.fblk + b);
-            q.r1 = __ldg(A.fblk + b + 1);
-            q.kb = __ldg(A.rowptr + q.r0);
-            q.ke = __ldg(A.rowptr + q.r1);
-            q.kc = q.kg = q.kb;
-            q.kend = min(q.ke, q.kb + kFlatCap);
+            m.r0 = __ldg(A.fblk + b);
+            m.r1 = __ldg(A.fblk + b + 1);
+            m.kb = __ldg(A.fblk_k + b);
+            m.ke = __ldg(A.fblk_k + b + 1);
         }
+        return m;
+    };
+    auto block_group = [&](const Meta &m) {
+        Group q;
+        q.b = m.b;
+        q.r0 = m.r0;
+        q.r1 = m.r1;
+        q.kb = m.kb;
+        q.ke = m.ke;
+        q.kc = q.kg = m.kb;
+        q.kend = min(m.ke, m.kb + kFlatCap);
         return q;
     };
     auto load_cols = [&](const Group &q, int (&c)[kFlatGroup]) {
@@ -488,8 +502,10 @@ __device__ __forceinline__ void flat_rows_ff_pipe(const MatView<double2> &A, con
             c[u] = (q.b < A.nfblk && k < q.kend) ? ld_stream(A.col + k, pol) : -1;
         }
     };
-    Group cur = block_group(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
-    if (cur.b >= A.nfblk) return;
+    const int b0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b0 >= A.nfblk) return;
+    Group cur = block_group(block_meta(b0));
+    Meta ahead = block_meta(b0 + step);   // the warp's next block
     int cn[kFlatGroup];
     load_cols(cur, cn);
     f32x2 LS = 0ull, LC = 0ull;   // long-row carry (lane 0)
@@ -529,7 +545,8 @@ __device__ __forceinline__ void flat_rows_ff_pipe(const MatView<double2> &A, con
             nxt.kc = nxt.kg = cur.kend;
             nxt.kend = min(cur.ke, cur.kend + kFlatCap);
         } else {
-            nxt = block_group(cur.b + step);
+            nxt = block_group(ahead);
+            ahead = block_meta(nxt.b + step);
         }
         load_cols(nxt, cn);
 #pragma unroll

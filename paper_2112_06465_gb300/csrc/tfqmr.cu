@@ -130,13 +130,18 @@ struct EpiTqV : EpiBase<V> {
     __device__ bool skip() const { return st->done; }
     // a finished solve must leave the loop even when this product is skipped
     __device__ void on_skip() const { set_cond(h, 0); }
-    template <int N> __device__ void row(int i, V y, Acc (&acc)[N]) const {
+    struct Pre {   // v[i] and rh[i], fetched ahead by the block-flat kernel
+        V v, rh;
+    };
+    __device__ Pre pre(int i) const { return Pre{v[i], rh[i]}; }
+    template <int N> __device__ void row(int i, V y, Acc (&acc)[N], const Pre &pf) const {
         au1[i] = y;
-        const V vi = Ar<V>::add(y, v[i]);
+        const V vi = Ar<V>::add(y, pf.v);
         v[i] = vi;
-        Ar<V>::dotc(acc[0], acc[1], rh[i], vi);
+        Ar<V>::dotc(acc[0], acc[1], pf.rh, vi);
         Ar<V>::nrm2(acc[2], vi);
     }
+    template <int N> __device__ void row(int i, V y, Acc (&acc)[N]) const { row(i, y, acc, pre(i)); }
     template <int N> __device__ void finish(R (&tot)[N]) const {
         const double2 sig = make_double2((double)tot[0], (double)tot[1]);
         if (!((double)tot[2] < kTqBig) || !(q->tau * q->tau < kTqBig)) q->pend = 1;

@@ -800,51 +800,106 @@ __device__ __forceinline__ void flat_rows_c64(const MatView<float2> &A, const fl
     const uint64_t pol = pol_evict_first();
     const int lane = threadIdx.x & 31;
     float2 *prod = slab + (threadIdx.x >> 5) * kFlatCap;
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < A.nfblk; b += nwarps) {
-        const int r0 = __ldg(A.fblk + b), r1 = __ldg(A.fblk + b + 1);
-        const int kb = __ldg(A.rowptr + r0), ke = __ldg(A.rowptr + r1);
-        const bool long_row = r1 - r0 == 1 && ke - kb > kFlatCap;
-        float2 carry = make_float2(0.f, 0.f);   // long-row carry (lane 0)
-        for (int kc = kb;; kc += kFlatCap) {
-            const int kend = min(ke, kc + kFlatCap);
-#pragma unroll 1
-            for (int g = 0; g < kFlatU; g += kFlatGroup) {
-                int c[kFlatGroup];
-                float2 a[kFlatGroup], v[kFlatGroup];
+    const int step = gridDim.x * (blockDim.x >> 5);
+    // the schedule of flat_rows_ff_pipe: columns one group ahead, the next
+    // block's bounds one block ahead, row bounds with a chunk's last group
+    struct Group {
+        int b, r0, r1, kb, ke, kc, kend, kg;
+    };
+    struct Meta {
+        int b, r0, r1, kb, ke;
+    };
+    auto block_meta = [&](int b) {
+        Meta m{b, 0, 0, 0, 0};
+        if (b < A.nfblk) {
+            m.r0 = __ldg(A.fblk + b);
+            m.r1 = __ldg(A.fblk + b + 1);
+            m.kb = __ldg(A.fblk_k + b);
+            m.ke = __ldg(A.fblk_k + b + 1);
+        }
+        return m;
+    };
+    auto block_group = [&](const Meta &m) {
+        Group q;
+        q.b = m.b;
+        q.r0 = m.r0;
+        q.r1 = m.r1;
+        q.kb = m.kb;
+        q.ke = m.ke;
+        q.kc = q.kg = m.kb;
+        q.kend = min(m.ke, m.kb + kFlatCap);
+        return q;
+    };
+    auto load_cols = [&](const Group &q, int (&c)[kFlatGroup]) {
 #pragma unroll
-                for (int u = 0; u < kFlatGroup; ++u) {
-                    const int k = kc + lane + 32 * (g + u);
-                    c[u] = k < kend ? ld_stream(A.col + k, pol) : -1;
-                    a[u] = k < kend ? ld_stream(A.val + k) : make_float2(0.f, 0.f);
-                }
+        for (int u = 0; u < kFlatGroup; ++u) {
+            const int k = q.kg + lane + 32 * u;
+            c[u] = (q.b < A.nfblk && k < q.kend) ? ld_stream(A.col + k, pol) : -1;
+        }
+    };
+    const int b0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b0 >= A.nfblk) return;
+    Group cur = block_group(block_meta(b0));
+    Meta ahead = block_meta(b0 + step);
+    int cn[kFlatGroup];
+    load_cols(cur, cn);
+    float2 carry = make_float2(0.f, 0.f);   // long-row carry (lane 0)
+    for (;;) {
+        int c[kFlatGroup];
+        float2 a[kFlatGroup], v[kFlatGroup];
 #pragma unroll
-                for (int u = 0; u < kFlatGroup; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float2(0.f, 0.f);
+        for (int u = 0; u < kFlatGroup; ++u) {
+            c[u] = cn[u];
+            const int k = cur.kg + lane + 32 * u;
+            a[u] = c[u] >= 0 ? ld_stream(A.val + k) : make_float2(0.f, 0.f);
+        }
 #pragma unroll
-                for (int u = 0; u < kFlatGroup; ++u)
-                    if (c[u] >= 0) prod[lane + 32 * (g + u)] = cmul(a[u], v[u]);
-                if (kc + 32 * (g + kFlatGroup) >= kend) break;
-            }
+        for (int u = 0; u < kFlatGroup; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float2(0.f, 0.f);
+        const bool chunk_done = cur.kg + 32 * kFlatGroup >= cur.kend;
+        int rb = 0, re = 0;
+        if (chunk_done && cur.r0 + lane < cur.r1) {
+            rb = __ldg(A.rowptr + cur.r0 + lane);
+            re = __ldg(A.rowptr + cur.r0 + lane + 1);
+        }
+        Group nxt = cur;
+        if (!chunk_done) {
+            nxt.kg = cur.kg + 32 * kFlatGroup;
+        } else if (cur.kend < cur.ke) {   // next pass over the same long row
+            nxt.kc = nxt.kg = cur.kend;
+            nxt.kend = min(cur.ke, cur.kend + kFlatCap);
+        } else {
+            nxt = block_group(ahead);
+            ahead = block_meta(nxt.b + step);
+        }
+        load_cols(nxt, cn);
+#pragma unroll
+        for (int u = 0; u < kFlatGroup; ++u)
+            if (c[u] >= 0) prod[cur.kg - cur.kc + lane + 32 * u] = cmul(a[u], v[u]);
+        if (chunk_done) {
             __syncwarp();
-            for (int row = r0 + lane; row < r1; row += 32) {
-                const int beg = max(__ldg(A.rowptr + row), kc), end = min(__ldg(A.rowptr + row + 1), kend);
+            const bool long_row = cur.r1 - cur.r0 == 1 && cur.ke - cur.kb > kFlatCap;
+            if (long_row && cur.kc == cur.kb) carry = make_float2(0.f, 0.f);
+            const int row = cur.r0 + lane;
+            if (row < cur.r1) {
+                const int beg = max(rb, cur.kc), end = min(re, cur.kend);
                 float2 y = make_float2(0.f, 0.f);
                 for (int k = beg; k < end; ++k) {
-                    const float2 q = prod[k - kc];
+                    const float2 q = prod[k - cur.kc];
                     y.x += q.x;
                     y.y += q.y;
                 }
                 if (long_row) {
                     carry.x += y.x;
                     carry.y += y.y;
-                    if (kend == ke) epi.row(row, carry, acc);
+                    if (cur.kend == cur.ke) epi.row(row, carry, acc);
                 } else {
                     epi.row(row, y, acc);
                 }
             }
             __syncwarp();
-            if (kend >= ke) break;
         }
+        if (nxt.b >= A.nfblk) break;
+        cur = nxt;
     }
 }
 

@@ -8,6 +8,7 @@ GPU history against the oracle's to 1e-10 relative.
 """
 
 import numpy as np
+import scipy.sparse as sp
 import pytest
 import torch
 
@@ -109,6 +110,26 @@ def test_bicgstab_edge_cases(hz, oracle):
     bn[5] = np.nan
     x, info = hz.zsolve(M, dev(bn))
     assert info.status == 6
+
+
+@pytest.mark.parametrize("method", ["bicgstab", "tfqmr", "bicgstabl"])
+def test_solvers_long_rows_double_float(hz, oracle, method):
+    """Rows longer than one 512-entry row block (summed in passes with a
+    carried sum) inside the fused solver products on the double-float path,
+    whose epilogues fetch their per-row operands ahead of the row sums.  The
+    matrix is made diagonally dominant so every method converges."""
+    R = K.random_csr(3000, 21, max_row=12, long_rows=(2500, 1300, 700)).to_scipy()
+    absum = np.asarray(abs(R).sum(axis=1)).ravel()
+    A = W.CSR.from_scipy(R + sp.diags(absum + 1.0))
+    b = K.vectors(A.n, 22)[0]
+    M = hz.Matrix.from_csr(A, ff=True)
+    kw = {"bicgstab": {}, "tfqmr": {"method": "tfqmr"}, "bicgstabl": {"method": "bicgstabl", "ell": 4}}[method]
+    x, info = hz.zsolve(M, dev(b), tol=1e-10, maxit=500, **kw)
+    assert info.converged, info
+    assert true_relres(oracle, A, host(x), b) <= 1e-10
+    xo, io = oracle.bicgstab(A, b, tol=1e-12, maxit=500)
+    assert io.status == 0
+    assert np.linalg.norm(host(x) - xo) <= 1e-8 * np.linalg.norm(xo)
 
 
 def test_bicgstab_breakdown_2x2(hz, oracle):

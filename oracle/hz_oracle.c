@@ -564,7 +564,10 @@ int or_tfqmr(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *val
 /* ---------------------------------------------------------------------- */
 /* Same iteration in complex64 with binary32 sums: the inner solver of the
  * mixed-precision refinement.  x0 = 0, stopping on ||r|| <= tol ||b||.
- * Returns the iteration count; *status gets the exit reason. */
+ * Returns the iteration count; *status gets the exit reason.  hist
+ * (optional, maxit+1 entries) receives ||r_j|| / ||b|| as or_bicgstab's does:
+ * hist[0] = 1 (r0 = b), hist[j] after iteration j (||s|| / ||b|| for a
+ * half-step exit). */
 static float c_norm(int32_t n, const oc *x)
 {
     float s = 0.0f;
@@ -579,7 +582,7 @@ static oc c_dotc(int32_t n, const oc *x, const oc *y)
 }
 
 int32_t or_cbicgstab(int32_t n, const int32_t *rowptr, const int32_t *col, const oc *val,
-                     const oc *b, oc *x, float tol, int32_t maxit, int32_t *status)
+                     const oc *b, oc *x, float tol, int32_t maxit, int32_t *status, double *hist)
 {
     oc *r = calloc((size_t)n, sizeof(oc)), *rh = calloc((size_t)n, sizeof(oc));
     oc *p = calloc((size_t)n, sizeof(oc)), *v = calloc((size_t)n, sizeof(oc));
@@ -589,7 +592,8 @@ int32_t or_cbicgstab(int32_t n, const int32_t *rowptr, const int32_t *col, const
     int32_t it = 0;
     *status = OR_NOT_CONVERGED;
     memset(x, 0, (size_t)n * sizeof(oc));
-    if (nb == 0.0f) { *status = OR_OK; goto done; }
+    if (nb == 0.0f) { *status = OR_OK; if (hist) hist[0] = 0.0; goto done; }
+    if (hist) hist[0] = 1.0;
     for (int32_t i = 0; i < n; ++i) { r[i] = b[i]; rh[i] = b[i]; }
     while (it < maxit) {
         oc rho, sig, ts, tt, beta;
@@ -609,6 +613,7 @@ int32_t or_cbicgstab(int32_t n, const int32_t *rowptr, const int32_t *col, const
         if (!isfinite(rel)) { *status = OR_NAN; break; }
         if (rel <= tol) {
             for (int32_t i = 0; i < n; ++i) x[i] = c_add(x[i], c_mul(alpha, p[i]));
+            if (hist) hist[it] = (double)rel;
             *status = OR_OK;
             break;
         }
@@ -623,6 +628,7 @@ int32_t or_cbicgstab(int32_t n, const int32_t *rowptr, const int32_t *col, const
         }
         rho_old = rho;
         rel = c_norm(n, r) / nb;
+        if (hist) hist[it] = (double)rel;
         if (!isfinite(rel)) { *status = OR_NAN; break; }
         if (rel <= tol) { *status = OR_OK; break; }
         if (omega.re == 0.0f && omega.im == 0.0f) { *status = OR_BREAKDOWN; break; }
@@ -660,7 +666,7 @@ int or_refine_mixed(int32_t n, const int32_t *rowptr, const int32_t *col, const 
             if (outer >= max_outer) break;
             ++outer;
             for (int32_t i = 0; i < n; ++i) { r32[i].re = (float)r[i].re; r32[i].im = (float)r[i].im; }
-            k = or_cbicgstab(n, rowptr, col, val32, r32, d32, tol_in, maxit_in, &st);
+            k = or_cbicgstab(n, rowptr, col, val32, r32, d32, tol_in, maxit_in, &st, NULL);
             inner += k;
             for (int32_t i = 0; i < n; ++i) {
                 x[i].re += (double)d32[i].re;

@@ -55,7 +55,7 @@ def load():
         lib.or_tfqmr.argtypes = [i32, P, P, P, P, P, f64, i32, P, P]
         lib.or_tfqmr.restype = C.c_int
         lib.or_zmul_elementwise.argtypes = [i64, P, P, P]
-        lib.or_cbicgstab.argtypes = [i32, P, P, P, P, P, f32, i32, P]
+        lib.or_cbicgstab.argtypes = [i32, P, P, P, P, P, f32, i32, P, P]
         lib.or_cbicgstab.restype = i32
         lib.or_refine_mixed.argtypes = [i32, P, P, P, P, P, P, f64, f32, i32, i32, P, P, P]
         lib.or_refine_mixed.restype = C.c_int
@@ -231,16 +231,20 @@ def tfqmr(A, b, x0=None, tol=1e-10, maxit=2000, history=True):
     return x, out
 
 
-def cbicgstab(A, b, tol=1e-5, maxit=1000, val32=None):
-    """complex64 BiCGStab with binary32 sums from x0 = 0; returns (x, iters, status)."""
+def cbicgstab(A, b, tol=1e-5, maxit=1000, val32=None, history=False):
+    """complex64 BiCGStab with binary32 sums from x0 = 0; returns (x, iters, status),
+    plus the residual history (||r_j|| / ||b||, j = 0..iters) with history=True."""
     lib = load()
     b = _c(b)
     v = _c(A.val if val32 is None else val32)
     x = np.zeros(A.n, dtype=np.complex64)
     st = C.c_int32(0)
     rp, cl = _i(A.rowptr), _i(A.col)
+    hist = np.full(int(maxit) + 1, np.nan) if history else None
     it = lib.or_cbicgstab(A.n, _p(rp), _p(cl), _p(v), _p(b), _p(x), float(tol), int(maxit),
-                          C.byref(st))
+                          C.byref(st), _p(hist) if history else None)
+    if history:
+        return x, int(it), int(st.value), hist[: int(it) + 1].copy()
     return x, int(it), int(st.value)
 
 

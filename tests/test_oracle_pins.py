@@ -415,6 +415,39 @@ def test_mixed_refinement(oracle):
     assert 1e-8 < r < 1e-4
 
 
+def test_cbicgstab_history_tracks_binary64(oracle):
+    """The complex64 inner solver takes the same steps as the binary64
+    BiCGStab (Section 7 with the Hermitian inner product): on a well
+    conditioned damped FD box with a complex right-hand side, its first ten
+    recursive residuals agree with or_bicgstab's to 1e-5 relative, the
+    binary32 rounding being the only difference.  A dropped conjugate in its
+    inner product, a swapped operand or a wrong sign of omega changes the
+    very first steps (rho = <r, r> is real only with the conjugate)."""
+    A = W.fd_helmholtz_box(8, kh=0.3, damping=1.0)
+    b = K.vectors(A.n, 60)[0]
+    _, info = oracle.bicgstab(A, b, tol=1e-12, maxit=200)
+    _, it, st, h32 = oracle.cbicgstab(A, b.astype(np.complex64), tol=1e-7, maxit=10, history=True)
+    assert it == 10 and info.iters > 10
+    h64 = info.hist[:11]
+    assert h32[0] == 1.0 and h64[0] == 1.0
+    assert np.all(np.abs(h32 - h64) <= 1e-5 * h64)
+
+
+def test_cbicgstab_nonsymmetric_dense_lu(oracle):
+    """complex64 BiCGStab on a general (non-symmetric, non-Hermitian)
+    complex matrix reaches the dense-LU solution to binary32 accuracy."""
+    rng = np.random.default_rng(61)
+    n = 60
+    D = ((rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2 * n)
+         + np.diag(2.0 + 1.0j + 0.5 * rng.standard_normal(n)))
+    A = W.CSR.from_scipy(sp.csr_matrix(D))
+    b = K.vectors(n, 62)[0]
+    x, it, st = oracle.cbicgstab(A, b.astype(np.complex64), tol=1e-6, maxit=200)
+    x_lu = np.linalg.solve(D, b)
+    assert st == 0 and it < 200
+    assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) <= 1e-5
+
+
 # --------------------------------------------------------------------------- adjoint
 def test_adjoint_oracle_gradient(oracle):
     """Oracle chain (solve, adjoint solve, outer product on the pattern) against

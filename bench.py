@@ -95,10 +95,10 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per SpMV launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "spmv_ffb_c2_traffic.txt")
+def recorded_traffic(name):
+    """DRAM bytes per SpMV launch from the committed ncu summary
+    profiles/<name>, if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", name)
     try:
         kv = {}
         with open(p) as f:
@@ -111,6 +111,9 @@ def recorded_traffic():
         return float(kv["dram_bytes_per_launch"])
     except Exception:
         return None
+
+
+TRAFFIC_FILES = {4: "spmv_ffb_c2_traffic.txt", 6: "spmv_d64b_c2_traffic.txt"}
 
 
 class ClockSampler:
@@ -172,12 +175,17 @@ def build_workload():
     return A, b
 
 
-def cpu_oracle_rate(A, b, iters):
-    """The oracle's BiCGStab for a fixed number of iterations; returns (GB/s, seconds)."""
+def cpu_oracle_rate(A, b, iters, threads=None):
+    """The oracle's BiCGStab for a fixed number of iterations; returns (GB/s,
+    seconds, iterations).  threads=None: the plain single-thread build;
+    threads=k: the OpenMP build on k threads."""
     import oracle
     oracle.build()
     t0 = time.perf_counter()
-    x, info = oracle.bicgstab(A, b, tol=1e-300, maxit=iters, history=False)
+    if threads is None:
+        x, info = oracle.bicgstab(A, b, tol=1e-300, maxit=iters, history=False)
+    else:
+        x, info = oracle.bicgstab_omp(A, b, tol=1e-300, maxit=iters, threads=threads)
     dt = time.perf_counter() - t0
     return solve_bytes(A.n, A.nnz, info.iters) / dt / 1e9, dt, info.iters
 
@@ -197,14 +205,22 @@ def run_reference(args):
         rates.append(r)
         times.append(dt)
     value = statistics.median(rates)
-    sample = f"{iters} BiCGStab iterations of C2 per step (n={A.n}, nnz={A.nnz})"
+    sample = f"{iters} BiCGStab iterations of C2 per step (n={A.n}, nnz={A.nnz}), single-thread build"
+    cores = len(os.sched_getaffinity(0))
+    try:
+        rN, dtN, itN = cpu_oracle_rate(A, b, iters, threads=cores)
+        all_cores = {"value": rN, "unit": "GB/s", "cores": cores, "kind": "oracle (OpenMP build)",
+                     "sample": f"{itN} BiCGStab iterations of C2 ({dtN:.1f} s)"}
+    except Exception as e:   # no OpenMP runtime on this host
+        all_cores = {"unavailable": str(e)[:200]}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": workload_config(A, iters),
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "all_cores": all_cores},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -214,7 +230,12 @@ DTYPES = {"fp64": "f64", "ff": "f32x2 (double-float complex128: hi+lo binary32 p
 SPMV_KINDS = {0: "binary64 CSR-vector (k_spmv)", 1: "binary64 SELL-C-sigma (k_spmv<0>)",
               2: "double-float CSR-vector (k_spmv_ff)", 3: "double-float SELL-C-sigma (k_spmv_ff<0>)",
               4: "double-float block-flat (k_spmv_ffb)",
-              5: "double-float block-flat, bulk-copy staged (k_spmv_fft)"}
+              5: "double-float block-flat, bulk-copy staged (k_spmv_fft)",
+              6: "binary64 block-flat, contiguous lane runs (k_spmv_d64b)"}
+# binary64 roof of GB300: the nominal FP64 rate of the profiling recipe's
+# table (1.25 TFLOP/s); an own FMA-throughput probe measured 1.05 TFLOP/s
+FP64_NOMINAL_TFLOPS = 1.25
+FP64_PROBE_TFLOPS = 1.052
 
 
 def run_spmv_only(args):
@@ -225,8 +246,6 @@ def run_spmv_only(args):
     M = hz.Matrix.from_csr(A, ff=args.arith == "ff")
     if args.spmv:
         M.set_spmv(args.spmv, args.group)
-    elif args.arith == "fp64":
-        M.set_spmv("csr", args.group)
     x = torch.randn(A.n, dtype=torch.complex128, device="cuda")
     y = torch.empty_like(x)
     for _ in range(3):
@@ -494,12 +513,86 @@ def adjoint_c5(hz, torch, stream, iters=300, reps=10):
                           "l2_resident": True}}
 
 
-def workload_config(A, maxit, arith="fp64"):
+def workload_config(A, maxit, arith="fp64", iters=None, status=None):
     return {"workload": "C2 jittered P1-FEM cylinder nr=40 ntheta=96 nz=160 k=20 impedance ends, "
                         f"complex128 BiCGStab x0=0 tol=1e-10 maxit={maxit}",
             "arith": arith, "n": A.n, "nnz": A.nnz, "maxit": maxit,
+            "solve_iters": iters, "solve_status": status,
             "l2": "inputs larger than L2 (CSR matrix %.0f MB > 129 MB L2); the SpMV roofline "
                   "launches flush L2 between launches" % (A.nnz * 20 / 1e6)}
+
+
+def spmv_roofline(hz, torch, M, A, stream, kind):
+    """Roofline object of the SpMV core of the handle's kind, timed alone.
+
+    A binary64 kind is bound by GB300's binary64 pipe (four FMAs per nonzero
+    at the FP64 rate cap the product near 0.44 of the HBM copy rate), so its
+    roofline is "alu": 8 flops per nonzero against the nominal FP64 rate;
+    the HBM fraction is given beside it.  A double-float kind is HBM-bound."""
+    sp_avg = time_spmv(hz, torch, M, A.n, stream)
+    peak, peak_src = peaks()
+    gbs = spmv_bytes(A.n, A.nnz) / (sp_avg / 1e3) / 1e9
+    traffic = recorded_traffic(TRAFFIC_FILES[kind]) if kind in TRAFFIC_FILES else None
+    hbm = {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+           "frac_of_nominal_8000": gbs / 8000.0, "peak_source": f"{peak_src} (burst copy)"}
+    desc = "%s SpMV through hz_zspmv alone, L2 flushed" % SPMV_KINDS.get(kind, kind)
+    if kind in (0, 1, 6):
+        tf = 8.0 * A.nnz / (sp_avg / 1e3) / 1e12
+        return {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": tf / FP64_NOMINAL_TFLOPS, "traffic": traffic,
+                "alu": "binary64 FMA pipe; peak = nominal FP64 rate (1.25 TFLOP/s); own FMA probe: "
+                       f"{FP64_PROBE_TFLOPS} TFLOP/s", "frac_of_probe": tf / FP64_PROBE_TFLOPS,
+                "kernel": desc, "algorithmic_flops_per_launch": 8 * A.nnz,
+                "algorithmic_bytes_per_launch": spmv_bytes(A.n, A.nnz), "launch_ms": sp_avg, "hbm": hbm}
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "traffic": traffic, "frac_of_nominal_8000": gbs / 8000.0,
+            "kernel": desc + "; peak %s (burst copy)" % peak_src,
+            "algorithmic_bytes_per_launch": spmv_bytes(A.n, A.nnz), "launch_ms": sp_avg}
+
+
+def double_float_entry(hz, torch, A, rp, cl, vl, bd, args, stream, steps=3):
+    """The double-float fast path (48-bit hi+lo binary32 values, binary32
+    exponent range), measured the same way as the headline for comparison:
+    the same solve from x0 = 0 and its SpMV roofline.  Not the paper's
+    arithmetic; reported beside the binary64 line, labelled."""
+    M = hz.Matrix(rp, cl, vl, ff=True)
+    x = torch.zeros_like(bd)
+    hz.zsolve(M, bd, x=x, tol=1e-10, maxit=args.maxit, x0_zero=True)
+    ms, its, sts = [], [], []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, info = hz.zsolve(M, bd, x=x, tol=1e-10, maxit=args.maxit, x0_zero=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        its.append(info.iters)
+        sts.append(info.status_name)
+    nbytes = sum(solve_bytes(A.n, A.nnz, it) for it in its)
+    out = {"dtype": DTYPES["ff"], "value": nbytes / (sum(ms) / 1e3) / 1e9, "unit": "GB/s",
+           "ms_per_step": sum(ms) / steps, "iters_per_step": its, "status": sts,
+           "iter_us": 1e3 * sum(ms) / max(sum(its), 1),
+           "roofline": spmv_roofline(hz, torch, M, A, stream, M.props()["spmv_kind"])}
+    M.close()
+    return out
+
+
+def cpu_baseline_entry(A, b, iters):
+    """The oracle's BiCGStab on the host cores: the plain single-thread
+    build and the OpenMP build (fixed-order chunk sums) on every core this
+    process may run on."""
+    import oracle
+    r1, dt1, it1 = cpu_oracle_rate(A, b, iters)
+    cores = len(os.sched_getaffinity(0))
+    out = {"value": r1, "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": f"{it1} BiCGStab iterations of C2 ({dt1:.1f} s), single-thread build"}
+    try:
+        rN, dtN, itN = cpu_oracle_rate(A, b, iters, threads=cores)
+        out["all_cores"] = {"value": rN, "unit": "GB/s", "cores": cores, "kind": "oracle (OpenMP build)",
+                            "sample": f"{itN} BiCGStab iterations of C2 ({dtN:.1f} s)"}
+    except Exception as e:   # no OpenMP runtime on this host
+        out["all_cores"] = {"unavailable": str(e)[:200]}
+    return out
 
 
 def main():
@@ -509,7 +602,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hz", choices=["hz", "reference"])
     ap.add_argument("--maxit", type=int, default=1000)
-    ap.add_argument("--arith", default="ff", choices=["ff", "fp64"])
+    ap.add_argument("--arith", default="fp64", choices=["ff", "fp64"],
+                    help="fp64: binary64 arithmetic (the paper's); ff: the double-float path")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the labelled double-float entry beside a binary64 line")
     # the oracle runs ~30 ms per C2 iteration on one Grace core: 500
     # iterations are ~15 s of CPU work, 200 per reference step ~6 s
     ap.add_argument("--ref-iters", type=int, default=200)
@@ -551,7 +647,8 @@ def main():
     cl = torch.as_tensor(A.col).to(dev)
     vl = torch.as_tensor(A.val).to(dev)
     bd = torch.as_tensor(b).to(dev)
-    M = hz.Matrix(rp, cl, vl, ff=args.arith == "ff")
+    ff = args.arith == "ff"
+    M = hz.Matrix(rp, cl, vl, ff=ff)
     if args.spmv:
         M.set_spmv(args.spmv, args.group)
     xd = torch.zeros_like(bd)
@@ -561,9 +658,10 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---------------- device-resident solve steps
+    # ---------------- device-resident solve steps: every step is the whole
+    # solve from x0 = 0 (x0_zero: xd only receives the result)
     for _ in range(args.warmup):
-        hz.zsolve(M, bd, x=xd, tol=1e-10, maxit=args.maxit)
+        hz.zsolve(M, bd, x=xd, tol=1e-10, maxit=args.maxit, x0_zero=True)
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -572,7 +670,7 @@ def main():
     with ClockSampler(local) as clk:
         for e0, e1 in ev:
             e0.record(stream)
-            _, info = hz.zsolve(M, bd, x=xd, tol=1e-10, maxit=args.maxit)
+            _, info = hz.zsolve(M, bd, x=xd, tol=1e-10, maxit=args.maxit, x0_zero=True)
             e1.record(stream)
             infos.append(info)
         barrier()
@@ -599,7 +697,7 @@ def main():
         d_cl = h_cl.to(dev, non_blocking=True)
         d_vl = h_vl.to(dev, non_blocking=True)
         d_b = h_b.to(dev, non_blocking=True)
-        M2 = hz.Matrix(d_rp, d_cl, d_vl, ff=args.arith == "ff")
+        M2 = hz.Matrix(d_rp, d_cl, d_vl, ff=ff)
         if args.spmv:
             M2.set_spmv(args.spmv, args.group)
         x2, inf2 = hz.zsolve(M2, d_b, tol=1e-10, maxit=args.maxit)
@@ -613,36 +711,32 @@ def main():
     e2e_t, e2e_bytes = job_totals(sum(e2e_times), e2e_bytes, world, dev)
     e2e_value = e2e_bytes / e2e_t / 1e9
 
-    # ---------------- roofline of the dominant kernel: the CSR SpMV core
+    # ---------------- roofline of the dominant kernel: the SpMV core
     # Every launch is preceded by a 1 GiB write (flushes the 129 MB L2 and
     # keeps the GPU busy while the host enqueues the next launch, so host
     # launch latency never lands between the events); all launches are
     # enqueued before the one synchronisation.
-    sp_avg = time_spmv(hz, torch, M, A.n, stream)
-    peak, peak_src = peaks()
-    achieved = spmv_bytes(A.n, A.nnz) / (sp_avg / 1e3) / 1e9
-    traffic = recorded_traffic()
-
     props = M.props()
+    line_roof = spmv_roofline(hz, torch, M, A, stream, props["spmv_kind"])
+
     launches = sum(4 + 5 * it for it in iters)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.arith], "data": "synthetic",
-        "config": workload_config(A, args.maxit, args.arith),
-        "solve": {"iters_per_step": iters[0], "status": infos[-1].status_name,
+        "config": workload_config(A, args.maxit, args.arith, iters[0], infos[-1].status_name),
+        "solve": {"iters_per_step": iters, "status": [i.status_name for i in infos],
                   "relres_true": infos[-1].relres_true, "s_per_solve": t_max / args.steps / 1e3,
                   "iter_us": 1e3 * t_max / args.steps / max(iters[0], 1),
-                  "spmv_variant": {"kind": props["spmv_kind"], "group": props["group"]}},
+                  "spmv_variant": {"kind": props["spmv_kind"], "group": props["group"],
+                                   "name": SPMV_KINDS.get(props["spmv_kind"])}},
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "frac_of_nominal_8000": achieved / 8000.0,
-                     "kernel": "%s SpMV through hz_zspmv alone, L2 flushed; peak %s (burst copy)"
-                               % (SPMV_KINDS.get(props["spmv_kind"], props["spmv_kind"]), peak_src),
-                     "algorithmic_bytes_per_launch": spmv_bytes(A.n, A.nnz), "launch_ms": sp_avg},
+        "roofline": line_roof,
         "clocks": clk.summary(),
         "gpu_launches": launches,
     }
+    if rank == 0 and not ff and not args.no_secondary:
+        line["double_float"] = double_float_entry(hz, torch, A, rp, cl, vl, bd, args, stream)
     if rank == 0 and not args.no_compare:
         line["compare"] = compare_modes(hz, torch, args.c4_full, args.compare_maxit)
         line["spmv_h1"] = spmv_h1(hz, torch, stream)
@@ -650,9 +744,7 @@ def main():
         line["adjoint_c5"] = adjoint_c5(hz, torch, stream)
         line["blas_sweep"] = blas_sweep(hz, torch, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, dt, it = cpu_oracle_rate(A, b, args.cpu_iters)
-        line["cpu_baseline"] = {"value": r, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{it} BiCGStab iterations of C2 ({dt:.1f} s)"}
+        line["cpu_baseline"] = cpu_baseline_entry(A, b, args.cpu_iters)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

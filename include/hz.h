@@ -67,7 +67,15 @@ enum {
     HZ_FLAG_C64 = 4u,        /* also build the complex64 copy used by the mixed solver */
     HZ_FLAG_AUTOTUNE = 8u,   /* time the SpMV variants once on this matrix and keep the fastest */
     HZ_FLAG_FF = 16u         /* also build the double-float split of the values and use the
-                                double-float SpMV (binary64 emulated on the binary32 pipes) */
+                                double-float SpMV: every binary64 value is carried as hi + lo
+                                binary32 parts (48 significant bits, NOT binary64) on the
+                                binary32 pipes.  The split keeps its 48 bits only for values
+                                of magnitude in [2^-100, 2^101): if any stored value lies
+                                outside, the handle keeps the binary64 kind HZ_SPMV_FLAT64
+                                (hz_mat_query reports it).  hz_zspmv on a double-float kind
+                                needs x in the same range; the BiCGStab solve scales b and the
+                                operator by powers of two (exact) so that its vectors stay
+                                there whatever the size of b */
 };
 
 /* solver modes */
@@ -107,9 +115,14 @@ enum {
     HZ_SPMV_FF_FLAT = 4,     /* double-float, row blocks streamed flat: each entry's product is
                                 formed with coalesced loads and all lanes busy, then whole rows
                                 are summed from shared memory (the default with HZ_FLAG_FF) */
-    HZ_SPMV_FF_TMA = 5       /* HZ_SPMV_FF_FLAT with the values and columns moved into shared
+    HZ_SPMV_FF_TMA = 5,      /* HZ_SPMV_FF_FLAT with the values and columns moved into shared
                                 memory by bulk asynchronous copies, one row block ahead of the
                                 arithmetic */
+    HZ_SPMV_FLAT64 = 6       /* binary64 (IEEE double FMAs), row blocks of complete rows with every
+                                lane summing one contiguous run of entries, rows that cross a
+                                run boundary finished from the runs' partial sums (the default
+                                without HZ_FLAG_FF); per-entry error within the binary64 bound
+                                of a sequential row sum */
 };
 
 typedef struct {

@@ -11,4 +11,5 @@ itself, is in ``tests/test_oracle_pins.py`` (one or more tests per function).
 from .oracle import (  # noqa: F401
     build, load, zspmv, cspmv, zdotc, zdotu, dznrm2, zaxpy, zscal, zcopy,
     bicgstab, cbicgstab, refine_mixed, outer_on_pattern, OracleInfo, jacobi_dinv, zmul_elementwise, bicgstabl, tfqmr,
+    build_omp, bicgstab_omp,
 )

@@ -21,6 +21,22 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Built plainly (the tests, the smoke check and the single-thread baseline)
+ * every loop below runs sequentially and OR_PAR_FOR is empty.  Built with
+ * -fopenmp (only for the benchmark's all-cores CPU baseline), the SpMV rows
+ * and the BiCGStab vector updates are spread over threads, and the reductions
+ * (or_zdotc, or_dznrm2) sum fixed chunks of OR_CHUNK elements with the same
+ * compensated sum and then add the chunk totals in chunk order, so that the
+ * result does not depend on the number of threads. */
+#ifdef _OPENMP
+#include <omp.h>
+#define OR_PAR_FOR _Pragma("omp parallel for schedule(static)")
+#define OR_CHUNK 8192
+void or_set_threads(int32_t k) { omp_set_num_threads(k); }
+#else
+#define OR_PAR_FOR
+#endif
+
 typedef struct { double re, im; } oz;   /* complex double */
 typedef struct { float re, im; } oc;    /* complex float  */
 
@@ -67,6 +83,7 @@ static double ks_val(const ksum *k) { return k->s + k->c; }
 void or_zspmv(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *val,
               const oz *x, oz *y)
 {
+    OR_PAR_FOR
     for (int32_t i = 0; i < n; ++i) {
         oz acc = {0.0, 0.0};
         for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
@@ -88,6 +105,7 @@ void or_cspmv(int32_t n, const int32_t *rowptr, const int32_t *col, const oc *va
 }
 
 /* Section 5, dot product: sum_i conj(x_i) y_i (conjugated) */
+#ifndef _OPENMP
 void or_zdotc(int64_t n, const oz *x, const oz *y, oz *out)
 {
     ksum re = {0, 0}, im = {0, 0};
@@ -99,6 +117,30 @@ void or_zdotc(int64_t n, const oz *x, const oz *y, oz *out)
     out->re = ks_val(&re);
     out->im = ks_val(&im);
 }
+#else
+void or_zdotc(int64_t n, const oz *x, const oz *y, oz *out)
+{
+    int64_t nc = (n + OR_CHUNK - 1) / OR_CHUNK;
+    oz *part = malloc((size_t)(nc > 0 ? nc : 1) * sizeof(oz));
+    ksum re = {0, 0}, im = {0, 0};
+    OR_PAR_FOR
+    for (int64_t c = 0; c < nc; ++c) {
+        ksum cr = {0, 0}, ci = {0, 0};
+        int64_t e = (c + 1) * OR_CHUNK < n ? (c + 1) * OR_CHUNK : n;
+        for (int64_t i = c * OR_CHUNK; i < e; ++i) {
+            oz p = z_mul(z_conj(x[i]), y[i]);
+            ks_add(&cr, p.re);
+            ks_add(&ci, p.im);
+        }
+        part[c].re = ks_val(&cr);
+        part[c].im = ks_val(&ci);
+    }
+    for (int64_t c = 0; c < nc; ++c) { ks_add(&re, part[c].re); ks_add(&im, part[c].im); }
+    free(part);
+    out->re = ks_val(&re);
+    out->im = ks_val(&im);
+}
+#endif
 
 /* Section 5, dot product without conjugation: sum_i x_i y_i */
 void or_zdotu(int64_t n, const oz *x, const oz *y, oz *out)
@@ -114,6 +156,7 @@ void or_zdotu(int64_t n, const oz *x, const oz *y, oz *out)
 }
 
 /* Section 5, L2 norm: sqrt(sum_i |x_i|^2) */
+#ifndef _OPENMP
 double or_dznrm2(int64_t n, const oz *x)
 {
     ksum s = {0, 0};
@@ -123,6 +166,27 @@ double or_dznrm2(int64_t n, const oz *x)
     }
     return sqrt(ks_val(&s));
 }
+#else
+double or_dznrm2(int64_t n, const oz *x)
+{
+    int64_t nc = (n + OR_CHUNK - 1) / OR_CHUNK;
+    double *part = malloc((size_t)(nc > 0 ? nc : 1) * sizeof(double));
+    ksum s = {0, 0};
+    OR_PAR_FOR
+    for (int64_t c = 0; c < nc; ++c) {
+        ksum cs = {0, 0};
+        int64_t e = (c + 1) * OR_CHUNK < n ? (c + 1) * OR_CHUNK : n;
+        for (int64_t i = c * OR_CHUNK; i < e; ++i) {
+            ks_add(&cs, x[i].re * x[i].re);
+            ks_add(&cs, x[i].im * x[i].im);
+        }
+        part[c] = ks_val(&cs);
+    }
+    for (int64_t c = 0; c < nc; ++c) ks_add(&s, part[c]);
+    free(part);
+    return sqrt(ks_val(&s));
+}
+#endif
 
 /* Section 5, Zaxpy: y_i = alpha x_i + y_i */
 void or_zaxpy(int64_t n, const oz *alpha, const oz *x, oz *y)
@@ -227,6 +291,7 @@ int or_bicgstab_pc(int32_t n, const int32_t *rowptr, const int32_t *col, const o
     for (;;) {                           /* at most one restart */
         oz rho_old = {1, 0}, alpha = {1, 0}, omega = {1, 0};
         or_zspmv(n, rowptr, col, val, x, r);
+        OR_PAR_FOR
         for (int32_t i = 0; i < n; ++i) { r[i] = z_sub(b[i], r[i]); rh[i] = r[i]; }
         memset(p, 0, (size_t)n * sizeof(oz));
         memset(v, 0, (size_t)n * sizeof(oz));
@@ -242,6 +307,7 @@ int or_bicgstab_pc(int32_t n, const int32_t *rowptr, const int32_t *col, const o
                 or_zdotc(n, rh, r, &rho);
                 if (rho.re == 0.0 && rho.im == 0.0) { status = OR_BREAKDOWN; break; }
                 beta = z_mul(z_div(rho, rho_old), z_div(alpha, omega));
+                OR_PAR_FOR
                 for (int32_t i = 0; i < n; ++i)
                     p[i] = z_add(r[i], z_mul(beta, z_sub(p[i], z_mul(omega, v[i]))));
                 if (dinv) or_zmul_elementwise(n, dinv, p, ph);
@@ -249,6 +315,7 @@ int or_bicgstab_pc(int32_t n, const int32_t *rowptr, const int32_t *col, const o
                 or_zdotc(n, rh, v, &sig);
                 if (sig.re == 0.0 && sig.im == 0.0) { status = OR_BREAKDOWN; break; }
                 alpha = z_div(rho, sig);
+                OR_PAR_FOR
                 for (int32_t i = 0; i < n; ++i) s[i] = z_sub(r[i], z_mul(alpha, v[i]));
                 rel = z_norm(n, s) / nb;
                 if (!isfinite(rel)) { status = OR_NAN; break; }
@@ -264,6 +331,7 @@ int or_bicgstab_pc(int32_t n, const int32_t *rowptr, const int32_t *col, const o
                 or_zdotc(n, t, t, &tt);
                 if (tt.re == 0.0 && tt.im == 0.0) { status = OR_BREAKDOWN; break; }
                 omega = z_div(ts, tt);
+                OR_PAR_FOR
                 for (int32_t i = 0; i < n; ++i) {
                     x[i] = z_add(x[i], z_add(z_mul(alpha, ph[i]), z_mul(omega, sh[i])));
                     r[i] = z_sub(s[i], z_mul(omega, t[i]));
@@ -642,16 +710,19 @@ done:
  *   repeat: r = b - A x (binary64);  stop if ||r|| <= tol ||b||
  *           solve A d = r approximately in complex64 (inner BiCGStab, tol_in)
  *           x = x + d (binary64)
- * The complex64 operator is the rounded copy val32 of val. */
+ * The complex64 operator is the rounded copy val32 of val.  The refinement
+ * keeps the iterate with the smallest outer residual: when a step fails to
+ * reduce ||r|| (or the residual is not finite), it stops and returns that
+ * best iterate with its residual instead of the last one. */
 int or_refine_mixed(int32_t n, const int32_t *rowptr, const int32_t *col, const oz *val,
                     const oc *val32, const oz *b, oz *x, double tol, float tol_in,
                     int32_t maxit_in, int32_t max_outer, int32_t *outer_out,
                     int32_t *inner_total, double *relres_out)
 {
-    oz *r = calloc((size_t)n, sizeof(oz));
+    oz *r = calloc((size_t)n, sizeof(oz)), *xbest = calloc((size_t)n, sizeof(oz));
     oc *r32 = calloc((size_t)n, sizeof(oc)), *d32 = calloc((size_t)n, sizeof(oc));
-    double nb = z_norm(n, b), rel = 0.0;
-    int32_t outer = 0, inner = 0, status = OR_NOT_CONVERGED;
+    double nb = z_norm(n, b), rel = 0.0, best = INFINITY;
+    int32_t outer = 0, inner = 0, status = OR_NOT_CONVERGED, use_best = 0;
     if (nb == 0.0) {
         memset(x, 0, (size_t)n * sizeof(oz));
         status = OR_OK;
@@ -661,9 +732,12 @@ int or_refine_mixed(int32_t n, const int32_t *rowptr, const int32_t *col, const 
             or_zspmv(n, rowptr, col, val, x, r);
             for (int32_t i = 0; i < n; ++i) r[i] = z_sub(b[i], r[i]);
             rel = z_norm(n, r) / nb;
-            if (!isfinite(rel)) { status = OR_NAN; break; }
+            if (!isfinite(rel)) { status = OR_NAN; use_best = outer > 0; break; }
             if (rel <= tol) { status = OR_OK; break; }
+            if (rel >= best) { use_best = 1; break; }
             if (outer >= max_outer) break;
+            best = rel;
+            memcpy(xbest, x, (size_t)n * sizeof(oz));
             ++outer;
             for (int32_t i = 0; i < n; ++i) { r32[i].re = (float)r[i].re; r32[i].im = (float)r[i].im; }
             k = or_cbicgstab(n, rowptr, col, val32, r32, d32, tol_in, maxit_in, &st, NULL);
@@ -674,10 +748,14 @@ int or_refine_mixed(int32_t n, const int32_t *rowptr, const int32_t *col, const 
             }
         }
     }
+    if (use_best) {
+        memcpy(x, xbest, (size_t)n * sizeof(oz));
+        rel = best;
+    }
     *outer_out = outer;
     *inner_total = inner;
     *relres_out = rel;
-    free(r); free(r32); free(d32);
+    free(r); free(xbest); free(r32); free(d32);
     return status;
 }
 

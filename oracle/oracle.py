@@ -29,6 +29,43 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source built with -fopenmp: SpMV rows and BiCGStab vector
+    updates over threads, reductions over fixed chunks (deterministic for
+    any thread count).  Used only for the benchmark's all-cores CPU baseline;
+    the tests use the plain build."""
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        tmp = _LIB_OMP + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def bicgstab_omp(A, b, tol=1e-10, maxit=2000, threads=1):
+    """or_bicgstab from the OpenMP build on `threads` threads; returns (x, OracleInfo)."""
+    global _lib_omp
+    if _lib_omp is None:
+        build_omp()
+        lib = C.CDLL(_LIB_OMP)
+        P = C.c_void_p
+        lib.or_bicgstab.argtypes = [C.c_int32, P, P, P, P, P, C.c_double, C.c_int32, P, P]
+        lib.or_bicgstab.restype = C.c_int
+        lib.or_set_threads.argtypes = [C.c_int32]
+        _lib_omp = lib
+    _lib_omp.or_set_threads(int(threads))
+    b = _z(b)
+    x = np.zeros(A.n, dtype=np.complex128)
+    info = _OrInfo()
+    rp, cl, vl = _i(A.rowptr), _i(A.col), _z(A.val)
+    _lib_omp.or_bicgstab(A.n, _p(rp), _p(cl), _p(vl), _p(b), _p(x), float(tol), int(maxit), None, C.byref(info))
+    return x, OracleInfo(info.iters, info.status, info.restarts, info.relres_rec, info.relres_true)
+
+
 def load():
     global _lib
     if _lib is None:

@@ -22,7 +22,8 @@ HZ_FLAG_VALIDATE, HZ_FLAG_SELL, HZ_FLAG_C64, HZ_FLAG_AUTOTUNE, HZ_FLAG_FF = 1, 2
 HZ_MODE_FP64, HZ_MODE_MIXED = 0, 1
 HZ_PRECOND_NONE, HZ_PRECOND_JACOBI = 0, 1
 HZ_METHOD_BICGSTAB, HZ_METHOD_BICGSTABL, HZ_METHOD_TFQMR = 0, 1, 2
-HZ_SPMV_CSR_VECTOR, HZ_SPMV_SELL, HZ_SPMV_FF, HZ_SPMV_SELL_FF, HZ_SPMV_FF_FLAT, HZ_SPMV_FF_TMA = 0, 1, 2, 3, 4, 5
+(HZ_SPMV_CSR_VECTOR, HZ_SPMV_SELL, HZ_SPMV_FF, HZ_SPMV_SELL_FF, HZ_SPMV_FF_FLAT, HZ_SPMV_FF_TMA,
+ HZ_SPMV_FLAT64) = 0, 1, 2, 3, 4, 5, 6
 
 # every symbol include/hz.h declares
 EXPORTS = (

@@ -65,7 +65,9 @@ struct EpiSigma : EpiBase<V> {
     __device__ bool skip() const { return st->done; }
     using Pre = V;   // rh[i], fetched ahead by the block-flat kernel
     __device__ V pre(int i) const { return rh[i]; }
+    double s;   // operator scale (double-float path; 1 in binary64)
     template <int N> __device__ void row(int i, V y, Acc (&acc)[N], const V &rhi) const {
+        if constexpr (Ar<V>::kFF) y = Ar<V>::pow2(y, s);
         v[i] = y;
         Ar<V>::dotc(acc[0], acc[1], rhi, y);
     }
@@ -121,7 +123,9 @@ struct EpiOmega : EpiBase<V> {
     __device__ bool skip() const { return st->done || st->half; }
     using Pre = V;   // s[i], fetched ahead by the block-flat kernel
     __device__ V pre(int i) const { return s[i]; }
+    double sc;   // operator scale (double-float path; 1 in binary64)
     template <int N> __device__ void row(int i, V y, Acc (&acc)[N], const V &si) const {
+        if constexpr (Ar<V>::kFF) y = Ar<V>::pow2(y, sc);
         t[i] = y;
         Ar<V>::dotc(acc[0], acc[1], y, si);
         Ar<V>::nrm2(acc[2], y);
@@ -217,8 +221,8 @@ struct EpiInit : EpiBase<V> {
     cudaGraphConditionalHandle h;
     __device__ bool skip() const { return false; }
     template <int N> __device__ void row(int i, V y, Acc (&acc)[N]) const {
-        const V bi = Ar<V>::from_c128(ctl->b[i]);
-        const V ri = Ar<V>::sub(bi, y);
+        const V bi = Ar<V>::from_c128(zscale(ctl->b[i], rhs_scale(ctl)));
+        const V ri = Ar<V>::sub(bi, Ar<V>::pow2(y, ctl->op_scale));
         r[i] = ri;
         rh[i] = ri;
         p[i] = Ar<V>::zero();
@@ -290,13 +294,23 @@ struct EpiOuter : EpiBase<V> {
             ost->rel = 0.0; ost->status = HZ_OK; ost->zero_x = 1;
             if (ctl->hist) ctl->hist[ost->outer] = 0.0;
         } else {
+            // the refinement keeps the iterate with the smallest outer
+            // residual and stops as soon as a step fails to reduce it: the
+            // answer is then that best iterate, not the last one
             const double rel = sqrt((double)tot[0]) / nb;
+            const double best = ost->rel_best;
             ost->rel = rel;
             if (ctl->hist) ctl->hist[ost->outer] = rel;
-            if (!finite_d(rel)) ost->status = HZ_ERR_NAN;
+            ost->save = 0;
+            if (!finite_d(rel)) { ost->status = HZ_ERR_NAN; ost->use_best = ost->outer > 0; }
             else if (rel <= ctl->tol) ost->status = HZ_OK;
+            else if (rel >= best) { ost->status = HZ_NOT_CONVERGED; ost->use_best = 1; }
             else if (ost->outer >= ctl->max_outer || *total_inner >= ctl->maxit) ost->status = HZ_NOT_CONVERGED;
-            else done = false;
+            else {
+                done = false;
+                ost->rel_best = rel;
+                ost->save = 1;   // x is the best so far: k_mixed_update keeps a copy
+            }
         }
         ost->done = done ? 1 : 0;
         if (!done) {
@@ -313,23 +327,32 @@ struct EpiOuter : EpiBase<V> {
             in->done = (in->nb == 0.0) ? 1 : 0;
         } else {
             in->done = 1;
-            info->iters = *total_inner;
-            info->status = ost->status;
-            info->outer = ost->outer;
-            info->relres_rec = ost->rel;
-            info->relres_true = ost->rel;
-            info->zero_x = ost->zero_x;
         }
         cudaGraphSetConditional(h_inner, (!done && !in->done) ? 1 : 0);
         cudaGraphSetConditional(h_outer, done ? 0 : 1);
     }
 };
 
+// last node of the refinement loop body: the outer loop goes on only while
+// the refinement state is not done and the body has run at most
+// max_outer + 1 times (the cap that EpiOuter itself enforces)
+__global__ void k_outer_guard(OuterState *ost, const Ctl *ctl, cudaGraphConditionalHandle h) {
+    const int runs = ost->guard + 1;
+    const bool go = !ost->done && runs <= ctl->max_outer + 1;
+    if (!go && !ost->done) {
+        ost->status = HZ_NOT_CONVERGED;
+        ost->done = 1;
+    }
+    ost->guard = go ? runs : 0;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 template <class V>
 __global__ void __launch_bounds__(kVecBlock) k_mixed_start(int n, const Ctl *ctl, OuterState *ost, int *total_inner,
                                                            V *__restrict__ xw) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ost->outer = 0; ost->done = 0; ost->status = HZ_NOT_CONVERGED; ost->zero_x = 0;
+        ost->rel_best = INFINITY; ost->save = 0; ost->use_best = 0; ost->guard = 0;
         *total_inner = 0;
     }
     const double2 *x0 = ctl->x, *pd = ctl->pre_d;
@@ -337,12 +360,45 @@ __global__ void __launch_bounds__(kVecBlock) k_mixed_start(int n, const Ctl *ctl
     vec_tiles(n, [&](int i) { xw[i] = zero ? Ar<V>::zero() : Ar<V>::from_c128(pd ? cmul(x0[i], pd[i]) : x0[i]); });
 }
 
-// x += d (d from the complex64 inner solve)
+// x += d (d from the complex64 inner solve); when the refinement marked the
+// current x as its best iterate so far, x is first copied to xb
 template <class V>
 __global__ void __launch_bounds__(kVecBlock) k_mixed_update(int n, const OuterState *ost, V *__restrict__ xw,
-                                                            const float2 *__restrict__ d) {
+                                                            V *__restrict__ xb, const float2 *__restrict__ d) {
     if (ost->done) return;
-    vec_tiles(n, [&](int i) { xw[i] = Ar<V>::sub(xw[i], Ar<V>::from_c128(to_c128(make_float2(-d[i].x, -d[i].y)))); });
+    const bool save = ost->save != 0;
+    vec_tiles(n, [&](int i) {
+        const V xi = xw[i];
+        if (save) xb[i] = xi;
+        xw[i] = Ar<V>::sub(xi, Ar<V>::from_c128(to_c128(make_float2(-d[i].x, -d[i].y))));
+    });
+}
+
+// copy-out of the refinement: the answer is the current x, or the kept best
+// iterate when the last step did not reduce the outer residual; the info
+// block is written from the refinement state
+template <class V>
+__global__ void __launch_bounds__(kVecBlock) k_mixed_copy_out(int n, const Ctl *ctl, const OuterState *ost,
+                                                              const int *total_inner, Info *info,
+                                                              const V *__restrict__ xw, const V *__restrict__ xb,
+                                                              const int *fault) {
+    const bool best = ost->use_best != 0, zero = ost->zero_x != 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        info->iters = *total_inner;
+        info->status = ost->status;
+        info->outer = ost->outer;
+        info->relres_rec = info->relres_true = best ? ost->rel_best : ost->rel;
+        info->zero_x = ost->zero_x;
+        // an expired bounded wait in an SpMV of this solve voids the result
+        if (fault && *(volatile const int *)fault) info->status = HZ_ERR_TIMEOUT;
+    }
+    double2 *x = ctl->x;
+    const double2 *pdi = ctl->pre_dinv;
+    const V *src = best ? xb : xw;
+    vec_tiles(n, [&](int i) {
+        const double2 y = Ar<V>::to_c128(src[i]);
+        x[i] = zero ? make_double2(0.0, 0.0) : (pdi ? cmul(y, pdi[i]) : y);
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -353,8 +409,10 @@ struct Solver {
     int grid_spmv = 1, grid_vec = 1;
     int grid_spmv_cv = 1;   // grid of the binary64/complex64 CSR or SELL kernels
     int grid_c64 = 1;       // grid of the block-flat complex64 kernel
+    double op_scale = 1.0;  // double-float BiCGStab: the iteration runs on op_scale * A
     bool pdl = false;       // programmatic dependent launches inside the iteration
     void *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
+    void *xbest = nullptr;  // mixed: the refinement's best iterate
     float2 *r32 = nullptr, *rh32 = nullptr, *p32 = nullptr, *v32 = nullptr, *s32 = nullptr, *t32 = nullptr,
            *d32 = nullptr;
     BiState<double2> *st = nullptr;
@@ -376,7 +434,7 @@ static void solver_free(Solver *S) {
     if (S->exec) cudaGraphExecDestroy(S->exec);
     if (S->graph) cudaGraphDestroy(S->graph);
     if (S->cap) cudaStreamDestroy(S->cap);
-    void *dev[] = {S->x, S->r, S->rh, S->p, S->v, S->s, S->t, S->r32, S->rh32, S->p32, S->v32, S->s32, S->t32,
+    void *dev[] = {S->x, S->xbest, S->r, S->rh, S->p, S->v, S->s, S->t, S->r32, S->rh32, S->p32, S->v32, S->s32, S->t32,
                    S->d32, S->st, S->st32, S->ost, S->dinfo, S->dctl, S->total, S->red.partials, S->red.counter};
     for (void *q : dev) cudaFree(q);
     cudaFreeHost(S->hctl);
@@ -409,6 +467,7 @@ static hz_status solver_alloc(Solver *S) {
         HZ_ALLOC(S->s, n * vb);
         HZ_ALLOC(S->t, n * vb);
     } else {
+        HZ_ALLOC(S->xbest, n * vb);
         HZ_ALLOC(S->r32, n * sizeof(float2));
         HZ_ALLOC(S->rh32, n * sizeof(float2));
         HZ_ALLOC(S->p32, n * sizeof(float2));
@@ -442,18 +501,17 @@ static hz_status solver_alloc(Solver *S) {
 template <class V, class Epi>
 static void spmv_on(const Solver *S, const hz_mat *A, const V *x, const Epi &e, cudaStream_t cs,
                     bool pdl = false) {
-    const bool sell = S->kind == HZ_SPMV_SELL || S->kind == HZ_SPMV_SELL_FF;
     if constexpr (std::is_same<V, float4>::value) {
         launch_spmv_ff(S->kind, S->group, mat_view<double2>(A), x, e, S->red, S->grid_spmv, cs, pdl);
     } else if constexpr (std::is_same<V, float2>::value) {
         // complex64 inner operator: block-flat when the handle runs a block-flat kind
-        if (A->fblk && (S->kind == HZ_SPMV_FF_FLAT || S->kind == HZ_SPMV_FF_TMA))
+        if (A->fblk && d64_kind(S->kind) == HZ_SPMV_FLAT64)
             launch_k(pdl, k_spmv_c64b<Epi>, S->grid_c64, kFlatThreads, cs, mat_view<float2>(A), x, e, S->red);
         else
-            launch_spmv<V>(S->kind == HZ_SPMV_SELL || S->kind == HZ_SPMV_SELL_FF ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR,
+            launch_spmv<V>(d64_kind(S->kind),
                            S->group, mat_view<V>(A), x, e, S->red, S->grid_spmv_cv, cs, pdl);
     } else {
-        launch_spmv<V>(sell ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR, S->group, mat_view<V>(A), x, e, S->red,
+        launch_spmv<V>(d64_kind(S->kind), S->group, mat_view<V>(A), x, e, S->red,
                        S->grid_spmv_cv, cs, pdl);
     }
 }
@@ -468,12 +526,12 @@ static void launch_iteration(const Solver *S, const hz_mat *A, StateOf<V> *st, V
     const bool pdl = S->pdl;
     launch_k(false, k_bicg_p<V>, S->grid_vec, kVecBlock, cs, n, st, p, r, v, total);
     EpiSigma<V> e2;
-    e2.st = st; e2.v = v; e2.rh = rh;
+    e2.st = st; e2.v = v; e2.rh = rh; e2.s = S->op_scale;
     spmv_on<V>(S, A, p, e2, cs, pdl);
     launch_k(pdl, k_bicg_s<V>, S->grid_vec, kVecBlock, cs, n, st, (const Ctl *)S->dctl, s, r, v, S->red,
              outer_level);
     EpiOmega<V> e4;
-    e4.st = st; e4.t = t; e4.s = s;
+    e4.st = st; e4.t = t; e4.s = s; e4.sc = S->op_scale;
     spmv_on<V>(S, A, s, e4, cs, pdl);
     launch_k(pdl, k_bicg_xr<V>, S->grid_vec, kVecBlock, cs, n, st, (const Ctl *)S->dctl, x, r, rh, p, s, t,
              (const int *)total, S->red, h, outer_level);
@@ -499,6 +557,8 @@ static hz_status build_fp64_graph(Solver *S, const hz_mat *A, cudaGraph_t g) {
     if (unroll <= 0) HZ_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, mode));
     cudaMemcpyAsync(S->dctl, S->hctl, sizeof(Ctl), cudaMemcpyHostToDevice, cs);
+    // double-float: scale the right-hand side to O(1) (binary32 exponent range)
+    if constexpr (Ar<V>::kFF) k_bmax<<<S->grid_vec, 256, 0, cs>>>(n, S->dctl);
     k_init_x<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->dctl, x);
     EpiInit<V> ei;
     ei.st = st; ei.info = S->dinfo; ei.ctl = S->dctl; ei.r = r; ei.rh = rh; ei.p = p; ei.v = v; ei.h = h;
@@ -513,6 +573,7 @@ static hz_status build_fp64_graph(Solver *S, const hz_mat *A, cudaGraph_t g) {
         HZ_TRY(add_while(g, leaves, h, &wn, &body));
         HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
         launch_iteration<V>(S, A, st, x, r, rh, p, v, s, t, nullptr, h, 1, cs);
+        k_loop_guard<typename Ar<V>::St><<<1, 1, 0, cs>>>(st, S->dctl, 1, h);
         HZ_CUDA(cudaStreamEndCapture(cs, &body));
         HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, &wn, nullptr, 1, mode));
     }
@@ -557,12 +618,15 @@ static hz_status build_mixed_graph(Solver *S, const hz_mat *A, cudaGraph_t g) {
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, ibody, nullptr, nullptr, 0, mode));
     launch_iteration<float2>(S, A, S->st32, S->d32, S->r32, S->rh32, S->p32, S->v32, S->s32, S->t32, S->total, hi,
                              0, cs);
+    k_loop_guard<float2><<<1, 1, 0, cs>>>(S->st32, S->dctl, 0, hi);
     HZ_CUDA(cudaStreamEndCapture(cs, &ibody));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, obody, &wi, nullptr, 1, mode));
-    k_mixed_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->ost, x, S->d32);
+    k_mixed_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->ost, x, (V *)S->xbest, S->d32);
+    k_outer_guard<<<1, 1, 0, cs>>>(S->ost, S->dctl, ho);
     HZ_CUDA(cudaStreamEndCapture(cs, &obody));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, &wo, nullptr, 1, mode));
-    k_copy_out<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->dctl, S->dinfo, x, A->fault);
+    k_mixed_copy_out<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->dctl, S->ost, S->total, S->dinfo, x,
+                                                          (const V *)S->xbest, A->fault);
     cudaMemcpyAsync(S->hinfo, S->dinfo, sizeof(Info), cudaMemcpyDeviceToHost, cs);
     HZ_CUDA(cudaStreamEndCapture(cs, &g));
     return HZ_OK;
@@ -597,8 +661,7 @@ static hz_status get_solver(hz_mat *A, uint32_t mode, cudaStream_t s, Solver **o
         S->kind = A->spmv_kind;
         S->group = A->group;
         S->grid_spmv = spmv_grid(A, S->kind, S->group);
-        const bool sell = S->kind == HZ_SPMV_SELL || S->kind == HZ_SPMV_SELL_FF;
-        S->grid_spmv_cv = spmv_grid(A, sell ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR, S->group);
+        S->grid_spmv_cv = spmv_grid(A, d64_kind(S->kind), S->group);
         S->grid_c64 = A->fblk ? c64_flat_grid(A) : 1;
         // HZ_PDL=1 (environment) captures F2..F5 as programmatic dependent
         // launches; measured slower on the C2 solve (185 vs 175 us per
@@ -606,7 +669,11 @@ static hz_status get_solver(hz_mat *A, uint32_t mode, cudaStream_t s, Solver **o
         const char *pdl_env = getenv("HZ_PDL");
         S->pdl = pdl_env && atoi(pdl_env) != 0;
         S->grid_vec = stream_grid(d, (A->n + kVecUnroll - 1) / kVecUnroll, kVecBlock, 8);
-        hz_status st = solver_alloc(S);
+        hz_status st = HZ_OK;
+        // the double-float iteration runs on A scaled to unit size, so that
+        // A p and A s stay inside the binary32 exponent range
+        if (mode == HZ_MODE_FP64 && is_ff_kind(S->kind)) st = operator_scale(A, &S->op_scale);
+        if (st == HZ_OK) st = solver_alloc(S);
         if (st == HZ_OK) st = build_graph(S, A);
         if (st != HZ_OK) { solver_free(S); return st; }
         A->solver[mode] = S;
@@ -673,6 +740,7 @@ extern "C" HZ_API hz_status hz_zsolve_opts(hz_mat *A, const hz_z *d_b, hz_z *d_x
     Solver *S = nullptr;
     HZ_TRY(get_solver(op, o->mode, s, &S));
     *S->hctl = c;
+    S->hctl->op_scale = S->op_scale;
     HZ_CUDA(cudaGraphLaunch(S->exec, s));
     HZ_CUDA(cudaStreamSynchronize(s));
     Info inf = *S->hinfo;

@@ -438,8 +438,7 @@ static void bl_spmv(const BlSolver *S, const hz_mat *A, const V *x, const Epi &e
     if constexpr (std::is_same<V, float4>::value) {
         launch_spmv_ff(S->kind, S->group, mat_view<double2>(A), x, e, S->red, S->grid_spmv, cs);
     } else {
-        const bool sell = S->kind == HZ_SPMV_SELL || S->kind == HZ_SPMV_SELL_FF;
-        launch_spmv<V>(sell ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR, S->group, mat_view<V>(A), x, e, S->red,
+        launch_spmv<V>(d64_kind(S->kind), S->group, mat_view<V>(A), x, e, S->red,
                        S->grid_spmv_cv, cs);
     }
 }
@@ -480,6 +479,7 @@ static hz_status bl_build_graph(BlSolver *S, const hz_mat *A, cudaGraph_t g) {
     }
     k_bl_gram<V><<<S->grid_gram, kVecBlock, 0, cs>>>(n, ell, st, R, S->red, S->ex);
     k_bl_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, ell, st, S->dctl, x, R, U, rh, S->ex, S->red, h);
+    k_loop_guard<typename Ar<V>::St><<<1, 1, 0, cs>>>(st, S->dctl, 1, h);
     HZ_CUDA(cudaStreamEndCapture(cs, &body));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, &wn, nullptr, 1, mode));
     EpiTrue<V> et;
@@ -506,7 +506,7 @@ __global__ void k_row_abs_max(int n, const int *__restrict__ rowptr, const doubl
 // two that brings the operator to unit scale, so that the vectors r_j = A^j r_0
 // of an outer iteration and their Gram products stay inside the exponent
 // range of binary32 on the double-float path
-static hz_status operator_scale(const hz_mat *A, double *out) {
+hz_status operator_scale(const hz_mat *A, double *out) {
     DevInfo d;
     HZ_TRY(dev_info(&d));
     unsigned long long *dm = nullptr, hm = 0;
@@ -542,8 +542,7 @@ static hz_status bl_get_solver(hz_mat *A, int ell, BlSolver **out) {
     S->kind = A->spmv_kind;
     S->group = A->group;
     S->grid_spmv = spmv_grid(A, S->kind, S->group);
-    const bool sell = S->kind == HZ_SPMV_SELL || S->kind == HZ_SPMV_SELL_FF;
-    S->grid_spmv_cv = spmv_grid(A, sell ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR, S->group);
+    S->grid_spmv_cv = spmv_grid(A, d64_kind(S->kind), S->group);
     S->grid_vec = stream_grid(d, (A->n + kVecUnroll - 1) / kVecUnroll, kVecBlock, 8);
     const int np = ell + ell * (ell + 1) / 2;
     S->grid_gram = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)2 * d.num_sms,

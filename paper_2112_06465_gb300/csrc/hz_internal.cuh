@@ -197,6 +197,12 @@ __device__ __forceinline__ double widen_d(float f) {
     return (double)f;
 }
 
+// binary exponents of the values for which split_d keeps all 48 bits
+// (both parts normal binary32 numbers, no overflow of the products with an
+// O(1) vector)
+constexpr int kFFMinExp = -100;
+constexpr int kFFMaxExp = 100;
+
 __device__ __forceinline__ float4 split_ff(double2 d) {
     float4 r;
     split_d(d.x, r.x, r.y);
@@ -497,6 +503,7 @@ struct hz_mat {
     // handle's x scratch for hz_zspmv on that path
     float4 *val_ff = nullptr;
     float4 *x_ff = nullptr;
+    bool ff_range_ok = false;   // every value lies where the split keeps 48 bits
     // row blocks of the block-flat double-float kernel (complete rows)
     int32_t nfblk = 0;
     int32_t *fblk = nullptr;

@@ -32,7 +32,38 @@ struct Ctl {
     const double2 *pre_d;      // Jacobi: y0 = D x0 (null without a preconditioner)
     const double2 *pre_dinv;   // Jacobi: x = D^-1 y
     double op_scale;           // s = 2^-k: the iteration runs on s A (x0 -> x0 / s, x -> s y); 1 = unscaled
+    // largest |Re b_i|, |Im b_i| as the bits of a non-negative double, written
+    // on the device by k_bmax (0: no scaling).  With it the iteration solves
+    // (s A) y = c b for c = 2^-e, 2^(e-1) <= max |b| < 2^e, so that the
+    // right-hand side and the residuals are O(1) whatever the size of b.
+    unsigned long long bmax_bits;
 };
+
+// c of the right-hand-side scaling above (a power of two: exact in binary64)
+__device__ __forceinline__ double rhs_scale(const Ctl *c) {
+    const double m = __longlong_as_double((long long)c->bmax_bits);
+    if (!(m > 0.0) || !isfinite(m)) return 1.0;
+    int e;
+    frexp(m, &e);
+    return ldexp(1.0, -e);
+}
+
+__device__ __forceinline__ double2 zscale(double2 a, double c) { return make_double2(a.x * c, a.y * c); }
+
+// the largest |Re b_i|, |Im b_i| into ctl->bmax_bits (zero on entry);
+// non-negative doubles order like their bit patterns read as unsigned
+static __global__ void __launch_bounds__(256) k_bmax(int n, Ctl *ctl) {
+    double m = 0.0;
+    const double2 *b = ctl->b;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double2 v = b[i];
+        m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0 && m > 0.0)
+        atomicMax(&ctl->bmax_bits, (unsigned long long)__double_as_longlong(m));
+}
 
 template <class St>
 struct BiState {
@@ -43,13 +74,19 @@ struct BiState {
     float tol32;     // inner tolerance (mixed)
     int maxit;       // inner iteration cap (mixed)
     int iter, done, half, status;
+    int guard;       // loop-body runs since the loop began (k_loop_guard; 0 between loops)
 };
 
 template <class V> using StateOf = BiState<typename Ar<V>::St>;
 
 struct OuterState {   // mixed-precision refinement state
     double nb, rel;
+    double rel_best;  // smallest outer residual ratio so far (its iterate is in the best-x vector)
     int outer, done, status, zero_x;
+    int save;         // 1: the current x is the best so far; keep a copy before x += d
+    int use_best;     // 1: the answer is the kept copy, not the current x
+    int guard;        // outer-loop body runs (k_outer_guard; 0 between solves)
+    int pad;
 };
 
 struct Info {
@@ -101,6 +138,26 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, unsigned 
     if (h) cudaGraphSetConditional(h, v);
 }
 
+// Last node of every solver loop body.  The WHILE condition a kernel of the
+// body set is replaced by one that also holds the loop to its caps: the loop
+// goes on only while the state is not done, the iteration count is below its
+// cap and the body has run at most cap times since the loop began (a body
+// that stopped advancing the count still ends).  A loop the guard ends is
+// marked done and NOT_CONVERGED.  cap = ctl->maxit for a solver's own loop
+// (outer_level), the inner iteration cap for the mixed method's inner loop.
+template <class St>
+__global__ void k_loop_guard(BiState<St> *st, const Ctl *ctl, int outer_level, cudaGraphConditionalHandle h) {
+    const int cap = outer_level ? ctl->maxit : st->maxit;
+    const int runs = st->guard + 1;
+    const bool go = !st->done && st->iter < cap && runs <= cap;
+    if (!go && !st->done) {
+        st->status = HZ_NOT_CONVERGED;
+        st->done = 1;
+    }
+    st->guard = go ? runs : 0;
+    set_cond(h, go ? 1u : 0u);
+}
+
 template <class V, int NV>
 __device__ __forceinline__ bool vec_reduce(typename Ar<V>::Acc (&acc)[NV], RedScratch red,
                                            typename Ar<V>::R (&tot)[NV]) {
@@ -125,7 +182,7 @@ __global__ void __launch_bounds__(kVecBlock) k_init_x(int n, const Ctl *ctl, V *
     if (ctl->restart) return;
     const double2 *x0 = ctl->x, *pd = ctl->pre_d;
     const bool zero = ctl->x0_zero != 0;
-    const double inv_s = 1.0 / ctl->op_scale;   // a power of two: exact
+    const double inv_s = rhs_scale(ctl) / ctl->op_scale;   // powers of two: exact
     vec_tiles(n, [&](int i) {
         const double2 v = pd ? cmul(x0[i], pd[i]) : x0[i];
         xw[i] = zero ? Ar<V>::zero() : Ar<V>::from_c128(make_double2(v.x * inv_s, v.y * inv_s));
@@ -143,7 +200,8 @@ struct EpiTrue : EpiBase<V> {
     const Ctl *ctl;
     __device__ bool skip() const { return false; }
     template <int N> __device__ void row(int i, V y, Acc (&acc)[N]) const {
-        Ar<V>::nrm2(acc[0], Ar<V>::sub(Ar<V>::from_c128(ctl->b[i]), Ar<V>::pow2(y, ctl->op_scale)));
+        const V bi = Ar<V>::from_c128(zscale(ctl->b[i], rhs_scale(ctl)));
+        Ar<V>::nrm2(acc[0], Ar<V>::sub(bi, Ar<V>::pow2(y, ctl->op_scale)));
     }
     template <int N> __device__ void finish(R (&tot)[N]) const {
         info->iters = st->iter;
@@ -162,7 +220,7 @@ __global__ void __launch_bounds__(kVecBlock) k_copy_out(int n, const Ctl *ctl, I
     const bool zero = info->zero_x != 0;
     // an expired bounded wait in an SpMV of this solve voids the result
     if (fault && blockIdx.x == 0 && threadIdx.x == 0 && *(volatile const int *)fault) info->status = HZ_ERR_TIMEOUT;
-    const double s = ctl->op_scale;
+    const double s = ctl->op_scale / rhs_scale(ctl);   // powers of two: exact
     vec_tiles(n, [&](int i) {
         const double2 y0 = Ar<V>::to_c128(xw[i]);
         const double2 y = make_double2(y0.x * s, y0.y * s);
@@ -191,6 +249,11 @@ static inline hz_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode
     *body = cp.conditional.phGraph_out[0];
     return HZ_OK;
 }
+
+// 2^-k with 2^(k-1) <= ||A||_inf < 2^k (1 for a zero matrix): the power of
+// two that brings an operator to unit scale for the double-float path
+// (bicgstabl.cu; synchronises the device)
+hz_status operator_scale(const hz_mat *A, double *out);
 
 // BiCGStab(l) (bicgstabl.cu): one solve on `op` with controls c, 1 <= l <= 8
 hz_status bl_solve(hz_mat *op, int ell, const Ctl &c, Info *out, int *restarts, cudaStream_t s);

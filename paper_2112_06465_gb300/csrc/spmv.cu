@@ -2,6 +2,7 @@
 // and optional timing-based autotuning), SELL-C-sigma construction and the
 // hz_zspmv / hz_cspmv entry points.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <numeric>
 #include <vector>
@@ -32,6 +33,35 @@ __global__ void k_sell_gather(int64_t slots, const int *__restrict__ src, const 
         sval[i] = v;
         if (sval32) sval32[i] = to_c64(v);
         if (svff) svff[i] = split_ff(v);
+    }
+}
+
+// smallest and largest binary exponent (IEEE field minus bias) over the
+// nonzero real and imaginary parts of the values: out[0] = min, out[1] = max
+// (out[0] = INT_MAX, out[1] = INT_MIN on entry); a non-finite part counts as
+// exponent 1024
+__global__ void k_exp_range(int64_t n, const double2 *__restrict__ val, int *out) {
+    int lo = INT32_MAX, hi = INT32_MIN;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = val[i];
+        const double c[2] = {v.x, v.y};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const unsigned hw = (unsigned)__double2hiint(c[q]), lw = (unsigned)__double2loint(c[q]);
+            if (((hw & 0x7fffffffu) | lw) == 0u) continue;   // a zero splits exactly
+            const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
+            lo = min(lo, e);
+            hi = max(hi, e);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(out, lo);
+        atomicMax(out + 1, hi);
     }
 }
 
@@ -71,17 +101,19 @@ MatView<float2> mat_view<float2>(const hz_mat *A) {
 int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap) {
     DevInfo d;
     if (dev_info(&d) != HZ_OK) return 1;
-    if (kind == HZ_SPMV_FF_FLAT || kind == HZ_SPMV_FF_TMA) {
+    if (kind == HZ_SPMV_FF_FLAT || kind == HZ_SPMV_FF_TMA || kind == HZ_SPMV_FLAT64) {
         // persistent: exactly the CTAs that fit at once (blocks are taken
         // grid-stride, so CTAs beyond one wave would only add a tail)
-        static int occ_flat = 0, occ_tma = 0;
-        int &occ = kind == HZ_SPMV_FF_TMA ? occ_tma : occ_flat;
+        static int occ_flat = 0, occ_tma = 0, occ_d64 = 0;
+        int &occ = kind == HZ_SPMV_FF_TMA ? occ_tma : kind == HZ_SPMV_FLAT64 ? occ_d64 : occ_flat;
         if (occ == 0) {
             cudaError_t e;
             if (kind == HZ_SPMV_FF_TMA) {
                 cudaFuncSetAttribute(k_spmv_fft<EpiStore<double2>>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      cudaSharedmemCarveoutMaxShared);
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_fft<EpiStore<double2>>, kFlatThreads, 0);
+            } else if (kind == HZ_SPMV_FLAT64) {
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_d64b<EpiStore<double2>>, kFlatThreads, 0);
             } else {
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_ffb<EpiStore<double2>>, kFlatThreads, 0);
             }
@@ -220,7 +252,8 @@ static hz_status autotune(hz_mat *A, cudaStream_t s) {
     if (A->val_ff)
         for (int w : {2, 4, 8, 16, 32}) cand.push_back({HZ_SPMV_FF, w});
     if (A->sell_vff) cand.push_back({HZ_SPMV_SELL_FF, 0});
-    if (A->fblk) cand.push_back({HZ_SPMV_FF_FLAT, 0});
+    if (A->fblk) cand.push_back({HZ_SPMV_FLAT64, 0});
+    if (A->val_ff && A->fblk) cand.push_back({HZ_SPMV_FF_FLAT, 0});
     if (A->col_pad) cand.push_back({HZ_SPMV_FF_TMA, 0});
     float best = 1e30f;
     MatView<double2> V = mat_view<double2>(A);
@@ -337,7 +370,33 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
     A->min_row = mn;
     A->mean_row = n ? (double)nnz / n : 0.0;
     A->group = pick_group(A->mean_row);
-    A->spmv_kind = HZ_SPMV_CSR_VECTOR;
+    // row blocks for the block-flat kernels: greedy runs of at most
+    // kFlatRows complete rows with at most `cap` entries; a longer row is
+    // a block of its own
+    // (and, for dev_k, the first entry of every block boundary row)
+    auto row_blocks = [&](int cap, int32_t **dev, int32_t *count, int32_t **dev_k) {
+        std::vector<int> fb{0};
+        for (int r = 0; r < n;) {
+            int r1 = r + 1;
+            while (r1 < n && r1 - r < kFlatRows && rp[r1 + 1] - rp[r] <= cap) ++r1;
+            fb.push_back(r1);
+            r = r1;
+        }
+        *count = (int32_t)fb.size() - 1;
+        if (cudaMalloc(dev, sizeof(int) * fb.size()) != cudaSuccess ||
+            cudaMemcpy(*dev, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return false;
+        if (!dev_k) return true;
+        std::vector<int> fk(fb.size());
+        for (size_t b = 0; b < fb.size(); ++b) fk[b] = rp[fb[b]];
+        return cudaMalloc(dev_k, sizeof(int) * fk.size()) == cudaSuccess &&
+               cudaMemcpy(*dev_k, fk.data(), sizeof(int) * fk.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    if (!row_blocks(kFlatCap, &A->fblk, &A->nfblk, &A->fblk_k)) {
+        set_error("hz_csr_create: allocation failed");
+        return fail(HZ_ERR_ALLOC);
+    }
+    A->spmv_kind = HZ_SPMV_FLAT64;
     hz_status st;
     if (flags & HZ_FLAG_SELL) {
         if ((st = build_sell(A, s, rp, cl, 1024)) != HZ_OK) return fail(st);
@@ -364,30 +423,7 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
                 return fail(HZ_ERR_ALLOC);
             }
         }
-        // row blocks for the block-flat kernels: greedy runs of at most
-        // kFlatRows complete rows with at most `cap` entries; a longer row is
-        // a block of its own
-        // (and, for dev_k, the first entry of every block boundary row)
-        auto row_blocks = [&](int cap, int32_t **dev, int32_t *count, int32_t **dev_k) {
-            std::vector<int> fb{0};
-            for (int r = 0; r < n;) {
-                int r1 = r + 1;
-                while (r1 < n && r1 - r < kFlatRows && rp[r1 + 1] - rp[r] <= cap) ++r1;
-                fb.push_back(r1);
-                r = r1;
-            }
-            *count = (int32_t)fb.size() - 1;
-            if (cudaMalloc(dev, sizeof(int) * fb.size()) != cudaSuccess ||
-                cudaMemcpy(*dev, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-                return false;
-            if (!dev_k) return true;
-            std::vector<int> fk(fb.size());
-            for (size_t b = 0; b < fb.size(); ++b) fk[b] = rp[fb[b]];
-            return cudaMalloc(dev_k, sizeof(int) * fk.size()) == cudaSuccess &&
-                   cudaMemcpy(*dev_k, fk.data(), sizeof(int) * fk.size(), cudaMemcpyHostToDevice) == cudaSuccess;
-        };
-        if (!row_blocks(kFlatCap, &A->fblk, &A->nfblk, &A->fblk_k) ||
-            !row_blocks(kTmaCap, &A->fblk_t, &A->nfblk_t, nullptr)) {
+        if (!row_blocks(kTmaCap, &A->fblk_t, &A->nfblk_t, nullptr)) {
             set_error("hz_csr_create: allocation failed");
             return fail(HZ_ERR_ALLOC);
         }
@@ -401,7 +437,30 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
         if (nnz) cudaMemcpyAsync(A->col_pad, A->col, sizeof(int) * nnz, cudaMemcpyDeviceToDevice, s);
         cudaMemsetAsync(A->col_pad + nnz, 0, sizeof(int) * 8, s);
         cudaMemsetAsync(A->fault, 0, sizeof(int), s);
-        A->spmv_kind = HZ_SPMV_FF_FLAT;
+        // the double-float split keeps 48 bits only while every value lies in
+        // [2^-100, 2^100] (both parts normal binary32 numbers); a matrix with
+        // values outside that range keeps the binary64 kind
+        bool in_range = true;
+        if (nnz) {
+            int *d_er = nullptr, h_er[2] = {INT32_MAX, INT32_MIN};
+            DevInfo di;
+            if (dev_info(&di) != HZ_OK || cudaMalloc(&d_er, 2 * sizeof(int)) != cudaSuccess) {
+                set_error("hz_csr_create: allocation failed");
+                return fail(HZ_ERR_ALLOC);
+            }
+            cudaMemcpyAsync(d_er, h_er, 2 * sizeof(int), cudaMemcpyHostToDevice, s);
+            k_exp_range<<<stream_grid(di, nnz, 256, 8), 256, 0, s>>>(nnz, A->val, d_er);
+            const cudaError_t e1 = cudaMemcpyAsync(h_er, d_er, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+            const cudaError_t e2 = cudaStreamSynchronize(s);
+            cudaFree(d_er);
+            if (e1 != cudaSuccess || e2 != cudaSuccess) {
+                set_error("hz_csr_create: value range check failed");
+                return fail(HZ_ERR_CUDA);
+            }
+            in_range = h_er[0] >= kFFMinExp && h_er[1] <= kFFMaxExp;
+        }
+        A->ff_range_ok = in_range;
+        A->spmv_kind = in_range ? HZ_SPMV_FF_FLAT : HZ_SPMV_FLAT64;
     }
     if ((st = refresh(A, s)) != HZ_OK) return fail(st);
     if (flags & HZ_FLAG_AUTOTUNE) {
@@ -508,8 +567,8 @@ extern "C" HZ_API hz_status hz_cspmv(hz_mat *A, const hz_c *d_x, hz_c *d_y, void
     HZ_CHECK(d_x && d_y, "hz_cspmv: null vector");
     HZ_CHECK((const void *)d_x != (const void *)d_y, "hz_cspmv: x and y must not alias");
     HZ_TRY(ensure_c64(A, (cudaStream_t)stream));
-    if (A->fblk && (A->spmv_kind == HZ_SPMV_FF_FLAT || A->spmv_kind == HZ_SPMV_FF_TMA)) {
-        // the row blocks exist: the block-flat complex64 kernel
+    if (A->fblk && d64_kind(A->spmv_kind) == HZ_SPMV_FLAT64) {
+        // the block-flat kinds: the block-flat complex64 kernel
         EpiStore<float2> epi{(float2 *)d_y};
         HZ_CUDA(launch_k(false, k_spmv_c64b<EpiStore<float2>>, c64_flat_grid(A), kFlatThreads, (cudaStream_t)stream,
                          mat_view<float2>(A), (const float2 *)d_x, epi, RedScratch{}));
@@ -531,8 +590,12 @@ extern "C" HZ_API hz_status hz_mat_set_spmv(hz_mat *A, int32_t kind, int32_t gro
         A->spmv_kind = HZ_SPMV_SELL;
         return HZ_OK;
     }
+    if (kind == HZ_SPMV_FLAT64) {
+        A->spmv_kind = kind;
+        return HZ_OK;
+    }
     if (kind == HZ_SPMV_FF_FLAT || kind == HZ_SPMV_FF_TMA) {
-        HZ_CHECK(A->fblk != nullptr, "hz_mat_set_spmv: the handle has no double-float copy (HZ_FLAG_FF)");
+        HZ_CHECK(A->val_ff != nullptr, "hz_mat_set_spmv: the handle has no double-float copy (HZ_FLAG_FF)");
         A->spmv_kind = kind;
         return HZ_OK;
     }

@@ -695,6 +695,141 @@ __device__ __forceinline__ void flat_rows_ff_tma(const MatView<double2> &A, cons
     }
 }
 
+// ---------------------------------------------------------------------------
+// Block-flat binary64 core with contiguous lane runs (HZ_SPMV_FLAT64).
+//
+// On GB300 the binary64 pipe retires about 1.7 lanes per SM per clock, and a
+// warp instruction occupies it for the same time whether 32 lanes or one are
+// active, so a binary64 SpMV is bound by the number of binary64 warp
+// instructions, not by the number of multiply-adds.  A group of lanes per
+// row leaves lanes idle at every row end and folds partial sums with extra
+// additions; here every lane of a warp runs one contiguous stretch of
+// ceil(nnz_block / 32) entries of its row block and accumulates it with four
+// FMAs per entry (the minimum for a complex multiply-accumulate), switching
+// rows inside its stretch as the row pointers say.  A row that crosses the
+// boundary between two lanes' stretches is finished in phase 2 from the
+// lanes' partial sums: the tail of the lane where it starts, the whole
+// stretch of every lane in between and the head of the lane where it ends,
+// added in that order (storage order of the entries).  Row blocks are those
+// of the block-flat double-float kernel (<= 32 complete rows and <= 512
+// entries, or one longer row), so phase 2 is one row per lane.
+struct alignas(16) D64Seg {
+    double2 head[32];   // lane l: its first run when that run's row began in an earlier lane
+    double2 tail[32];   // lane l: its last run when that run's row continues in a later lane
+    double2 full[32];   // rows that lie inside one lane's stretch, by row offset
+    int rp[33];         // row pointers of the block's rows (rp[nr] = end of the block)
+};
+#ifndef HZ_D64_GROUP
+#define HZ_D64_GROUP 8
+#endif
+constexpr int kD64Group = HZ_D64_GROUP;   // entries per lane whose loads are in flight together
+#ifndef HZ_D64_MIN_BLOCKS
+#define HZ_D64_MIN_BLOCKS 4
+#endif
+constexpr int kD64MinBlocks = HZ_D64_MIN_BLOCKS;   // resident CTAs per SM asked of the register allocator
+
+__device__ __forceinline__ double2 ld_stream_l1(const double2 *ptr, uint64_t pol) {
+    double2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int ld_stream_l1(const int *ptr, uint64_t pol) {
+    int v;
+    asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+
+template <class Epi, int NV>
+__device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const double2 *__restrict__ x,
+                                              const Epi &epi, typename Epi::Acc (&acc)[NV], D64Seg *sg) {
+    const uint64_t pol = pol_evict_first();
+    const int lane = threadIdx.x & 31;
+    const int step = gridDim.x * (blockDim.x >> 5);
+    for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < A.nfblk; b += step) {
+        const int r0 = __ldg(A.fblk + b), r1 = __ldg(A.fblk + b + 1);
+        const int kb = __ldg(A.fblk_k + b), ke = __ldg(A.fblk_k + b + 1);
+        const int nr = r1 - r0;
+        typename PreOf<Epi>::T pf{};
+        if (lane < nr) {
+            sg->rp[lane] = __ldg(A.rowptr + r0 + lane);
+            pf = epi_pre(epi, r0 + lane);
+        }
+        if (lane == 0) sg->rp[nr] = ke;
+        __syncwarp();
+        // this lane's stretch [c0, c1) of the block's entries [kb, ke)
+        const int U = (ke - kb + 31) >> 5;
+        const int c0 = min(ke, kb + lane * U), c1 = min(ke, c0 + U);
+        // the row holding c0: the last j < nr with rp[j] <= c0 (rows without
+        // entries before it are skipped, since their rp equals the next one's)
+        int j = 0;
+        if (c0 < c1) {
+            int hi = nr - 1;
+            while (j < hi) {
+                const int mid = (j + hi + 1) >> 1;
+                if (sg->rp[mid] <= c0) j = mid;
+                else hi = mid - 1;
+            }
+        }
+        int nxt = sg->rp[j + 1];   // first entry of the next row (> c0)
+        int seg0 = c0;             // first entry of the current run
+        double2 s = make_double2(0.0, 0.0);
+        // a finished run [beg, end) of row jj: a head, a tail, or a whole row
+        auto flush = [&](int jj, int beg, int end) {
+            if (beg == end) return;
+            if (beg == c0 && sg->rp[jj] < c0) sg->head[lane] = s;
+            else if (end == c1 && sg->rp[jj + 1] > c1) sg->tail[lane] = s;
+            else sg->full[jj] = s;
+        };
+#pragma unroll 1
+        for (int k0 = c0; k0 < c0 + U; k0 += kD64Group) {
+            int c[kD64Group];
+            double2 a[kD64Group], v[kD64Group];
+#pragma unroll
+            for (int u = 0; u < kD64Group; ++u) {
+                const int k = k0 + u;
+                c[u] = k < c1 ? ld_stream_l1(A.col + k, pol) : -1;
+                a[u] = k < c1 ? ld_stream_l1(A.val + k, pol) : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < kD64Group; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_double2(0.0, 0.0);
+#pragma unroll
+            for (int u = 0; u < kD64Group; ++u) {
+                const int k = k0 + u;
+                if (k < c1) {
+                    while (k == nxt && j < nr - 1) {   // row j ends before entry k
+                        flush(j, seg0, k);
+                        ++j;
+                        nxt = sg->rp[j + 1];
+                        s = make_double2(0.0, 0.0);
+                        seg0 = k;
+                    }
+                    cmac(s, a[u], v[u]);
+                }
+            }
+        }
+        if (c0 < c1) flush(j, seg0, c1);
+        __syncwarp();
+        // phase 2: lane j finishes row r0 + j
+        if (lane < nr) {
+            const int rb = sg->rp[lane], re = sg->rp[lane + 1];
+            double2 y = make_double2(0.0, 0.0);
+            if (re > rb) {
+                // (clamped: with monotone row pointers both are in 0..31 already)
+                const int la = min(31, max(0, (rb - kb) / U)), lb = min(31, max(la, (re - 1 - kb) / U));
+                if (la == lb) {
+                    y = sg->full[lane];
+                } else {
+                    y = sg->tail[la];
+                    for (int l = la + 1; l < lb; ++l) y = cadd(y, sg->head[l]);
+                    y = cadd(y, sg->head[lb]);
+                }
+            }
+            epi_row(epi, r0 + lane, y, acc, pf);
+        }
+        __syncwarp();
+    }
+}
+
 // per-thread accumulators -> one grid total -> epi.finish (last block)
 template <class Epi, int NV>
 __device__ __forceinline__ void spmv_reduce(const Epi &epi, typename Epi::Acc (&acc)[NV], RedScratch red) {
@@ -703,6 +838,26 @@ __device__ __forceinline__ void spmv_reduce(const Epi &epi, typename Epi::Acc (&
     if (grid_reduce_acc(acc, red, tot, [](const typename Epi::Acc &a) { return Epi::total(a); })) {
         if (threadIdx.x == 0) epi.finish(tot);
     }
+}
+
+// the block-flat binary64 kernel (kFlatThreads threads, row blocks, contiguous lane runs)
+template <class Epi>
+__global__ void __launch_bounds__(kFlatThreads, kD64MinBlocks) k_spmv_d64b(MatView<double2> A,
+                                                                            const double2 *__restrict__ x, Epi epi,
+                                                                            RedScratch red) {
+    __shared__ D64Seg seg[kFlatThreads / 32];
+    constexpr int NV = Epi::NV > 0 ? Epi::NV : 1;
+    pdl_wait();
+    pdl_release();
+    if (epi.skip()) {   // grid-uniform early exit; one thread reports it to the epilogue
+        if (blockIdx.x == 0 && threadIdx.x == 0) epi.on_skip();
+        return;
+    }
+    typename Epi::Acc acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
+    flat_rows_d64<Epi, NV>(A, x, epi, acc, &seg[threadIdx.x >> 5]);
+    if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
 }
 
 template <int W, class T, class Epi>
@@ -956,6 +1111,12 @@ cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, cudaS
 template <class T, class Epi>
 cudaError_t launch_spmv(int kind, int group, const MatView<T> &A, const T *x, const Epi &epi,
                         RedScratch red, int grid, cudaStream_t s, bool pdl = false) {
+    if constexpr (std::is_same<T, double2>::value) {
+        if (kind == HZ_SPMV_FLAT64) {
+            launch_k(pdl, k_spmv_d64b<Epi>, grid, kFlatThreads, s, A, x, epi, red);
+            return cudaGetLastError();
+        }
+    }
     if (kind == HZ_SPMV_SELL) {
         launch_k(pdl, k_spmv<0, T, Epi>, grid, kSpmvBlock, s, A, x, epi, red);
     } else {
@@ -1004,8 +1165,19 @@ cudaError_t launch_spmv_ff(int kind, int group, const MatView<double2> &A, const
 }
 
 // grid for a fused SpMV: enough blocks to cover the rows once, capped at a
-// whole number of waves over the SMs (the row loop is grid-stride).
+// whole number of waves over the SMs (the row loop is grid-stride); the
+// block-flat kinds get exactly the CTAs that fit at once.
 int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap = 8);
+
+// the binary64 (and complex64) kernel family that stands for a handle's
+// kind when a solver runs in binary64: the SELL kinds -> HZ_SPMV_SELL, the
+// CSR-vector kinds -> HZ_SPMV_CSR_VECTOR, the block-flat kinds ->
+// HZ_SPMV_FLAT64 (the row blocks exist for every handle)
+inline int d64_kind(int kind) {
+    if (kind == HZ_SPMV_SELL || kind == HZ_SPMV_SELL_FF) return HZ_SPMV_SELL;
+    if (kind == HZ_SPMV_CSR_VECTOR || kind == HZ_SPMV_FF) return HZ_SPMV_CSR_VECTOR;
+    return HZ_SPMV_FLAT64;
+}
 
 template <class T>
 MatView<T> mat_view(const hz_mat *A);

@@ -303,8 +303,7 @@ static void tq_spmv(const TqSolver *S, const hz_mat *A, const V *x, const Epi &e
     if constexpr (std::is_same<V, float4>::value) {
         launch_spmv_ff(S->kind, S->group, mat_view<double2>(A), x, e, S->red, S->grid_spmv, cs);
     } else {
-        const bool sell = S->kind == HZ_SPMV_SELL || S->kind == HZ_SPMV_SELL_FF;
-        launch_spmv<V>(sell ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR, S->group, mat_view<V>(A), x, e, S->red,
+        launch_spmv<V>(d64_kind(S->kind), S->group, mat_view<V>(A), x, e, S->red,
                        S->grid_spmv_cv, cs);
     }
 }
@@ -343,6 +342,7 @@ static hz_status tq_build_graph(TqSolver *S, const hz_mat *A, cudaGraph_t g) {
     tq_spmv<V>(S, A, u2, ew, cs);
     k_tq_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->q, d, x, u2, u1, w, au, v, h);
     tq_spmv<V>(S, A, u1, ev, cs);
+    k_loop_guard<typename Ar<V>::St><<<1, 1, 0, cs>>>(st, S->dctl, 1, h);
     HZ_CUDA(cudaStreamEndCapture(cs, &body));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, &wn, nullptr, 1, mode));
     EpiTrue<V> et;
@@ -371,8 +371,7 @@ static hz_status tq_get_solver(hz_mat *A, TqSolver **out) {
     S->kind = A->spmv_kind;
     S->group = A->group;
     S->grid_spmv = spmv_grid(A, S->kind, S->group);
-    const bool sell = S->kind == HZ_SPMV_SELL || S->kind == HZ_SPMV_SELL_FF;
-    S->grid_spmv_cv = spmv_grid(A, sell ? HZ_SPMV_SELL : HZ_SPMV_CSR_VECTOR, S->group);
+    S->grid_spmv_cv = spmv_grid(A, d64_kind(S->kind), S->group);
     S->grid_vec = stream_grid(dv, (A->n + kVecUnroll - 1) / kVecUnroll, kVecBlock, 8);
     const size_t nb = (size_t)A->n * 16;
     void **vecs[] = {&S->x, &S->w, &S->u1, &S->u2, &S->v, &S->d, &S->au1, &S->au, &S->rh};

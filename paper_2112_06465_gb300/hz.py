@@ -80,10 +80,11 @@ class Matrix:
         return {f: getattr(p, f) for f, _ in p._fields_}
 
     def set_spmv(self, kind="csr", group=4):
-        """Force the SpMV variant: ("csr" | "ff", lanes per row) or ("sell" | "sellff" |
-        "ffflat" | "fftma", ignored)."""
+        """Force the SpMV variant: ("csr" | "ff", lanes per row) or ("flat64" | "sell" |
+        "sellff" | "ffflat" | "fftma", ignored)."""
         k = {"sell": _lib.HZ_SPMV_SELL, "ff": _lib.HZ_SPMV_FF, "sellff": _lib.HZ_SPMV_SELL_FF,
-             "ffflat": _lib.HZ_SPMV_FF_FLAT, "fftma": _lib.HZ_SPMV_FF_TMA}.get(kind, _lib.HZ_SPMV_CSR_VECTOR)
+             "ffflat": _lib.HZ_SPMV_FF_FLAT, "fftma": _lib.HZ_SPMV_FF_TMA,
+             "flat64": _lib.HZ_SPMV_FLAT64}.get(kind, _lib.HZ_SPMV_CSR_VECTOR)
         check(_L.hz_mat_set_spmv(self.handle, k, int(group)))
 
     def check(self):
@@ -232,10 +233,12 @@ def _info(i: hz_info) -> SolveInfo:
 
 
 def zsolve(A: Matrix, b, x=None, tol=1e-10, maxit=2000, mode="fp64", hist=None,
-           inner_tol=1e-5, inner_maxit=1000, max_outer=50, precond="none", method="bicgstab", ell=4):
+           inner_tol=1e-5, inner_maxit=1000, max_outer=50, precond="none", method="bicgstab", ell=4,
+           x0_zero=None):
     """Solve A x = b with BiCGStab on the device; returns (x, SolveInfo).
 
-    x (optional) holds x0 and receives the solution; mode is "fp64" or
+    x (optional) holds x0 and receives the solution (x0_zero=True: start
+    from x0 = 0 whatever x holds; the default is x0 = 0 only without x); mode is "fp64" or
     "mixed"; precond is "none" or "jacobi" (right preconditioning by the
     inverse diagonal); method is "bicgstab", "bicgstabl" (BiCGStab(ell),
     iterations counted in BiCG steps) or "tfqmr" (stopping on the
@@ -248,7 +251,8 @@ def zsolve(A: Matrix, b, x=None, tol=1e-10, maxit=2000, mode="fp64", hist=None,
     if precond not in ("none", "jacobi"):
         raise ValueError("precond must be 'none' or 'jacobi'")
     b = _vec(b, name="b")
-    x0_zero = x is None
+    if x0_zero is None:
+        x0_zero = x is None
     if x is None:
         x = torch.empty_like(b)
     x = _vec(x, name="x")

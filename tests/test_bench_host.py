@@ -58,14 +58,14 @@ def test_recorded_traffic_only_for_the_measured_source(tmp_path, monkeypatch):
     root = _fake_root(tmp_path, "0" * 16)
     monkeypatch.setattr(bench, "ROOT", root)
     current = bench.kernel_source_sha()
-    assert bench.recorded_traffic() is None               # another kernel source
+    assert bench.recorded_traffic("spmv_ffb_c2_traffic.txt") is None               # another kernel source
     (tmp_path / "profiles" / "spmv_ffb_c2_traffic.txt").write_text(
         "dram_bytes_per_launch: 123456\nkernel_source_sha: %s\n" % current)
-    assert bench.recorded_traffic() == 123456.0
+    assert bench.recorded_traffic("spmv_ffb_c2_traffic.txt") == 123456.0
     with open(os.path.join(root, "paper_2112_06465_gb300", "csrc", "spmv.cu"), "a") as f:
         f.write("\n// edited\n")
     assert bench.kernel_source_sha() != current          # any edit invalidates it
-    assert bench.recorded_traffic() is None
+    assert bench.recorded_traffic("spmv_ffb_c2_traffic.txt") is None
 
 
 def test_peaks_fall_back_when_unmeasured(tmp_path, monkeypatch):

@@ -448,6 +448,32 @@ def test_cbicgstab_nonsymmetric_dense_lu(oracle):
     assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) <= 1e-5
 
 
+def test_mixed_refinement_returns_best_iterate(oracle):
+    """Refinement to a tolerance below binary64 rounding (1e-17) cannot
+    converge: once a step fails to reduce the outer residual the refinement
+    stops and returns the iterate with the smallest one.  The returned x has
+    exactly the reported residual (not the larger one of the last step) and
+    is the dense-LU solution to binary64 accuracy."""
+    A, b, _ = W.c1_small_fd()
+    S = A.to_scipy()
+    x, d = oracle.refine_mixed(A, b, tol=1e-17, max_outer=30)
+    assert d["status"] == 4 and 2 <= d["outer"] < 30
+    r = np.linalg.norm(b - S @ x) / np.linalg.norm(b)
+    assert abs(r - d["relres"]) <= 1e-6 * r and r < 1e-12
+    x_lu = np.linalg.solve(S.toarray(), b)
+    assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) <= 1e-10
+    # a right-hand side the inner solve cannot improve returns x0 = 0
+    rng = np.random.default_rng(63)
+    n = 40
+    Q1, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    D = Q1 @ np.diag(np.logspace(0, -8, n)) @ Q2.conj().T
+    Ad = W.CSR.from_scipy(sp.csr_matrix(D))
+    bd = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    xd, dd = oracle.refine_mixed(Ad, bd, tol=1e-12, max_outer=30)
+    assert dd["status"] == 4 and dd["relres"] == 1.0 and not xd.any()
+
+
 # --------------------------------------------------------------------------- adjoint
 def test_adjoint_oracle_gradient(oracle):
     """Oracle chain (solve, adjoint solve, outer product on the pattern) against

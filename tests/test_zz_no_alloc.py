@@ -2,9 +2,13 @@
 device memory (its scratch is a fixed array inside libhz.so).
 
 Called through the C ABI and compared with hz_zdotc, which allocates its own
-scratch, within the dot-product tolerance of the other GPU tests:
+scratch, and with the CPU oracle's compensated dot product, within the
+dot-product tolerance of the other GPU tests:
 |difference| <= 1e-13 * sum |x_i| |y_i|.  Two calls in a row check that the
-shared array left by one call does not disturb the next.  This file is
+shared array left by one call does not disturb the next.  The sizes cover
+one tile, a ragged tail, more tiles than a block has threads (the last
+block's fold then takes several partials per thread) and the largest
+accepted length, where x = y = 1 gives the exact sum 2^28.  This file is
 collected last so that a run stopping at the first failure has already run
 every other test; it also passes on its own in a fresh process.
 """
@@ -34,8 +38,8 @@ def _dot(lib, fn, x, y):
     return complex(out.cpu()[0])
 
 
-@pytest.mark.parametrize("n", [1, 4095, 4097, 1_000_003])
-def test_noalloc_matches_zdotc_twice(hz, n):
+@pytest.mark.parametrize("n", [1, 4095, 4097, 1_000_003, (1 << 21) + 1, (1 << 22) + 3])
+def test_noalloc_matches_zdotc_twice(hz, oracle, n):
     from paper_2112_06465_gb300 import _lib
     lib = _lib.load()
     for call in range(2):
@@ -45,6 +49,21 @@ def test_noalloc_matches_zdotc_twice(hz, n):
         got = _dot(lib, lib.hz_zdotc_noalloc, xd, yd)
         bound = TOL * float(np.sum(np.abs(x) * np.abs(y)))
         assert abs(got - ref) <= bound, (call, got, ref)
+        assert abs(got - oracle.zdotc(x, y)) <= bound, (call, got)
+
+
+def test_noalloc_at_capacity(hz):
+    """n = 2^28, the largest accepted length (65536 tiles), twice: with
+    x = y = 1 every partial and the total are exact, so the result is 2^28."""
+    from paper_2112_06465_gb300 import _lib
+    lib = _lib.load()
+    n = 1 << 28
+    x = torch.ones(n, dtype=torch.complex128, device="cuda")
+    for _ in range(2):
+        got = _dot(lib, lib.hz_zdotc_noalloc, x, x)
+        assert got == complex(n, 0.0)
+    del x
+    torch.cuda.empty_cache()
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(hz):

@@ -275,7 +275,9 @@ def compare_modes(hz, torch, full_c4, maxit):
     stream = torch.cuda.current_stream()
     mats, bs = [], []
     for name, A, b in systems:
-        M = hz.Matrix.from_csr(A, ff=True, c64=True)
+        # autotune: times the SpMV kinds and CSR-vector groups on this matrix;
+        # the batched solver's row tile per geometry is the group it keeps
+        M = hz.Matrix.from_csr(A, ff=True, c64=True, autotune=True)
         mats.append(M)
         bs.append(torch.as_tensor(b).to("cuda"))
 
@@ -288,27 +290,31 @@ def compare_modes(hz, torch, full_c4, maxit):
         return out, e0.elapsed_time(e1)
 
     variants = {
-        "fp64_binary64": ("csr", dict(mode="fp64")),
+        "fp64_binary64": ("flat64", dict(mode="fp64")),
+        "mixed": ("flat64", dict(mode="mixed")),
+        "bicgstab4_binary64": ("flat64", dict(method="bicgstabl", ell=4)),
+        "tfqmr_binary64": ("flat64", dict(method="tfqmr")),
         "fp64_double_float": ("ffflat", dict(mode="fp64")),
-        "mixed": ("csr", dict(mode="mixed")),
         "mixed_double_float": ("ffflat", dict(mode="mixed")),
         "fp64_double_float_jacobi": ("ffflat", dict(mode="fp64", precond="jacobi")),
         "bicgstab4_double_float": ("ffflat", dict(method="bicgstabl", ell=4)),
         "tfqmr_double_float": ("ffflat", dict(method="tfqmr")),
     }
     res = {k: [] for k in variants}
-    for M, b in zip(mats, bs):
+    groups = [M.props()["group"] for M in mats]
+    for M, b, g in zip(mats, bs, groups):
         for key, (kind, kw) in variants.items():
-            M.set_spmv(kind, M.props()["group"] if kind == "csr" else 0)
+            M.set_spmv(kind, g)
             hz.zsolve(M, b, tol=1e-10, maxit=maxit, **kw)          # graph capture
             (_, info), ms = timed(lambda: hz.zsolve(M, b, tol=1e-10, maxit=maxit, **kw))
             res[key].append((ms, info))
     batched = {}
-    for key, kind in (("batched_fp64", "csr"), ("batched_double_float", "ffflat")):
-        for M in mats:   # the batch runs double-float when every handle's kind is
-            M.set_spmv(kind, M.props()["group"] if kind == "csr" else 0)
-        hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit)
-        batched[key] = timed(lambda: hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit))
+    for key, kind, mode in (("batched_fp64", "flat64", "fp64"), ("batched_mixed", "flat64", "mixed"),
+                            ("batched_double_float", "ffflat", "fp64")):
+        for M, g in zip(mats, groups):   # the batch runs double-float when every handle's kind is;
+            M.set_spmv(kind, g)          # its row tile is each handle's autotuned group
+        hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit, mode=mode)
+        batched[key] = timed(lambda: hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit, mode=mode))
     binfos = batched["batched_fp64"][0][1]
     ok_all = [all(res[k][i][1].converged for k in variants) and binfos[i].converged
               for i in range(len(mats))]
@@ -321,6 +327,7 @@ def compare_modes(hz, torch, full_c4, maxit):
                 "max_relres_true": max(i.relres_true for _, i in rows)}
 
     out = {"systems": len(mats), "solved_by_all": sum(ok_all), "tol": 1e-10, "maxit": maxit,
+           "batch_row_tile_groups": groups,
            "workload": "C4 frequency sweep: FD boxes %s x 8 kh in [0.2, 0.8] + jittered P1 cylinders %s x 8 kh, "
                        "shift 0.05i" % (list(WC.C4_BOXES), [list(c) for c in cyl])}
     for key in variants:
@@ -334,7 +341,17 @@ def compare_modes(hz, torch, full_c4, maxit):
         k: base / max(out[k]["s_on_common"], 1e-12) for k in variants if k != "fp64_binary64"}
     out["speedup_vs_fp64_binary64_all_systems"] = {
         k: out["fp64_binary64"]["s_total"] / out[k]["s_total"]
-        for k in list(variants)[1:] + ["batched_fp64", "batched_double_float"]}
+        for k in list(variants)[1:] + ["batched_fp64", "batched_mixed", "batched_double_float"]}
+    # the systems that the binary64 solver and the mixed and batched solvers
+    # all solve: time to rel.res 1e-10 on exactly those
+    ok_mb = [res["fp64_binary64"][i][1].converged and res["mixed"][i][1].converged
+             and batched["batched_fp64"][0][1][i].converged and batched["batched_mixed"][0][1][i].converged
+             for i in range(len(mats))]
+    out["mixed_batched_vs_binary64_on_common"] = {
+        "systems": sum(ok_mb),
+        "s_binary64": sum(ms for (ms, _), ok in zip(res["fp64_binary64"], ok_mb) if ok) / 1e3,
+        "s_mixed": sum(ms for (ms, _), ok in zip(res["mixed"], ok_mb) if ok) / 1e3,
+        "note": "batched solvers run every system in one launch; their time is over all systems"}
     for M in mats:
         M.close()
     return out
@@ -439,30 +456,23 @@ def spmv_c64_c2(hz, torch, A, stream):
             "algorithmic_bytes_per_launch": nbytes, "achieved_gbs": gbs, "frac": gbs / peak}
 
 
-def adjoint_c5(hz, torch, stream, iters=300, reps=10):
-    """The adjoint step of the C5 inverse problem (64^3 FD, n = 262,144,
-    A(theta) = L - kappa^2 diag(theta)): the forward solve A x = b and the
-    adjoint solve A^T mu = conj(g) (g = the data misfit at the 512 sample
-    points) with the double-float solver for a fixed number of iterations
-    (the undamped 64^3 operator does not reach 1e-12 without a
-    preconditioner), then the two gradient kernels, each timed alone with
-    the L2 flushed (median of `reps`): the outer product on A's pattern
-    (16 nnz bytes written; 4 nnz + 4 (n + 1) of pattern and 32 n of mu and x
-    read) and the diagonal gradient (48 n)."""
+def adjoint_c5(hz, torch, stream, reps=10):
+    """The C5 inverse problem (A(theta) = L - kappa^2 diag(theta), kh = 0.5).
+
+    converged: the adjoint step on the largest grid where a Krylov forward
+    solve reaches 1e-12 (32^3, n = 32,768; TFQMR in binary64 for the forward
+    and the adjoint solve, through solve_diag_param and loss.backward()),
+    with the time of the forward and of the backward pass.
+    grid_64: the configured 64^3 grid (n = 262,144), where no method here
+    reaches 1e-12 (the forward solve stagnates): 300 binary64 TFQMR
+    iterations of the forward solve (time per iteration), then the two
+    gradient kernels, each timed alone with the L2 flushed (median of
+    `reps`): the outer product on A's pattern (16 nnz bytes written;
+    4 nnz + 4 (n + 1) of pattern and 32 n of mu and x read) and the diagonal
+    gradient (48 n)."""
     import numpy as np
     import statistics as st_
     import workloads as W
-    prob = W.c5_inverse_problem()
-    A = prob["A"]
-    n, nnz = A.n, A.nnz
-    M = hz.Matrix.from_csr(A, ff=True)
-    base = torch.as_tensor(prob["L"].to_scipy().diagonal().astype(np.complex128)).cuda()
-    theta = torch.as_tensor(prob["theta"].astype(np.complex128)).cuda()
-    b = torch.as_tensor(prob["b"]).cuda()
-    idx = torch.as_tensor(prob["sample_idx"]).cuda()
-    d = torch.as_tensor(prob["data"]).cuda()
-    scale = -prob["kappa2"]
-    flush = torch.empty(8 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def timed(fn):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -471,6 +481,42 @@ def adjoint_c5(hz, torch, stream, iters=300, reps=10):
         e1.record(stream)
         e1.synchronize()
         return out, e0.elapsed_time(e1)
+
+    # the converged adjoint step at 32^3
+    p32 = W.c5_inverse_problem(m=32, nsample=512)
+    M32 = hz.Matrix.from_csr(p32["A"])
+    base32 = torch.as_tensor(p32["L"].to_scipy().diagonal().astype(np.complex128)).cuda()
+    b32 = torch.as_tensor(p32["b"]).cuda()
+    idx32 = torch.as_tensor(p32["sample_idx"]).cuda()
+    d32 = torch.as_tensor(p32["data"]).cuda()
+
+    def step():
+        th = torch.as_tensor(p32["theta"].astype(np.complex128)).cuda().requires_grad_(True)
+        x = hz.solve_diag_param(th, b32, M32, base32, -p32["kappa2"], tol=1e-12, maxit=8000, method="tfqmr")
+        loss = torch.sum(torch.abs(x[idx32] - d32) ** 2)
+        return th, x, loss
+
+    th, x, loss = step()
+    loss.backward()                                           # graph capture
+    (th, x, loss), ms_fwd = timed(step)
+    _, ms_bwd = timed(lambda: loss.backward())
+    fwd_info = x.grad_fn.fwd_info if hasattr(x.grad_fn, "fwd_info") else None
+    conv = {"workload": "C5 inverse problem at 32^3 (n = 32,768), TFQMR binary64 to 1e-12",
+            "forward_ms": ms_fwd, "backward_ms": ms_bwd, "loss": float(loss),
+            "forward_iters": fwd_info.iters if fwd_info else None}
+    M32.close()
+
+    prob = W.c5_inverse_problem()
+    A = prob["A"]
+    n, nnz = A.n, A.nnz
+    M = hz.Matrix.from_csr(A)
+    base = torch.as_tensor(prob["L"].to_scipy().diagonal().astype(np.complex128)).cuda()
+    theta = torch.as_tensor(prob["theta"].astype(np.complex128)).cuda()
+    b = torch.as_tensor(prob["b"]).cuda()
+    idx = torch.as_tensor(prob["sample_idx"]).cuda()
+    d = torch.as_tensor(prob["data"]).cuda()
+    scale = -prob["kappa2"]
+    flush = torch.empty(8 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def cold(fn):
         fn()
@@ -485,13 +531,13 @@ def adjoint_c5(hz, torch, stream, iters=300, reps=10):
         torch.cuda.synchronize()
         return st_.median(a.elapsed_time(z) for a, z in ev)
 
+    iters = 300
     hz.mat_set_diag(M, base, scale, theta)
-    hz.zsolve(M, b, tol=1e-12, maxit=iters)                      # graph capture
-    (x, inf_f), ms_f = timed(lambda: hz.zsolve(M, b, tol=1e-12, maxit=iters))
+    hz.zsolve(M, b, tol=1e-12, maxit=iters, method="tfqmr")       # graph capture
+    (x, inf_f), ms_f = timed(lambda: hz.zsolve(M, b, tol=1e-12, maxit=iters, method="tfqmr"))
     g = torch.zeros_like(x)
     g[idx] = x[idx] - d
-    rhs = hz.zconj(g)
-    (mu, inf_a), ms_a = timed(lambda: hz.zsolve(M, rhs, tol=1e-12, maxit=iters))
+    mu = hz.zconj(g)
     gval = torch.empty(nnz, dtype=torch.complex128, device="cuda")
     gth = torch.empty_like(x)
     ms_outer = cold(lambda: hz.outer_on_pattern(M, mu, x, out=gval))
@@ -499,18 +545,18 @@ def adjoint_c5(hz, torch, stream, iters=300, reps=10):
     peak, _ = peaks()
     ob = 20 * nnz + 36 * n + 4
     M.close()
-    return {"workload": "C5 64^3 FD inverse problem, A(theta) = L - kappa^2 diag(theta), kh = 0.5",
-            "n": n, "nnz": nnz, "iters": iters,
-            "forward": {"ms": ms_f, "iters": inf_f.iters, "status": inf_f.status_name,
-                        "relres_true": inf_f.relres_true, "iter_us": 1e3 * ms_f / max(inf_f.iters, 1)},
-            "adjoint": {"ms": ms_a, "iters": inf_a.iters, "status": inf_a.status_name,
-                        "relres_true": inf_a.relres_true, "iter_us": 1e3 * ms_a / max(inf_a.iters, 1)},
-            "outer_on_pattern": {"us": 1e3 * ms_outer, "algorithmic_bytes": ob,
-                                 "gbs": ob / (ms_outer / 1e3) / 1e9,
-                                 "frac": ob / (ms_outer / 1e3) / 1e9 / peak,
-                                 "note": "L2 flushed before each launch; the 29 MB it writes fits in L2"},
-            "diag_grad": {"us": 1e3 * ms_diag, "gbs": 48 * n / (ms_diag / 1e3) / 1e9,
-                          "l2_resident": True}}
+    return {"converged": conv,
+            "grid_64": {"workload": "C5 64^3 FD inverse problem, A(theta) = L - kappa^2 diag(theta), kh = 0.5",
+                        "n": n, "nnz": nnz,
+                        "forward": {"ms": ms_f, "iters": inf_f.iters, "status": inf_f.status_name,
+                                    "relres_true": inf_f.relres_true,
+                                    "iter_us": 1e3 * ms_f / max(inf_f.iters, 1)},
+                        "outer_on_pattern": {"us": 1e3 * ms_outer, "algorithmic_bytes": ob,
+                                             "gbs": ob / (ms_outer / 1e3) / 1e9,
+                                             "frac": ob / (ms_outer / 1e3) / 1e9 / peak,
+                                             "note": "L2 flushed before each launch; the 29 MB it writes fits in L2"},
+                        "diag_grad": {"us": 1e3 * ms_diag, "gbs": 48 * n / (ms_diag / 1e3) / 1e9,
+                                      "l2_resident": True}}}
 
 
 def workload_config(A, maxit, arith="fp64", iters=None, status=None):

@@ -65,7 +65,9 @@ enum {
     HZ_FLAG_VALIDATE = 1u,   /* check rowptr monotone, rowptr[n]==nnz, cols in range (host copy) */
     HZ_FLAG_SELL = 2u,       /* also build a SELL-C-sigma copy and use it for SpMV */
     HZ_FLAG_C64 = 4u,        /* also build the complex64 copy used by the mixed solver */
-    HZ_FLAG_AUTOTUNE = 8u,   /* time the SpMV variants once on this matrix and keep the fastest */
+    HZ_FLAG_AUTOTUNE = 8u,   /* time the SpMV variants once on this matrix and keep the fastest;
+                                `group` becomes the fastest binary64 CSR-vector group (the row
+                                tile of this matrix in hz_zsolve_batched) whichever kind wins */
     HZ_FLAG_FF = 16u         /* also build the double-float split of the values and use the
                                 double-float SpMV: every binary64 value is carried as hi + lo
                                 binary32 parts (48 significant bits, NOT binary64) on the
@@ -326,10 +328,17 @@ HZ_API hz_status hz_zsolve_opts(hz_mat *A, const hz_z *d_b, hz_z *d_x,
  * on the device; all systems advance together through the phases of the
  * iteration and leave the batch as they converge.  Same algorithm,
  * stopping rule and status semantics as hz_zsolve (no restart), per system.
- * The batch runs in double-float arithmetic when every handle (with n > 0)
- * was created with HZ_FLAG_FF and its SpMV kind is a double-float one, in
- * binary64 otherwise.  d_x[s] holds x0 on entry and the solution on exit.
- * h_info has nsys entries.  Synchronises `stream`.
+ * mode HZ_MODE_FP64: the batch runs in double-float arithmetic when every
+ * handle (with n > 0) was created with HZ_FLAG_FF and its SpMV kind is a
+ * double-float one, in binary64 otherwise.  mode HZ_MODE_MIXED: every system
+ * runs the mixed-precision refinement of hz_zsolve (binary64 outer residual
+ * and update, complex64 inner BiCGStab to 1e-5 with at most 1000 iterations,
+ * at most 50 refinement steps, maxit capping the inner iterations in total,
+ * the best iterate kept), each system at its own stage; the handles' complex64
+ * copies are made on demand (synchronising).  d_x[s] holds x0 on entry and
+ * the solution on exit.  h_info has nsys entries.  Synchronises `stream`.
+ * Errors: HZ_ERR_ARG (nsys outside 0..1024, unknown mode, null pointers),
+ * HZ_ERR_ALLOC, HZ_ERR_TIMEOUT (a grid-barrier wait expired).
  */
 HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, const hz_z *const *d_b,
                                    hz_z *const *d_x, double tol, int32_t maxit, uint32_t mode,

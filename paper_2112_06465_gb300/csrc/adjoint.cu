@@ -34,6 +34,45 @@ __global__ void __launch_bounds__(256) k_outer_pattern(int n, const int *__restr
     }
 }
 
+// The same product on the row blocks of the block-flat SpMV kernels (<= 32
+// complete rows and <= 512 entries, or one longer row): one warp per block,
+// lane l takes entries kb + l, kb + l + 32, ... so that every lane of every
+// binary64 instruction is busy (the binary64 pipe is the limit here: four
+// multiply-adds per entry) and the writes of g are coalesced; each lane
+// walks the block's row pointers (shared memory) forward to the row of its
+// next entry.
+constexpr int kOpThreads = 128;
+__global__ void __launch_bounds__(kOpThreads) k_outer_flat(int nfblk, const int *__restrict__ fblk,
+                                                           const int *__restrict__ fblk_k,
+                                                           const int *__restrict__ rowptr,
+                                                           const int *__restrict__ col,
+                                                           const double2 *__restrict__ mu,
+                                                           const double2 *__restrict__ x, double2 *__restrict__ g) {
+    __shared__ int rps[kOpThreads / 32][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int *rp = rps[w];
+    const int step = gridDim.x * (kOpThreads / 32);
+    for (int b = blockIdx.x * (kOpThreads / 32) + w; b < nfblk; b += step) {
+        const int r0 = __ldg(fblk + b), r1 = __ldg(fblk + b + 1);
+        const int kb = __ldg(fblk_k + b), ke = __ldg(fblk_k + b + 1);
+        const int nr = r1 - r0;
+        if (lane < nr) rp[lane] = __ldg(rowptr + r0 + lane);
+        if (lane == 0) rp[nr] = ke;
+        __syncwarp();
+        int j = 0;   // row (offset in the block) of this lane's current entry
+        double2 m = make_double2(0.0, 0.0);
+        int mrow = -1;
+        for (int k = kb + lane; k < ke; k += 32) {
+            while (j < nr - 1 && rp[j + 1] <= k) ++j;
+            if (j != mrow) { m = __ldg(mu + r0 + j); mrow = j; }
+            const double2 xj = __ldg(x + __ldg(col + k));
+            const double2 p = cmul(m, xj);
+            g[k] = make_double2(-p.x, p.y);
+        }
+        __syncwarp();
+    }
+}
+
 // position of the diagonal entry of every row (-1 if absent)
 __global__ void k_find_diag(int n, const int *__restrict__ rowptr, const int *__restrict__ col, int *__restrict__ pos) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -95,6 +134,17 @@ extern "C" HZ_API hz_status hz_outer_on_pattern(const hz_mat *A, const hz_z *d_m
     HZ_CHECK(A, "hz_outer_on_pattern: null handle");
     if (A->n == 0 || A->nnz == 0) return HZ_OK;
     HZ_CHECK(d_mu && d_x && d_gradval, "hz_outer_on_pattern: null vector");
+    if (A->fblk) {   // every handle has its row blocks; the row-group kernel stays for the rest
+        DevInfo d;
+        HZ_TRY(dev_info(&d));
+        const int grid = (int)std::max<int64_t>(
+            1, std::min<int64_t>((A->nfblk + kOpThreads / 32 - 1) / (kOpThreads / 32), (int64_t)d.num_sms * 16));
+        k_outer_flat<<<grid, kOpThreads, 0, (cudaStream_t)stream>>>(A->nfblk, A->fblk, A->fblk_k, A->rowptr, A->col,
+                                                                     (const double2 *)d_mu, (const double2 *)d_x,
+                                                                     (double2 *)d_gradval);
+        HZ_CUDA(cudaGetLastError());
+        return HZ_OK;
+    }
     int w = 2;
     while (w < 32 && w < A->mean_row) w *= 2;
     const int grid = grid_for((int64_t)A->n * w);

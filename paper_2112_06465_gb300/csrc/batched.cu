@@ -19,6 +19,16 @@
 // products then read the handles' split values, the iterate lives in a
 // double-float workspace loaded from and stored to the caller's x, and the
 // per-item reductions are folded in binary64 as before.
+//
+// Mixed precision (HZ_MODE_MIXED, k_batched_mixed): every system runs the
+// refinement of the single-system mixed solve -- outer residual r = b - A x
+// in binary64 (phase P_OUT), an inner BiCGStab on the complex64 copy of A
+// with complex64 vectors and binary32 sums (phases F1..F5 in float2), then
+// x += d in binary64 (P_UPD) -- each system at its own stage: in one round
+// the systems whose inner solve is running take an inner iteration, those
+// whose inner solve just ended are updated and take their next outer
+// residual.  The refinement keeps each system's best iterate and stops a
+// system when a step fails to reduce its outer residual.
 #include <algorithm>
 #include <type_traits>
 #include <vector>
@@ -43,6 +53,11 @@ struct BSys {
     double2 *x;                  // the caller's x0 / solution
     void *xw;                    // the iterate (double-float batches; else x itself)
     void *r, *rh, *p, *v, *s, *t;
+    // mixed batches: complex64 values and inner vectors (d = the inner
+    // iterate), and the refinement's best iterate
+    const float2 *val32;
+    float2 *r32, *rh32, *p32, *v32, *s32, *t32, *d32;
+    double2 *xbest;
 };
 
 // the system's vectors in format V
@@ -52,18 +67,33 @@ template <class V> struct BVecs {
 template <class V>
 __device__ __forceinline__ BVecs<V> bvecs(const BSys &sy) {
     BVecs<V> o;
-    o.x = std::is_same<V, double2>::value ? (V *)sy.x : (V *)sy.xw;
-    o.r = (V *)sy.r; o.rh = (V *)sy.rh; o.p = (V *)sy.p; o.v = (V *)sy.v; o.s = (V *)sy.s; o.t = (V *)sy.t;
+    if constexpr (std::is_same<V, float2>::value) {   // the inner solve of a mixed batch
+        o.x = sy.d32; o.r = sy.r32; o.rh = sy.rh32; o.p = sy.p32; o.v = sy.v32; o.s = sy.s32; o.t = sy.t32;
+    } else {
+        o.x = std::is_same<V, double2>::value ? (V *)sy.x : (V *)sy.xw;
+        o.r = (V *)sy.r; o.rh = (V *)sy.rh; o.p = (V *)sy.p; o.v = (V *)sy.v; o.s = (V *)sy.s; o.t = (V *)sy.t;
+    }
     return o;
 }
 
+// a device-state scalar (binary64 complex) in the arithmetic of format V
+template <class V>
+__device__ __forceinline__ typename Ar<V>::S bscal(double2 a) {
+    if constexpr (std::is_same<V, float2>::value) return to_c64(a);
+    else return Ar<V>::scal(a);
+}
+
 struct BState {
-    double2 rho, rho_old, alpha, omega, beta;
+    double2 rho, rho_old, alpha, omega, beta;   // BiCGStab scalars (the inner solve in a mixed batch)
     double nb, rel, relres_true;
     int iter, done, half, status;
     unsigned int cnt;            // items finished in the current phase
-    int pad;
+    // mixed batches: the refinement
+    int stage;                   // S_OUTER, S_INNER, S_UPDATE or S_FINISHED
+    int outer, total_inner, out_status, use_best, save, zero_x;
+    double nb_out, rel_out, rel_best;
 };
+enum Stage { S_OUTER = 0, S_INNER = 1, S_UPDATE = 2, S_FINISHED = 3 };
 
 struct BCtl {
     double tol;
@@ -72,9 +102,13 @@ struct BCtl {
     unsigned int bar_count;
     volatile unsigned int bar_gen;
     int err;
+    // mixed batches
+    int mixed;
+    double in_tol;
+    int in_maxit, max_outer;
 };
 
-enum Phase { P_INIT = 0, P_F1, P_F2, P_F3, P_F4, P_F5, P_TRUE, P_LOAD, P_STORE };
+enum Phase { P_INIT = 0, P_F1, P_F2, P_F3, P_F4, P_F5, P_TRUE, P_LOAD, P_STORE, P_OUT, P_UPD, P_BEST };
 
 // bounded grid barrier: gives up after ~1 s and flags the error
 __device__ bool bgrid_sync(BCtl *c) {
@@ -130,8 +164,50 @@ __device__ __forceinline__ void bsum(double (&v)[NV]) {
 }
 
 // per-system scalar work after a phase's reduction (thread 0)
+__device__ void finalize_phase(int phase, const BCtl *c, BState *S, const double *tot);
+
 __device__ void finalize(int phase, const BCtl *c, BState *S, const double *tot) {
+    finalize_phase(phase, c, S, tot);
+    if (c->mixed && phase >= P_F1 && phase <= P_F5) {
+        if (phase == P_F5) {   // one more inner iteration, held to the total cap
+            S->total_inner += 1;
+            if (!S->done && S->total_inner >= c->maxit) { S->status = HZ_NOT_CONVERGED; S->done = 1; }
+        }
+        if (S->done && S->stage == S_INNER) S->stage = S_UPDATE;
+    }
+}
+
+// the outer step of a mixed batch: the refinement's decision after r = b - A x
+// (tot = ||r||^2, ||b||^2, ||r32||^2) and the start of the next inner solve
+__device__ void finalize_outer(const BCtl *c, BState *S, const double *tot) {
     const double2 one = make_double2(1.0, 0.0);
+    const double nb = sqrt(tot[1]);
+    S->nb_out = nb;
+    S->save = 0;
+    S->stage = S_FINISHED;
+    if (nb == 0.0) { S->rel_out = 0.0; S->out_status = HZ_OK; S->zero_x = 1; return; }
+    const double rel = sqrt(tot[0]) / nb;
+    S->rel_out = rel;
+    if (!isfinite(rel)) { S->out_status = HZ_ERR_NAN; S->use_best = S->outer > 0; return; }
+    if (rel <= c->tol) { S->out_status = HZ_OK; return; }
+    if (rel >= S->rel_best) { S->out_status = HZ_NOT_CONVERGED; S->use_best = 1; return; }
+    if (S->outer >= c->max_outer || S->total_inner >= c->maxit) { S->out_status = HZ_NOT_CONVERGED; return; }
+    S->rel_best = rel;
+    S->save = 1;   // this x is the best so far: P_UPD keeps a copy before x += d
+    S->outer += 1;
+    const double nb32 = sqrt(tot[2]);
+    S->rho = make_double2(tot[2], 0.0);
+    S->rho_old = one; S->alpha = one; S->omega = one; S->beta = make_double2(0.0, 0.0);
+    S->nb = nb32; S->rel = 1.0; S->half = 0; S->iter = 1;
+    S->status = HZ_NOT_CONVERGED;
+    S->done = nb32 == 0.0;
+    S->stage = S->done ? S_UPDATE : S_INNER;
+}
+
+__device__ void finalize_phase(int phase, const BCtl *c, BState *S, const double *tot) {
+    const double2 one = make_double2(1.0, 0.0);
+    const double tol = c->mixed ? c->in_tol : c->tol;
+    const int maxit = c->mixed ? c->in_maxit : c->maxit;
     switch (phase) {
         case P_INIT: {
             const double nb = sqrt(tot[1]);
@@ -157,7 +233,7 @@ __device__ void finalize(int phase, const BCtl *c, BState *S, const double *tot)
         case P_F3: {
             const double rel = sqrt(tot[0]) / S->nb;
             if (!isfinite(rel)) { S->status = HZ_ERR_NAN; S->done = 1; S->rel = rel; break; }
-            if (rel <= c->tol) { S->half = 1; S->rel = rel; }
+            if (rel <= tol) { S->half = 1; S->rel = rel; }
             break;
         }
         case P_F4: {
@@ -170,9 +246,9 @@ __device__ void finalize(int phase, const BCtl *c, BState *S, const double *tot)
             const double rel = sqrt(tot[2]) / S->nb;
             S->rel = rel;
             if (!isfinite(rel)) { S->status = HZ_ERR_NAN; S->done = 1; }
-            else if (rel <= c->tol) { S->status = HZ_OK; S->done = 1; }
+            else if (rel <= tol) { S->status = HZ_OK; S->done = 1; }
             else if (cis_zero(S->omega)) { S->status = HZ_BREAKDOWN; S->done = 1; }
-            else if (S->iter >= c->maxit) { S->status = HZ_NOT_CONVERGED; S->done = 1; }
+            else if (S->iter >= maxit) { S->status = HZ_NOT_CONVERGED; S->done = 1; }
             else {
                 const double2 rn = make_double2(tot[0], tot[1]);
                 S->beta = cmul(cdiv(rn, S->rho), cdiv(S->alpha, S->omega));
@@ -183,8 +259,13 @@ __device__ void finalize(int phase, const BCtl *c, BState *S, const double *tot)
             }
             break;
         }
-        case P_TRUE:
-            S->relres_true = S->nb == 0.0 ? 0.0 : sqrt(tot[0]) / S->nb;
+        case P_TRUE: {
+            const double nb = c->mixed ? S->nb_out : S->nb;
+            S->relres_true = nb == 0.0 ? 0.0 : sqrt(tot[0]) / nb;
+            break;
+        }
+        case P_OUT:
+            finalize_outer(c, S, tot);
             break;
         default: break;
     }
@@ -271,14 +352,17 @@ __device__ void item_done_ff(int phase, const BCtl *c, const BSys &sy, BState *S
 template <class V, class Acc>
 __device__ __forceinline__ void row_epilogue(int phase, const BSys &sy, int row, V y, Acc (&acc)[3]) {
     using A = Ar<V>;
+    constexpr bool kC64 = std::is_same<V, float2>::value;   // inner solve of a mixed batch
     const BVecs<V> w = bvecs<V>(sy);
     if (phase == P_INIT) {
-        const V bi = A::from_c128(sy.b[row]);
-        const V ri = A::sub(bi, y);
-        w.r[row] = ri; w.rh[row] = ri;
-        w.p[row] = A::zero(); w.v[row] = A::zero();
-        A::nrm2(acc[0], ri);
-        A::nrm2(acc[1], bi);
+        if constexpr (!kC64) {
+            const V bi = A::from_c128(sy.b[row]);
+            const V ri = A::sub(bi, y);
+            w.r[row] = ri; w.rh[row] = ri;
+            w.p[row] = A::zero(); w.v[row] = A::zero();
+            A::nrm2(acc[0], ri);
+            A::nrm2(acc[1], bi);
+        }
     } else if (phase == P_F2) {
         w.v[row] = y;
         A::dotc(acc[0], acc[1], w.rh[row], y);
@@ -286,7 +370,18 @@ __device__ __forceinline__ void row_epilogue(int phase, const BSys &sy, int row,
         w.t[row] = y;
         A::dotc(acc[0], acc[1], y, w.s[row]);
         A::nrm2(acc[2], y);
-    } else {   // P_TRUE
+    } else if (phase == P_OUT) {   // mixed: outer residual in binary64, inner start in complex64
+        if constexpr (std::is_same<V, double2>::value) {
+            const double2 ri = csub(sy.b[row], y);
+            const float2 r32 = to_c64(ri);
+            sy.r32[row] = r32; sy.rh32[row] = r32;
+            sy.p32[row] = make_float2(0.f, 0.f); sy.v32[row] = make_float2(0.f, 0.f);
+            sy.d32[row] = make_float2(0.f, 0.f);
+            A::nrm2(acc[0], ri);
+            A::nrm2(acc[1], sy.b[row]);
+            A::nrm2(acc[2], to_c128(r32));
+        }
+    } else if constexpr (!kC64) {   // P_TRUE
         A::nrm2(acc[0], A::sub(A::from_c128(sy.b[row]), y));
     }
 }
@@ -304,6 +399,14 @@ __device__ void spmv_item(int phase, const BSys &sy, int r0, int r1, typename Ar
         if constexpr (std::is_same<V, double2>::value) {
             y = make_double2(0.0, 0.0);
             for (int k = beg + lane; k < end; k += W) cmac(y, ld_stream(sy.val + k), __ldg(x + ld_stream(sy.col + k)));
+#pragma unroll
+            for (int off = W / 2; off > 0; off >>= 1) {
+                y.x += __shfl_xor_sync(gmask, y.x, off, W);
+                y.y += __shfl_xor_sync(gmask, y.y, off, W);
+            }
+        } else if constexpr (std::is_same<V, float2>::value) {   // complex64 inner operator
+            y = make_float2(0.f, 0.f);
+            for (int k = beg + lane; k < end; k += W) cmac(y, ld_stream(sy.val32 + k), __ldg(x + ld_stream(sy.col + k)));
 #pragma unroll
             for (int off = W / 2; off > 0; off >>= 1) {
                 y.x += __shfl_xor_sync(gmask, y.x, off, W);
@@ -337,8 +440,25 @@ template <class V>
 __device__ void vec_item(int phase, const BSys &sy, const BState *S, int e0, int e1, typename Ar<V>::Acc (&acc)[3]) {
     using A = Ar<V>;
     const BVecs<V> w = bvecs<V>(sy);
-    const typename A::S alpha = A::scal(S->alpha), omega = A::scal(S->omega), beta = A::scal(S->beta);
+    const typename A::S alpha = bscal<V>(S->alpha), omega = bscal<V>(S->omega), beta = bscal<V>(S->beta);
     const bool half = S->half;
+    if constexpr (std::is_same<V, double2>::value) {
+        if (phase == P_UPD) {   // mixed: keep the best iterate, then x += d
+            const bool save = S->save != 0;
+            for (int i = e0 + threadIdx.x; i < e1; i += kBBlock) {
+                const double2 xi = sy.x[i];
+                if (save) sy.xbest[i] = xi;
+                sy.x[i] = cadd(xi, to_c128(sy.d32[i]));
+            }
+            return;
+        }
+        if (phase == P_BEST) {   // mixed: the answer is the kept best iterate (or 0 for b = 0)
+            const bool zero = S->zero_x != 0;
+            for (int i = e0 + threadIdx.x; i < e1; i += kBBlock)
+                sy.x[i] = zero ? make_double2(0.0, 0.0) : sy.xbest[i];
+            return;
+        }
+    }
     for (int i = e0 + threadIdx.x; i < e1; i += kBBlock) {
         if (phase == P_F1) {
             w.p[i] = A::axpy(w.r[i], beta, A::axmy(w.p[i], omega, w.v[i]));
@@ -358,10 +478,9 @@ __device__ void vec_item(int phase, const BSys &sy, const BState *S, int e0, int
             w.r[i] = ri;
             A::dotc(acc[0], acc[1], w.rh[i], ri);
             A::nrm2(acc[2], ri);
-        } else if (phase == P_LOAD) {
-            w.x[i] = A::from_c128(sy.x[i]);
-        } else {   // P_STORE
-            sy.x[i] = A::to_c128(w.x[i]);
+        } else if constexpr (!std::is_same<V, float2>::value) {
+            if (phase == P_LOAD) w.x[i] = A::from_c128(sy.x[i]);
+            else if (phase == P_STORE) sy.x[i] = A::to_c128(w.x[i]);
         }
     }
 }
@@ -370,7 +489,10 @@ __device__ void vec_item(int phase, const BSys &sy, const BState *S, int e0, int
 template <class V>
 __device__ void run_phase(int phase, const BCtl *c, const BSys *sys, BState *st, double *partials, const int *act,
                           const int *pref, int nact) {
-    const bool spmv = phase == P_INIT || phase == P_F2 || phase == P_F4 || phase == P_TRUE;
+    const bool spmv = phase == P_INIT || phase == P_F2 || phase == P_F4 || phase == P_TRUE || phase == P_OUT;
+    // phases over a list the stage already filters (mixed) or over every system
+    const bool listed = phase == P_INIT || phase == P_TRUE || phase == P_LOAD || phase == P_STORE ||
+                        phase == P_OUT || phase == P_UPD || phase == P_BEST;
     const int total = pref[nact];
     for (int j = blockIdx.x; j < total; j += gridDim.x) {
         int lo = 0, hi = nact - 1;          // system owning item j
@@ -385,8 +507,7 @@ __device__ void run_phase(int phase, const BCtl *c, const BSys *sys, BState *st,
         __shared__ int skip;
         if (threadIdx.x == 0) {
             const int done = *(volatile int *)&S->done, half = *(volatile int *)&S->half;
-            skip = (phase != P_INIT && phase != P_TRUE && phase != P_LOAD && phase != P_STORE && done) ||
-                   (phase == P_F4 && half);
+            skip = (!listed && done) || (phase == P_F4 && half);
         }
         __syncthreads();
         if (skip) continue;
@@ -412,7 +533,7 @@ __device__ void run_phase(int phase, const BCtl *c, const BSys *sys, BState *st,
             } else {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) acc[q] = (double)Ar<V>::total(va[q]);
-                if (phase == P_F4) item_done<3>(phase, c, sy, S, partials, g, sy.sp_item0, nit, acc);
+                if (phase == P_F4 || phase == P_OUT) item_done<3>(phase, c, sy, S, partials, g, sy.sp_item0, nit, acc);
                 else if (phase == P_TRUE) {
                     double a1[1] = {acc[0]};
                     item_done<1>(phase, c, sy, S, partials, g, sy.sp_item0, nit, a1);
@@ -447,13 +568,28 @@ __device__ void run_phase(int phase, const BCtl *c, const BSys *sys, BState *st,
 // table of systems still running and their item prefix sums: the flags and
 // item counts are loaded by all threads at once, the prefix is taken in
 // shared memory by one thread
+enum { A_ALL = 0, A_RUNNING = 1, A_INNER = 2, A_UPDATE = 3, A_BEST = 4, A_UNFINISHED = 5 };
+
+__device__ __forceinline__ bool bactive(int which, const BState &S) {
+    switch (which) {
+        case A_ALL: return true;
+        case A_RUNNING: return !*(volatile const int *)&S.done;
+        case A_INNER: return *(volatile const int *)&S.stage == S_INNER && !*(volatile const int *)&S.done;
+        case A_UPDATE: return *(volatile const int *)&S.stage == S_UPDATE;
+        case A_BEST:
+            return *(volatile const int *)&S.stage == S_FINISHED &&
+                   (*(volatile const int *)&S.use_best || *(volatile const int *)&S.zero_x);
+        default: return *(volatile const int *)&S.stage != S_FINISHED;
+    }
+}
+
 __device__ int build_active(int spmv_items, const BCtl *c, const BSys *sys, const BState *st, int *act,
-                            int *pref, bool only_running) {
+                            int *pref, int which) {
     __shared__ int nact;
     __shared__ int cnt[kBMaxSys];
     const int nsys = c->nsys;
     for (int s = threadIdx.x; s < nsys; s += kBBlock) {
-        const bool run = !only_running || !*(volatile const int *)&st[s].done;
+        const bool run = bactive(which, st[s]);
         cnt[s] = run ? (spmv_items ? sys[s].sp_items : sys[s].vc_items) : -1;
     }
     __syncthreads();
@@ -480,17 +616,17 @@ __global__ void __launch_bounds__(kBBlock) k_batched(BCtl *c, const BSys *sys, B
     constexpr bool kFF = !std::is_same<V, double2>::value;
     int nact;
     if constexpr (kFF) {   // the iterate into the double-float workspace
-        nact = build_active(0, c, sys, st, act, pref_vc, false);
+        nact = build_active(0, c, sys, st, act, pref_vc, A_ALL);
         run_phase<V>(P_LOAD, c, sys, st, partials, act, pref_vc, nact);
         if (!bgrid_sync(c)) return;
     }
-    nact = build_active(1, c, sys, st, act, pref_sp, false);
+    nact = build_active(1, c, sys, st, act, pref_sp, A_ALL);
     run_phase<V>(P_INIT, c, sys, st, partials, act, pref_sp, nact);
     if (!bgrid_sync(c)) return;
     for (int guard = 0; guard <= c->maxit + 1; ++guard) {
-        nact = build_active(1, c, sys, st, act, pref_sp, true);
+        nact = build_active(1, c, sys, st, act, pref_sp, A_RUNNING);
         if (nact == 0) break;
-        build_active(0, c, sys, st, act, pref_vc, true);
+        build_active(0, c, sys, st, act, pref_vc, A_RUNNING);
         run_phase<V>(P_F1, c, sys, st, partials, act, pref_vc, nact);
         if (!bgrid_sync(c)) return;
         run_phase<V>(P_F2, c, sys, st, partials, act, pref_sp, nact);
@@ -502,14 +638,60 @@ __global__ void __launch_bounds__(kBBlock) k_batched(BCtl *c, const BSys *sys, B
         run_phase<V>(P_F5, c, sys, st, partials, act, pref_vc, nact);
         if (!bgrid_sync(c)) return;
     }
-    nact = build_active(1, c, sys, st, act, pref_sp, false);
+    nact = build_active(1, c, sys, st, act, pref_sp, A_ALL);
     run_phase<V>(P_TRUE, c, sys, st, partials, act, pref_sp, nact);
     if constexpr (kFF) {   // the solution back to the caller's x
         if (!bgrid_sync(c)) return;
-        nact = build_active(0, c, sys, st, act, pref_vc, false);
+        nact = build_active(0, c, sys, st, act, pref_vc, A_ALL);
         run_phase<V>(P_STORE, c, sys, st, partials, act, pref_vc, nact);
     }
 }
+
+// mixed-precision sweep: every system refines in binary64 around complex64
+// inner BiCGStab solves, each at its own stage (see the file comment)
+__global__ void __launch_bounds__(kBBlock) k_batched_mixed(BCtl *c, const BSys *sys, BState *st, double *partials) {
+    __shared__ int act[kBMaxSys];
+    __shared__ int pref_sp[kBMaxSys + 1];
+    __shared__ int pref_vc[kBMaxSys + 1];
+    int nact = build_active(1, c, sys, st, act, pref_sp, A_UNFINISHED);
+    run_phase<double2>(P_OUT, c, sys, st, partials, act, pref_sp, nact);
+    if (!bgrid_sync(c)) return;
+    // every round advances each system by one inner iteration or one
+    // refinement step, so a system leaves within maxit + max_outer + 1 rounds
+    const int cap = c->maxit + c->max_outer + 2;
+    for (int round = 0; round <= cap; ++round) {
+        const int nin = build_active(1, c, sys, st, act, pref_sp, A_INNER);
+        if (nin > 0) {
+            build_active(0, c, sys, st, act, pref_vc, A_INNER);
+            run_phase<float2>(P_F1, c, sys, st, partials, act, pref_vc, nin);
+            if (!bgrid_sync(c)) return;
+            run_phase<float2>(P_F2, c, sys, st, partials, act, pref_sp, nin);
+            if (!bgrid_sync(c)) return;
+            run_phase<float2>(P_F3, c, sys, st, partials, act, pref_vc, nin);
+            if (!bgrid_sync(c)) return;
+            run_phase<float2>(P_F4, c, sys, st, partials, act, pref_sp, nin);
+            if (!bgrid_sync(c)) return;
+            run_phase<float2>(P_F5, c, sys, st, partials, act, pref_vc, nin);
+            if (!bgrid_sync(c)) return;
+        }
+        const int nup = build_active(0, c, sys, st, act, pref_vc, A_UPDATE);
+        if (nin == 0 && nup == 0) break;
+        if (nup > 0) {
+            run_phase<double2>(P_UPD, c, sys, st, partials, act, pref_vc, nup);
+            if (!bgrid_sync(c)) return;
+            build_active(1, c, sys, st, act, pref_sp, A_UPDATE);
+            run_phase<double2>(P_OUT, c, sys, st, partials, act, pref_sp, nup);
+            if (!bgrid_sync(c)) return;
+        }
+    }
+    nact = build_active(0, c, sys, st, act, pref_vc, A_BEST);
+    run_phase<double2>(P_BEST, c, sys, st, partials, act, pref_vc, nact);
+    if (!bgrid_sync(c)) return;
+    nact = build_active(1, c, sys, st, act, pref_sp, A_ALL);
+    run_phase<double2>(P_TRUE, c, sys, st, partials, act, pref_sp, nact);
+}
+
+hz_status ensure_c64(hz_mat *A, cudaStream_t s);
 
 }  // namespace hz
 
@@ -519,7 +701,8 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
                                               hz_z *const *d_x, double tol, int32_t maxit, uint32_t mode,
                                               hz_info *h_info, void *stream) {
     HZ_CHECK(nsys >= 0 && nsys <= kBMaxSys, "hz_zsolve_batched: nsys out of range (0..1024)");
-    HZ_CHECK(mode == HZ_MODE_FP64, "hz_zsolve_batched: only HZ_MODE_FP64 is batched");
+    HZ_CHECK(mode == HZ_MODE_FP64 || mode == HZ_MODE_MIXED, "hz_zsolve_batched: unknown mode");
+    const bool mixed = mode == HZ_MODE_MIXED;
     HZ_CHECK(maxit >= 0 && tol >= 0.0, "hz_zsolve_batched: bad tol/maxit");
     if (nsys == 0) return HZ_OK;
     HZ_CHECK(A && d_b && d_x && h_info, "hz_zsolve_batched: null argument");
@@ -528,12 +711,17 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
     int64_t sp = 0, vc = 0, vec_elems = 0;
     // double-float when every handle carries the split values and runs a
     // double-float SpMV kind; binary64 otherwise
-    bool ff = true;
+    // (a mixed batch refines in binary64 around complex64 inner solves)
+    bool ff = !mixed;
     for (int k = 0; k < nsys; ++k) {
         HZ_CHECK(A[k], "hz_zsolve_batched: null matrix handle");
         if (A[k]->n > 0 && !(A[k]->val_ff && is_ff_kind(A[k]->spmv_kind))) ff = false;
+        if (mixed && A[k]->n > 0) HZ_TRY(ensure_c64(A[k], s));
     }
-    const int nvec = ff ? 7 : 6;
+    // per system: 16-byte vectors (6 binary64 or 7 double-float; mixed: the
+    // best iterate) and, in a mixed batch, 7 complex64 inner vectors
+    const int nvec = mixed ? 1 : ff ? 7 : 6;
+    const int nvec32 = mixed ? 7 : 0;
     for (int k = 0; k < nsys; ++k) {
         HZ_CHECK(A[k]->n == 0 || (d_b[k] && d_x[k]), "hz_zsolve_batched: null vector");
         BSys &y = hs[k];
@@ -545,6 +733,7 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
         y.vc_item0 = (int)vc;
         y.vc_items = (y.n + kBVecItem - 1) / kBVecItem;
         y.rowptr = A[k]->rowptr; y.col = A[k]->col; y.val = A[k]->val; y.vff = A[k]->val_ff;
+        y.val32 = A[k]->val32;
         y.b = (const double2 *)d_b[k]; y.x = (double2 *)d_x[k]; y.xw = nullptr;
         sp += y.sp_items;
         vc += y.vc_items;
@@ -553,12 +742,16 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
     HZ_CHECK(sp < INT32_MAX / 4 && vc < INT32_MAX / 4, "hz_zsolve_batched: batch too large");
     // workspace: 6 vectors per system, item partials, states, controls
     double2 *work = nullptr;
+    float2 *work32 = nullptr;
     double *partials = nullptr;
     BState *st = nullptr;
     BSys *dsys = nullptr;
     BCtl *ctl = nullptr;
-    auto cleanup = [&]() { cudaFree(work); cudaFree(partials); cudaFree(st); cudaFree(dsys); cudaFree(ctl); };
+    auto cleanup = [&]() {
+        cudaFree(work); cudaFree(work32); cudaFree(partials); cudaFree(st); cudaFree(dsys); cudaFree(ctl);
+    };
     if (cudaMalloc(&work, sizeof(double2) * std::max<int64_t>(nvec * vec_elems, 1)) != cudaSuccess ||
+        cudaMalloc(&work32, sizeof(float2) * std::max<int64_t>(nvec32 * vec_elems, 1)) != cudaSuccess ||
         cudaMalloc(&partials, sizeof(double) * 4 * std::max<int64_t>(std::max(sp, vc), 1)) != cudaSuccess ||
         cudaMalloc(&st, sizeof(BState) * nsys) != cudaSuccess || cudaMalloc(&dsys, sizeof(BSys) * nsys) != cudaSuccess ||
         cudaMalloc(&ctl, sizeof(BCtl)) != cudaSuccess) {
@@ -566,25 +759,42 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
         set_error("hz_zsolve_batched: workspace allocation failed");
         return HZ_ERR_ALLOC;
     }
-    int64_t off = 0;
+    int64_t off = 0, off32 = 0;
     for (auto &y : hs) {   // 16-byte elements in either format
+        if (mixed) {
+            y.xbest = work + off;
+            off += y.n;
+            float2 **v32[7] = {&y.r32, &y.rh32, &y.p32, &y.v32, &y.s32, &y.t32, &y.d32};
+            for (int q = 0; q < nvec32; ++q) { *v32[q] = work32 + off32; off32 += y.n; }
+            continue;
+        }
         void **vecs[7] = {&y.r, &y.rh, &y.p, &y.v, &y.s, &y.t, &y.xw};
         for (int q = 0; q < nvec; ++q) { *vecs[q] = work + off; off += y.n; }
     }
     BCtl hc{};
     hc.tol = tol; hc.maxit = maxit; hc.nsys = nsys;
+    // the refinement's controls: the defaults of the single-system mixed solve
+    hc.mixed = mixed ? 1 : 0;
+    hc.in_tol = 1e-5;
+    hc.in_maxit = 1000;
+    hc.max_outer = 50;
     cudaError_t e = cudaMemcpyAsync(dsys, hs.data(), sizeof(BSys) * nsys, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctl, &hc, sizeof(BCtl), cudaMemcpyHostToDevice, s);
     std::vector<BState> hst(nsys);
     for (int k = 0; k < nsys; ++k) {
         hst[k] = BState{};
-        if (hs[k].n == 0) { hst[k].done = 1; hst[k].status = HZ_OK; }   // nothing to solve
+        hst[k].stage = S_OUTER;
+        hst[k].rel_best = INFINITY;
+        if (hs[k].n == 0) {   // nothing to solve
+            hst[k].done = 1; hst[k].status = HZ_OK;
+            hst[k].stage = S_FINISHED; hst[k].out_status = HZ_OK;
+        }
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(st, hst.data(), sizeof(BState) * nsys, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     DevInfo d;
     int occ = 0;
-    void *kern = ff ? (void *)k_batched<float4> : (void *)k_batched<double2>;
+    void *kern = mixed ? (void *)k_batched_mixed : ff ? (void *)k_batched<float4> : (void *)k_batched<double2>;
     if (e == cudaSuccess && dev_info(&d) == HZ_OK)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBBlock, 0);
     if (e == cudaSuccess && occ < 1) e = cudaErrorInvalidConfiguration;
@@ -607,9 +817,16 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
     for (int k = 0; k < nsys; ++k) {
         hz_info &o = h_info[k];
         o = hz_info{};
-        o.iters = hst[k].iter;
-        o.status = hst[k].status;
-        o.relres_rec = hst[k].rel;
+        if (mixed) {
+            o.iters = hst[k].total_inner;
+            o.status = hst[k].out_status;
+            o.outer = hst[k].outer;
+            o.relres_rec = hst[k].use_best ? hst[k].rel_best : hst[k].rel_out;
+        } else {
+            o.iters = hst[k].iter;
+            o.status = hst[k].status;
+            o.relres_rec = hst[k].rel;
+        }
         o.relres_true = hst[k].relres_true;
         if (A[k]->n == 0) { o.status = HZ_OK; o.iters = 0; }
         if (o.status == HZ_OK && o.relres_true > tol) o.status = HZ_NOT_CONVERGED;

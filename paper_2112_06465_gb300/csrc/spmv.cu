@@ -255,7 +255,8 @@ static hz_status autotune(hz_mat *A, cudaStream_t s) {
     if (A->fblk) cand.push_back({HZ_SPMV_FLAT64, 0});
     if (A->val_ff && A->fblk) cand.push_back({HZ_SPMV_FF_FLAT, 0});
     if (A->col_pad) cand.push_back({HZ_SPMV_FF_TMA, 0});
-    float best = 1e30f;
+    float best = 1e30f, best_cv = 1e30f;   // over all kinds; over the binary64 CSR-vector groups
+    int group_cv = A->group;
     MatView<double2> V = mat_view<double2>(A);
     EpiStore<double2> epi{y};
     hz_status st = HZ_OK;
@@ -273,12 +274,20 @@ static hz_status autotune(hz_mat *A, cudaStream_t s) {
         }
         if (st != HZ_OK) break;
         std::sort(tms, tms + 5);
+        if (c.first == HZ_SPMV_CSR_VECTOR && tms[2] < best_cv) {
+            best_cv = tms[2];
+            group_cv = c.second;
+        }
         if (tms[2] < best) {
             best = tms[2];
             A->spmv_kind = c.first;
-            if (c.first != HZ_SPMV_SELL) A->group = c.second;
+            if (c.first == HZ_SPMV_CSR_VECTOR || c.first == HZ_SPMV_FF) A->group = c.second;
         }
     }
+    // the lanes per row of the fastest binary64 CSR-vector product: the row
+    // tile of this matrix's items in the persistent batched solver (and of
+    // the CSR-vector kinds), whichever kind won overall
+    if (A->spmv_kind != HZ_SPMV_FF) A->group = group_cv;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(x);

@@ -278,11 +278,13 @@ def zsolve(A: Matrix, b, x=None, tol=1e-10, maxit=2000, mode="fp64", hist=None,
     return x, _info(info)
 
 
-def zsolve_batched(mats, bs, xs=None, tol=1e-10, maxit=2000):
+def zsolve_batched(mats, bs, xs=None, tol=1e-10, maxit=2000, mode="fp64"):
     """Solve A[s] x[s] = b[s] for every s in one persistent launch.
 
     xs (optional) hold the starting guesses (zero if omitted) and receive the
-    solutions.  Returns (xs, [SolveInfo])."""
+    solutions; mode "fp64" (BiCGStab) or "mixed" (complex64 inner BiCGStab
+    with binary64 refinement per system; maxit caps each system's inner
+    iterations in total).  Returns (xs, [SolveInfo])."""
     ns = len(mats)
     if xs is None:
         xs = [torch.zeros_like(b) for b in bs]
@@ -290,7 +292,10 @@ def zsolve_batched(mats, bs, xs=None, tol=1e-10, maxit=2000):
     arrB = (C.c_void_p * ns)(*[_vec(b, name="b").data_ptr() for b in bs])
     arrX = (C.c_void_p * ns)(*[_vec(x, name="x").data_ptr() for x in xs])
     infos = (hz_info * ns)()
-    check(_L.hz_zsolve_batched(ns, arrA, arrB, arrX, float(tol), int(maxit), HZ_MODE_FP64, infos,
+    if mode not in ("fp64", "mixed"):
+        raise ValueError("mode must be 'fp64' or 'mixed'")
+    md = HZ_MODE_MIXED if mode == "mixed" else HZ_MODE_FP64
+    check(_L.hz_zsolve_batched(ns, arrA, arrB, arrX, float(tol), int(maxit), md, infos,
                                _stream()), allow=_lib.SOLVE_OUTCOMES)
     return xs, [_info(i) for i in infos]
 

@@ -351,6 +351,44 @@ def test_batched_uneven_systems(hz, oracle, ff):
         assert abs(infos[k].iters - io.iters) <= max(5, 0.05 * io.iters), (k, infos[k].iters, io.iters)
 
 
+def test_batched_mixed_uneven_systems(hz, oracle):
+    """The mixed-precision batch (complex64 inner BiCGStab, binary64
+    refinement, each system at its own stage) against the oracle's
+    refinement: FD boxes of three sizes at two wavenumbers, a right-hand
+    side of zeros, a nonzero start, and the refinement to 1e-17 that cannot
+    converge (the batch must stop it at its best iterate like the oracle)."""
+    systems = [W.fd_helmholtz_box(m, kh=kh, damping=0.05) for m in (6, 11, 16) for kh in (0.3, 0.5)]
+    bs = [K.vectors(A.n, 4200 + s)[0] for s, A in enumerate(systems)]
+    A1, b1, _ = W.c1_small_fd()
+    systems += [A1, A1]
+    bs += [b1, np.zeros(A1.n, np.complex128)]
+    mats = [hz.Matrix.from_csr(A, c64=True) for A in systems]
+    x0s = [torch.zeros(A.n, dtype=torch.complex128, device="cuda") for A in systems]
+    x0_2 = K.vectors(systems[2].n, 4300)[0]
+    x0s[2] = dev(x0_2)
+    x0s[-1] = dev(K.vectors(A1.n, 4301)[0])   # b = 0: the answer is x = 0 whatever x0 is
+    xs, infos = hz.zsolve_batched(mats, [dev(b) for b in bs], xs=x0s, tol=1e-10, maxit=20000, mode="mixed")
+    for k, (A, b, x, info) in enumerate(zip(systems, bs, xs, infos)):
+        xg = host(x)
+        if k == len(systems) - 1:
+            assert info.status == 0 and not xg.any()
+            continue
+        xm, dm = oracle.refine_mixed(A, b, x0=x0_2 if k == 2 else None, tol=1e-10)
+        assert info.status == dm["status"], (k, info, dm)
+        if dm["status"] == 0:
+            assert true_relres(oracle, A, xg, b) <= 1e-10
+            assert np.linalg.norm(xg - xm) / np.linalg.norm(xm) <= 1e-8
+            assert info.outer >= 1
+    # refinement below binary64 rounding stops at the best iterate
+    xs, infos = hz.zsolve_batched([mats[-2]], [dev(b1)], tol=1e-17, maxit=20000, mode="mixed")
+    xm, dm = oracle.refine_mixed(A1, b1, tol=1e-17, max_outer=50)
+    xg = host(xs[0])
+    r = true_relres(oracle, A1, xg, b1)
+    assert infos[0].status == 4 and dm["status"] == 4 and 2 <= infos[0].outer < 50
+    assert abs(r - infos[0].relres_rec) <= 2e-15 and abs(r - infos[0].relres_true) <= 2e-15
+    assert np.linalg.norm(xg - xm) / np.linalg.norm(xm) <= 1e-10
+
+
 def test_batched_edge_cases(hz, oracle):
     A, b, _ = W.c1_small_fd()
     M = hz.Matrix.from_csr(A)
@@ -371,6 +409,60 @@ def _loss_and_grad_dense(L, kappa2, theta, b, idx, d):
     # dL/dA_ii = -lambda_i conj(x_i) and dA_ii/dtheta_i = -kappa2 (holomorphic)
     grad_theta = kappa2 * lam * np.conj(x)
     return loss, grad_theta
+
+
+def test_adjoint_gradient_c5_largest_converging_grid(hz):
+    """The C5 inverse problem on the largest grid where a Krylov forward solve
+    reaches 1e-12 (32^3, n = 32768, TFQMR for the forward and the adjoint
+    solve; at 40^3 and 64^3 none of the methods does, see the design notes):
+    the gradient against the one of a sparse direct factorisation (1e-6), and
+    central differences of the loss along the 20 seeded directions at step
+    1e-6 (1e-5 relative).  The perturbed losses are exact solves too: each
+    refines A(theta +- eps v) x = b with the factorisation of A(theta)."""
+    import scipy.sparse.linalg as spla
+    m = 32
+    prob = W.c5_inverse_problem(m=m, nsample=512)
+    L, kappa2, theta, b = prob["L"], prob["kappa2"], prob["theta"], prob["b"]
+    idx, d = prob["sample_idx"], prob["data"]
+    n = L.n
+    M = hz.Matrix.from_csr(prob["A"])
+    base = dev(L.to_scipy().diagonal().astype(np.complex128))
+    th = dev(theta).requires_grad_(True)
+    x = hz.solve_diag_param(th, dev(b), M, base, -kappa2, tol=1e-12, maxit=8000, method="tfqmr")
+    loss = torch.sum(torch.abs(x[dev(idx)] - dev(d)) ** 2)
+    loss.backward()
+    g_gpu = host(th.grad)
+    Ls = L.to_scipy().tocsc()
+
+    def op(t):
+        return (Ls - kappa2 * sp.diags(t)).tocsc()
+
+    lu = spla.splu(op(theta))
+    x_lu = lu.solve(b)
+    loss_lu = float(np.sum(np.abs(x_lu[idx] - d) ** 2))
+    gx = np.zeros(n, np.complex128)
+    gx[idx] = 2 * (x_lu[idx] - d)
+    lam = lu.solve(gx, trans="H")                       # A^H lambda = g
+    g_lu = kappa2 * lam * np.conj(x_lu)                  # dA_ii / dtheta_i = -kappa2
+    assert abs(float(loss) - loss_lu) <= 1e-9 * loss_lu
+    assert np.linalg.norm(g_gpu - g_lu) <= 1e-6 * np.linalg.norm(g_lu)
+
+    def loss_at(t):
+        At = op(t)
+        xt = x_lu.copy()
+        for _ in range(10):                              # refinement with the factorisation of A(theta)
+            r = b - At @ xt
+            if np.linalg.norm(r) <= 1e-13 * np.linalg.norm(b):
+                break
+            xt = xt + lu.solve(r)
+        return float(np.sum(np.abs(xt[idx] - d) ** 2))
+
+    eps = 1e-6
+    for v in W.c5_directions(n, count=20):
+        fd = (loss_at(theta + eps * v) - loss_at(theta - eps * v)) / (2 * eps)
+        an = float(np.real(np.vdot(g_gpu, v)))
+        assert abs(fd - an) <= 1e-5 * max(abs(fd), 1e-12), (fd, an)
+    M.close()
 
 
 def test_outer_on_pattern_and_diag_grad(hz, oracle):

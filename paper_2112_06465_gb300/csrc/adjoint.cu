@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(256) k_outer_pattern(int n, const int *__restr
 // walks the block's row pointers (shared memory) forward to the row of its
 // next entry.
 constexpr int kOpThreads = 128;
+constexpr int kOpGroup = 8;
 __global__ void __launch_bounds__(kOpThreads) k_outer_flat(int nfblk, const int *__restrict__ fblk,
                                                            const int *__restrict__ fblk_k,
                                                            const int *__restrict__ rowptr,
@@ -60,14 +61,29 @@ __global__ void __launch_bounds__(kOpThreads) k_outer_flat(int nfblk, const int 
         if (lane == 0) rp[nr] = ke;
         __syncwarp();
         int j = 0;   // row (offset in the block) of this lane's current entry
-        double2 m = make_double2(0.0, 0.0);
-        int mrow = -1;
-        for (int k = kb + lane; k < ke; k += 32) {
-            while (j < nr - 1 && rp[j + 1] <= k) ++j;
-            if (j != mrow) { m = __ldg(mu + r0 + j); mrow = j; }
-            const double2 xj = __ldg(x + __ldg(col + k));
-            const double2 p = cmul(m, xj);
-            g[k] = make_double2(-p.x, p.y);
+        // kOpGroup entries per lane at a time: their column loads, x gathers
+        // and mu loads are all issued before the first product
+        for (int k0 = kb + lane; k0 < ke; k0 += 32 * kOpGroup) {
+            int c[kOpGroup];
+            double2 xv[kOpGroup], m[kOpGroup];
+#pragma unroll
+            for (int u = 0; u < kOpGroup; ++u) {
+                const int k = k0 + 32 * u;
+                c[u] = k < ke ? __ldg(col + k) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kOpGroup; ++u) {
+                const int k = k0 + 32 * u;
+                while (j < nr - 1 && rp[j + 1] <= k) ++j;
+                m[u] = c[u] >= 0 ? __ldg(mu + r0 + j) : make_double2(0.0, 0.0);
+                xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < kOpGroup; ++u) {
+                if (c[u] < 0) continue;
+                const double2 p = cmul(m[u], xv[u]);
+                g[k0 + 32 * u] = make_double2(-p.x, p.y);
+            }
         }
         __syncwarp();
     }

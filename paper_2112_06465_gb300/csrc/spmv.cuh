@@ -713,6 +713,13 @@ __device__ __forceinline__ void flat_rows_ff_tma(const MatView<double2> &A, cons
 // added in that order (storage order of the entries).  Row blocks are those
 // of the block-flat double-float kernel (<= 32 complete rows and <= 512
 // entries, or one longer row), so phase 2 is one row per lane.
+//
+// Helmholtz operators with a real wavenumber are real away from their
+// impedance boundary (stiffness and mass entries); where a whole group of a
+// warp (kD64Group entries per lane) holds values with zero imaginary parts
+// and finite x, the group takes two FMAs per entry instead of four.  The
+// skipped terms are exact zeros, so the sums are the same numbers (up to
+// the sign of a zero result).
 struct alignas(16) D64Seg {
     double2 head[32];   // lane l: its first run when that run's row began in an earlier lane
     double2 tail[32];   // lane l: its last run when that run's row continues in a later lane
@@ -727,6 +734,11 @@ constexpr int kD64Group = HZ_D64_GROUP;   // entries per lane whose loads are in
 #define HZ_D64_MIN_BLOCKS 4
 #endif
 constexpr int kD64MinBlocks = HZ_D64_MIN_BLOCKS;   // resident CTAs per SM asked of the register allocator
+
+// both parts finite (exponent field not all ones), by the bit pattern
+__device__ __forceinline__ bool finite2(double2 v) {
+    return ((__double2hiint(v.x) & 0x7ff00000) != 0x7ff00000) && ((__double2hiint(v.y) & 0x7ff00000) != 0x7ff00000);
+}
 
 __device__ __forceinline__ double2 ld_stream_l1(const double2 *ptr, uint64_t pol) {
     double2 v;
@@ -792,20 +804,36 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
             }
 #pragma unroll
             for (int u = 0; u < kD64Group; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_double2(0.0, 0.0);
+            // a group of the warp whose values all have a zero imaginary part
+            // (and whose gathered x are finite) needs two FMAs per entry, not
+            // four: the terms -Im(a) Im(x) and Im(a) Re(x) are exact zeros
+            bool real = true;
 #pragma unroll
-            for (int u = 0; u < kD64Group; ++u) {
-                const int k = k0 + u;
-                if (k < c1) {
-                    while (k == nxt && j < nr - 1) {   // row j ends before entry k
-                        flush(j, seg0, k);
-                        ++j;
-                        nxt = sg->rp[j + 1];
-                        s = make_double2(0.0, 0.0);
-                        seg0 = k;
+            for (int u = 0; u < kD64Group; ++u) real = real && a[u].y == 0.0 && finite2(v[u]);
+            const bool all_real = __all_sync(0xffffffffu, real);
+            auto run = [&](auto real_tag) {
+#pragma unroll
+                for (int u = 0; u < kD64Group; ++u) {
+                    const int k = k0 + u;
+                    if (k < c1) {
+                        while (k == nxt && j < nr - 1) {   // row j ends before entry k
+                            flush(j, seg0, k);
+                            ++j;
+                            nxt = sg->rp[j + 1];
+                            s = make_double2(0.0, 0.0);
+                            seg0 = k;
+                        }
+                        if constexpr (decltype(real_tag)::value) {
+                            s.x = fma(a[u].x, v[u].x, s.x);
+                            s.y = fma(a[u].x, v[u].y, s.y);
+                        } else {
+                            cmac(s, a[u], v[u]);
+                        }
                     }
-                    cmac(s, a[u], v[u]);
                 }
-            }
+            };
+            if (all_real) run(std::true_type{});
+            else run(std::false_type{});
         }
         if (c0 < c1) flush(j, seg0, c1);
         __syncwarp();

@@ -126,6 +126,37 @@ def test_spmv_hexcar(hz, oracle):
         M.close()
 
 
+def test_spmv_real_valued_groups_and_nonfinite_x(hz, oracle):
+    """The binary64 block-flat kernel takes two FMAs per entry where a whole
+    group of a warp holds real values: a real matrix with a band of complex
+    rows gives the same products as the oracle at the binary64 bound, and
+    an infinite or NaN entry of x propagates as in binary64 arithmetic
+    (0 * inf = NaN in the rows that touch it)."""
+    A = K.random_csr(4000, 81, max_row=20)
+    val = A.val.real.astype(np.complex128)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    band = (rows >= 1500) & (rows < 1600)
+    val[band] = A.val[band]                                   # complex values in 100 rows only
+    Ar = W.CSR(A.n, A.rowptr, A.col, val)
+    x = K.vectors(A.n, 82)[0]
+    check_spmv(hz, oracle, Ar, x, [("flat64", 0), ("csr", 4)])
+    xb = x.copy()
+    xb[17] = complex(np.inf, 1.0)
+    xb[2900] = complex(0.5, np.nan)
+    M = hz.Matrix.from_csr(Ar)
+    y = host(hz.zspmv(M, dev(xb)))
+    ref = oracle.zspmv(Ar, xb)
+    assert np.array_equal(np.isnan(y.real), np.isnan(ref.real))
+    assert np.array_equal(np.isnan(y.imag), np.isnan(ref.imag))
+    assert np.array_equal(np.isinf(y.real), np.isinf(ref.real))
+    ok = np.isfinite(ref)
+    m = np.diff(Ar.rowptr).astype(np.float64)
+    xf = np.where(np.isfinite(xb), xb, 0)
+    bound = (2 * m + 2) * 2.0 ** -52 * K.row_abs_scale(Ar, xf)
+    assert np.all(np.abs(y[ok] - ref[ok]) <= bound[ok])
+    M.close()
+
+
 def test_spmv_wide_band_fallback(hz, oracle):
     """Wide bands: random columns anywhere in a 70000-row matrix, and a band
     whose entries sit 32768 columns left of the diagonal."""

@@ -255,6 +255,63 @@ def run_spmv_only(args):
                       "n": A.n, "nnz": A.nnz}))
 
 
+def run_kernel_case(args):
+    """Profiling aid: one small case per kernel family, for ncu captures
+    (nothing is timed).  spmv / cspmv: three C2 products (--arith picks
+    binary64 or double-float); blas: zdotc, zaxpy, zscal, dznrm2 at 1e8
+    elements, twice; outer: the adjoint outer product on C5 64^3, three
+    times; batched: a four-box binary64 sweep, 100 iterations, twice; solve:
+    two C2 solves of HZ_PROFILE_UNROLL iterations (set HZ_PROFILE_UNROLL=k so
+    the iteration kernels are plain graph nodes)."""
+    import numpy as np
+    import torch
+    import paper_2112_06465_gb300 as hz
+    import workloads as W
+    dev = torch.device("cuda")
+    case = args.kernel_case
+    if case in ("spmv", "cspmv", "solve"):
+        A, b = build_workload()
+        M = hz.Matrix.from_csr(A, ff=args.arith == "ff", c64=case == "cspmv")
+        if case == "cspmv":
+            x = torch.randn(A.n, dtype=torch.complex64, device=dev)
+            for _ in range(3):
+                hz.cspmv(M, x)
+        elif case == "spmv":
+            x = torch.randn(A.n, dtype=torch.complex128, device=dev)
+            for _ in range(3):
+                hz.zspmv(M, x)
+        else:
+            bd = torch.as_tensor(b).to(dev)
+            k = int(os.environ.get("HZ_PROFILE_UNROLL", "3"))
+            for _ in range(2):
+                hz.zsolve(M, bd, tol=1e-10, maxit=k)
+    elif case == "blas":
+        n = 100_000_000
+        x = torch.randn(n, dtype=torch.complex128, device=dev)
+        y = torch.randn(n, dtype=torch.complex128, device=dev)
+        a = torch.tensor([0.5 - 0.25j], dtype=torch.complex128, device=dev)
+        for _ in range(2):
+            hz.zdotc(x, y)
+            hz.zaxpy(a, x, y)
+            hz.zscal(a, x)
+            hz.dznrm2(x)
+    elif case == "outer":
+        A = W.c5_inverse_problem()["A"]
+        M = hz.Matrix.from_csr(A)
+        mu = torch.randn(A.n, dtype=torch.complex128, device=dev)
+        x = torch.randn(A.n, dtype=torch.complex128, device=dev)
+        for _ in range(3):
+            hz.outer_on_pattern(M, mu, x)
+    elif case == "batched":
+        systems = [W.fd_helmholtz_box(m, kh=0.3, damping=0.05) for m in (24, 32, 40, 48)]
+        mats = [hz.Matrix.from_csr(A) for A in systems]
+        bs = [torch.ones(A.n, dtype=torch.complex128, device=dev) for A in systems]
+        for _ in range(2):
+            hz.zsolve_batched(mats, bs, tol=1e-10, maxit=100)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": case, "arith": args.arith}))
+
+
 def compare_modes(hz, torch, full_c4, maxit):
     """Mixed precision and the batched sweep against the plain complex128
     solver on the C4 frequency-sweep systems, each to relative residual 1e-10.
@@ -665,6 +722,8 @@ def main():
     ap.add_argument("--spmv-only", action="store_true",
                     help="profiling aid: build C2, run three SpMV launches of the chosen "
                          "arithmetic (--arith, --group) and exit without timing")
+    ap.add_argument("--kernel-case", default=None, choices=["spmv", "cspmv", "blas", "outer", "batched", "solve"],
+                    help="profiling aid: run one small case of a kernel family and exit (see run_kernel_case)")
     ap.add_argument("--group", type=int, default=4, help="lanes per row of the CSR-vector kinds")
     ap.add_argument("--spmv", default=None, choices=["csr", "sell", "ff", "sellff", "ffflat", "fftma"],
                     help="force an SpMV variant (default: the handle's own choice)")
@@ -673,6 +732,8 @@ def main():
         return run_reference(args)
     if args.spmv_only:
         return run_spmv_only(args)
+    if args.kernel_case:
+        return run_kernel_case(args)
 
     import torch
     import torch.distributed as dist

@@ -152,8 +152,11 @@ typedef struct {
  * hz_mat_set_diag); with index_base == 1 it keeps 0-based copies it owns.
  * SELL-C-sigma and complex64 copies (flags) are owned by the handle.
  * Synchronises `stream` once (row statistics are computed on the host).
+ * d_val must be 16-byte aligned (any complex128 allocation is), d_col and
+ * d_rowptr 4-byte aligned.
  * Errors: HZ_ERR_ARG for n < 0, nnz < 0, null pointers with nonzero sizes,
- * index_base not 0/1, or (with HZ_FLAG_VALIDATE) a malformed CSR.
+ * misaligned arrays, index_base not 0/1, or (with HZ_FLAG_VALIDATE) a
+ * malformed CSR.
  */
 HZ_API hz_status hz_csr_create(hz_mat **A, int32_t n, int32_t nnz, const int32_t *d_rowptr,
                                const int32_t *d_col, const hz_z *d_val, int32_t index_base,
@@ -196,7 +199,7 @@ HZ_API hz_status hz_mat_refresh_values(hz_mat *A, void *stream);
 
 /*
  * y = A x (Section 6, CSR matrix-vector product), complex128.
- * d_x and d_y have n entries and must not overlap.  On the double-float
+ * d_x and d_y have n entries, are 16-byte aligned and must not overlap.  On the double-float
  * variants (HZ_SPMV_FF, HZ_SPMV_SELL_FF, HZ_SPMV_FF_FLAT, HZ_SPMV_FF_TMA)
  * the handle's own x scratch holds
  * the split of d_x, so calls on one handle must not overlap in time

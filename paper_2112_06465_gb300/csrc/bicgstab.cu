@@ -12,7 +12,8 @@
 // Each reduction's last block also does the scalar work (alpha, omega, beta,
 // stopping and breakdown tests), so the scalars never leave the device.  The
 // iteration is one CUDA graph: init -> WHILE(conditional node){F1..F5} ->
-// true residual -> copy-out -> info readback; F5 sets the loop condition.
+// true residual -> copy-out -> info readback; the loop guard after F5 sets
+// the loop condition (no kernel of the body but the guard touches it).
 //
 // The kernels are written once over the vector element type (arith.cuh):
 // complex128 in binary64 (HZ_SPMV_CSR_VECTOR / HZ_SPMV_SELL handles),
@@ -148,15 +149,11 @@ __global__ void __launch_bounds__(kVecBlock, 2) k_bicg_xr(int n, StateOf<V> *st,
                                                        V *__restrict__ r, const V *__restrict__ rh,
                                                        const V *__restrict__ p, const V *__restrict__ s,
                                                        const V *__restrict__ t, const int *total_iters,
-                                                       RedScratch red, cudaGraphConditionalHandle h,
-                                                       int outer_level) {
+                                                       RedScratch red, int outer_level) {
     using A = Ar<V>;
     pdl_wait();
     pdl_release();
-    if (st->done) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(h, 0);
-        return;
-    }
+    if (st->done) return;
     const typename A::S alpha = A::scal(st->alpha);
     if (st->half) {   // half-step exit: x += alpha p, r = s
         vec_tiles(n, [&](int i) {
@@ -167,7 +164,6 @@ __global__ void __launch_bounds__(kVecBlock, 2) k_bicg_xr(int n, StateOf<V> *st,
             st->status = HZ_OK;
             st->done = 1;
             if (outer_level && ctl->hist) ctl->hist[st->iter] = st->rel;
-            set_cond(h, 0);
         }
         return;
     }
@@ -204,7 +200,6 @@ __global__ void __launch_bounds__(kVecBlock, 2) k_bicg_xr(int n, StateOf<V> *st,
             st->rho_old = st->rho;
             st->rho = rn;
         }
-        set_cond(h, st->done ? 0 : 1);
     }
 }
 
@@ -518,7 +513,7 @@ static void spmv_on(const Solver *S, const hz_mat *A, const V *x, const Epi &e, 
 
 template <class V>
 static void launch_iteration(const Solver *S, const hz_mat *A, StateOf<V> *st, V *x, V *r, V *rh, V *p, V *v, V *s,
-                             V *t, int *total, cudaGraphConditionalHandle h, int outer_level, cudaStream_t cs) {
+                             V *t, int *total, int outer_level, cudaStream_t cs) {
     // with S->pdl, F2..F5 are launched as programmatic dependents of their
     // predecessor: each kernel's CTAs may be scheduled while the previous one
     // drains and wait in pdl_wait() for its results
@@ -534,7 +529,7 @@ static void launch_iteration(const Solver *S, const hz_mat *A, StateOf<V> *st, V
     e4.st = st; e4.t = t; e4.s = s; e4.sc = S->op_scale;
     spmv_on<V>(S, A, s, e4, cs, pdl);
     launch_k(pdl, k_bicg_xr<V>, S->grid_vec, kVecBlock, cs, n, st, (const Ctl *)S->dctl, x, r, rh, p, s, t,
-             (const int *)total, S->red, h, outer_level);
+             (const int *)total, S->red, outer_level);
 }
 
 // FP64-mode graph: start -> WHILE{F1..F5} -> true residual, copy-out, info
@@ -564,7 +559,7 @@ static hz_status build_fp64_graph(Solver *S, const hz_mat *A, cudaGraph_t g) {
     ei.st = st; ei.info = S->dinfo; ei.ctl = S->dctl; ei.r = r; ei.rh = rh; ei.p = p; ei.v = v; ei.h = h;
     spmv_on<V>(S, A, x, ei, cs);
     if (unroll > 0) {
-        for (int k = 0; k < unroll; ++k) launch_iteration<V>(S, A, st, x, r, rh, p, v, s, t, nullptr, 0, 1, cs);
+        for (int k = 0; k < unroll; ++k) launch_iteration<V>(S, A, st, x, r, rh, p, v, s, t, nullptr, 1, cs);
     } else {
         HZ_TRY(capture_leaves(cs, &leaves));
         HZ_CUDA(cudaStreamEndCapture(cs, &g));
@@ -572,7 +567,7 @@ static hz_status build_fp64_graph(Solver *S, const hz_mat *A, cudaGraph_t g) {
         cudaGraph_t body;
         HZ_TRY(add_while(g, leaves, h, &wn, &body));
         HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
-        launch_iteration<V>(S, A, st, x, r, rh, p, v, s, t, nullptr, h, 1, cs);
+        launch_iteration<V>(S, A, st, x, r, rh, p, v, s, t, nullptr, 1, cs);
         k_loop_guard<typename Ar<V>::St><<<1, 1, 0, cs>>>(st, S->dctl, 1, h);
         HZ_CUDA(cudaStreamEndCapture(cs, &body));
         HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, &wn, nullptr, 1, mode));
@@ -616,8 +611,8 @@ static hz_status build_mixed_graph(Solver *S, const hz_mat *A, cudaGraph_t g) {
     cudaGraph_t ibody;
     HZ_TRY(add_while(obody, leaves, hi, &wi, &ibody));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, ibody, nullptr, nullptr, 0, mode));
-    launch_iteration<float2>(S, A, S->st32, S->d32, S->r32, S->rh32, S->p32, S->v32, S->s32, S->t32, S->total, hi,
-                             0, cs);
+    launch_iteration<float2>(S, A, S->st32, S->d32, S->r32, S->rh32, S->p32, S->v32, S->s32, S->t32, S->total, 0,
+                             cs);
     k_loop_guard<float2><<<1, 1, 0, cs>>>(S->st32, S->dctl, 0, hi);
     HZ_CUDA(cudaStreamEndCapture(cs, &ibody));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, obody, &wi, nullptr, 1, mode));

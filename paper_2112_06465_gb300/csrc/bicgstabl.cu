@@ -354,13 +354,9 @@ __global__ void __launch_bounds__(kVecBlock) k_bl_gram(int n, int ell, StateOf<V
 template <class V>
 __global__ void __launch_bounds__(kVecBlock) k_bl_update(int n, int ell, StateOf<V> *st, const Ctl *ctl,
                                                          V *__restrict__ X, V *__restrict__ R, V *__restrict__ U,
-                                                         const V *__restrict__ rh, const BlExtra *ex, RedScratch red,
-                                                         cudaGraphConditionalHandle h) {
+                                                         const V *__restrict__ rh, const BlExtra *ex, RedScratch red) {
     using A = Ar<V>;
-    if (st->done) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(h, 0);
-        return;
-    }
+    if (st->done) return;
     typename A::S g[kMaxEll + 1];
     for (int j = 1; j <= ell; ++j) g[j] = A::scal(ex->g[j]);
     typename A::Acc acc[3];
@@ -398,7 +394,6 @@ __global__ void __launch_bounds__(kVecBlock) k_bl_update(int n, int ell, StateOf
                 st->rho = rho1;
             }
         }
-        set_cond(h, st->done ? 0 : 1);
     }
 }
 
@@ -478,7 +473,7 @@ static hz_status bl_build_graph(BlSolver *S, const hz_mat *A, cudaGraph_t g) {
         bl_spmv<V>(S, A, Rv(j), er, cs);
     }
     k_bl_gram<V><<<S->grid_gram, kVecBlock, 0, cs>>>(n, ell, st, R, S->red, S->ex);
-    k_bl_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, ell, st, S->dctl, x, R, U, rh, S->ex, S->red, h);
+    k_bl_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, ell, st, S->dctl, x, R, U, rh, S->ex, S->red);
     k_loop_guard<typename Ar<V>::St><<<1, 1, 0, cs>>>(st, S->dctl, 1, h);
     HZ_CUDA(cudaStreamEndCapture(cs, &body));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, &wn, nullptr, 1, mode));

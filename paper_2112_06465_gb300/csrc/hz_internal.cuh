@@ -397,18 +397,63 @@ struct RedScratch {
     unsigned int *counter;     // one counter, zero between kernels
 };
 
+// Warp sums of NV values per lane.  For 2..4 values the first one or two
+// butterfly levels split the values between the two halves of each exchange
+// (each lane keeps the half it adds and sends the other), so a warp does 5
+// (NV = 2) or 6 (NV = 3, 4) additions per lane instead of 5 NV; the total of
+// value q ends in lane q * (32 / P), P = NV rounded up to a power of two.
+// (On GB300 a binary64 addition occupies the binary64 pipe for a whole warp
+// instruction, so the solver's three-value reductions save nine of fifteen.)
+template <class R, int NV>
+__device__ __forceinline__ void warp_sum_split(R (&v)[NV], R &out) {
+    const int lane = threadIdx.x & 31;
+    if constexpr (NV == 1) {
+        out = v[0];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) out += __shfl_xor_sync(0xffffffffu, out, off);
+    } else if constexpr (NV == 2) {
+        const bool hi = lane & 16;
+        R t = (hi ? v[1] : v[0]) + __shfl_xor_sync(0xffffffffu, hi ? v[0] : v[1], 16);
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        out = t;
+    } else {
+        static_assert(NV <= 4, "warp_sum_split takes at most four values");
+        R w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = q < NV ? v[q] : R(0);
+        const bool h16 = lane & 16, h8 = lane & 8;
+        // level 16: keep values {0,1} (low half) or {2,3} (high half)
+        const R k0 = (h16 ? w[2] : w[0]) + __shfl_xor_sync(0xffffffffu, h16 ? w[0] : w[2], 16);
+        const R k1 = (h16 ? w[3] : w[1]) + __shfl_xor_sync(0xffffffffu, h16 ? w[1] : w[3], 16);
+        // level 8: keep the first or the second of the two
+        R t = (h8 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        out = t;
+    }
+}
+
 template <class R, int NV>
 __device__ __forceinline__ void block_sum(R (&v)[NV], R (*sh)[NV]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = (blockDim.x + 31) >> 5;
+    if constexpr (NV <= 4) {
+        R t;
+        warp_sum_split<R, NV>(v, t);
+        constexpr int P = NV == 1 ? 1 : NV == 2 ? 2 : 4;
+        const int q = lane / (32 / P);
+        if (q < NV && lane % (32 / P) == 0) sh[warp][q] = t;
+    } else {
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
+        for (int j = 0; j < NV; ++j) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
-    }
-    if (lane == 0) {
+            for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
+        }
+        if (lane == 0) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) sh[warp][j] = v[j];
+            for (int j = 0; j < NV; ++j) sh[warp][j] = v[j];
+        }
     }
     __syncthreads();
     if (warp == 0) {

@@ -119,7 +119,9 @@ int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap) {
             }
             if (e != cudaSuccess || occ < 1) occ = 1;
         }
-        int64_t g = std::min<int64_t>(kind == HZ_SPMV_FF_TMA ? A->nfblk_t : A->nfblk, (int64_t)d.num_sms * occ);
+        const int wpc = kFlatThreads / 32;
+        int64_t g = std::min<int64_t>(((kind == HZ_SPMV_FF_TMA ? A->nfblk_t : A->nfblk) + wpc - 1) / wpc,
+                                      (int64_t)d.num_sms * occ);
         return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
     }
     const bool sell = kind == HZ_SPMV_SELL || kind == HZ_SPMV_SELL_FF;
@@ -311,6 +313,9 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
     HZ_CHECK(index_base == 0 || index_base == 1, "hz_csr_create: index_base must be 0 or 1");
     HZ_CHECK(d_rowptr != nullptr, "hz_csr_create: null rowptr");
     HZ_CHECK(nnz == 0 || (d_col != nullptr && d_val != nullptr), "hz_csr_create: null col/val");
+    // the kernels read values with 16-byte vector loads and copies
+    HZ_CHECK(((uintptr_t)d_val & 15u) == 0 && ((uintptr_t)d_col & 3u) == 0 && ((uintptr_t)d_rowptr & 3u) == 0,
+             "hz_csr_create: d_val must be 16-byte aligned, d_col and d_rowptr 4-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     hz_mat *A = new hz_mat();
     int dev = 0;
@@ -550,6 +555,7 @@ extern "C" HZ_API hz_status hz_zspmv(const hz_mat *A, const hz_z *d_x, hz_z *d_y
     if (A->n == 0) return HZ_OK;
     HZ_CHECK(d_x && d_y, "hz_zspmv: null vector");
     HZ_CHECK((const void *)d_x != (const void *)d_y, "hz_zspmv: x and y must not alias");
+    HZ_CHECK((((uintptr_t)d_x | (uintptr_t)d_y) & 15u) == 0, "hz_zspmv: x and y must be 16-byte aligned");
     const int grid = spmv_grid(A, A->spmv_kind, A->group);
     EpiStore<double2> epi{(double2 *)d_y};
     if (is_ff_kind(A->spmv_kind)) {

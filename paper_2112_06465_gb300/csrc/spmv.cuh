@@ -716,10 +716,11 @@ __device__ __forceinline__ void flat_rows_ff_tma(const MatView<double2> &A, cons
 //
 // Helmholtz operators with a real wavenumber are real away from their
 // impedance boundary (stiffness and mass entries); where a whole group of a
-// warp (kD64Group entries per lane) holds values with zero imaginary parts
-// and finite x, the group takes two FMAs per entry instead of four.  The
-// skipped terms are exact zeros, so the sums are the same numbers (up to
-// the sign of a zero result).
+// warp (kD64Group entries per lane) holds values with zero imaginary parts,
+// the group takes two FMAs per entry instead of four.  The skipped terms are
+// exact zeros for finite x, so the sums are the same numbers (up to the sign
+// of a zero result); an infinite or NaN x turns the skipped 0 * x into NaN,
+// which the lane applies to its partial sum when it flushes the run.
 struct alignas(16) D64Seg {
     double2 head[32];   // lane l: its first run when that run's row began in an earlier lane
     double2 tail[32];   // lane l: its last run when that run's row continues in a later lane
@@ -734,11 +735,23 @@ constexpr int kD64Group = HZ_D64_GROUP;   // entries per lane whose loads are in
 #define HZ_D64_MIN_BLOCKS 4
 #endif
 constexpr int kD64MinBlocks = HZ_D64_MIN_BLOCKS;   // resident CTAs per SM asked of the register allocator
+#ifndef HZ_D64_TWO_ACC
+#define HZ_D64_TWO_ACC 1
+#endif
+constexpr bool kD64TwoAcc = HZ_D64_TWO_ACC != 0;   // even / odd entries of a group in two accumulators
+#ifndef HZ_D64_REAL_GROUPS
+#define HZ_D64_REAL_GROUPS 1
+#endif
+constexpr bool kD64RealGroups = HZ_D64_REAL_GROUPS != 0;   // two FMAs per entry for real-valued groups
 
-// both parts finite (exponent field not all ones), by the bit pattern
-__device__ __forceinline__ bool finite2(double2 v) {
-    return ((__double2hiint(v.x) & 0x7ff00000) != 0x7ff00000) && ((__double2hiint(v.y) & 0x7ff00000) != 0x7ff00000);
+// a zero imaginary part (+0 or -0), by the bit pattern (integer pipe; a
+// binary64 compare would occupy the binary64 pipe like an FMA)
+__device__ __forceinline__ bool zero_im(double2 a) {
+    return ((__double2hiint(a.y) & 0x7fffffff) | __double2loint(a.y)) == 0;
 }
+
+// finite (exponent field not all ones), by the bit pattern
+__device__ __forceinline__ bool finite1(double v) { return (__double2hiint(v) & 0x7ff00000) != 0x7ff00000; }
 
 __device__ __forceinline__ double2 ld_stream_l1(const double2 *ptr, uint64_t pol) {
     double2 v;
@@ -784,13 +797,17 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
         }
         int nxt = sg->rp[j + 1];   // first entry of the next row (> c0)
         int seg0 = c0;             // first entry of the current run
-        double2 s = make_double2(0.0, 0.0);
+        double2 s = make_double2(0.0, 0.0), s2 = make_double2(0.0, 0.0);
+        bool nan_re = false, nan_im = false;   // a real group met a non-finite x (see below)
         // a finished run [beg, end) of row jj: a head, a tail, or a whole row
         auto flush = [&](int jj, int beg, int end) {
             if (beg == end) return;
-            if (beg == c0 && sg->rp[jj] < c0) sg->head[lane] = s;
-            else if (end == c1 && sg->rp[jj + 1] > c1) sg->tail[lane] = s;
-            else sg->full[jj] = s;
+            double2 t = cadd(s, s2);
+            if (nan_re) t.x = __longlong_as_double(0x7ff8000000000000ll);
+            if (nan_im) t.y = __longlong_as_double(0x7ff8000000000000ll);
+            if (beg == c0 && sg->rp[jj] < c0) sg->head[lane] = t;
+            else if (end == c1 && sg->rp[jj + 1] > c1) sg->tail[lane] = t;
+            else sg->full[jj] = t;
         };
 #pragma unroll 1
         for (int k0 = c0; k0 < c0 + U; k0 += kD64Group) {
@@ -805,12 +822,13 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
 #pragma unroll
             for (int u = 0; u < kD64Group; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_double2(0.0, 0.0);
             // a group of the warp whose values all have a zero imaginary part
-            // (and whose gathered x are finite) needs two FMAs per entry, not
-            // four: the terms -Im(a) Im(x) and Im(a) Re(x) are exact zeros
+            // needs two FMAs per entry, not four: the terms -Im(a) Im(x) and
+            // Im(a) Re(x) are exact zeros (decided on the values alone, after
+            // the gathers are issued, so neither waits for the other)
             bool real = true;
 #pragma unroll
-            for (int u = 0; u < kD64Group; ++u) real = real && a[u].y == 0.0 && finite2(v[u]);
-            const bool all_real = __all_sync(0xffffffffu, real);
+            for (int u = 0; u < kD64Group; ++u) real = real && zero_im(a[u]);
+            const bool all_real = kD64RealGroups && __all_sync(0xffffffffu, real);
             auto run = [&](auto real_tag) {
 #pragma unroll
                 for (int u = 0; u < kD64Group; ++u) {
@@ -820,14 +838,22 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
                             flush(j, seg0, k);
                             ++j;
                             nxt = sg->rp[j + 1];
-                            s = make_double2(0.0, 0.0);
+                            s = s2 = make_double2(0.0, 0.0);
+                            nan_re = nan_im = false;
                             seg0 = k;
                         }
+                        // even and odd entries of the group go to two
+                        // accumulators: two dependent FMA chains per lane
+                        double2 &q = (kD64TwoAcc && (u & 1)) ? s2 : s;
                         if constexpr (decltype(real_tag)::value) {
-                            s.x = fma(a[u].x, v[u].x, s.x);
-                            s.y = fma(a[u].x, v[u].y, s.y);
+                            q.x = fma(a[u].x, v[u].x, q.x);
+                            q.y = fma(a[u].x, v[u].y, q.y);
+                            // the skipped 0 * Im(x) and 0 * Re(x) are NaN for a
+                            // non-finite x: remembered and applied at the flush
+                            nan_re = nan_re || !finite1(v[u].y);
+                            nan_im = nan_im || !finite1(v[u].x);
                         } else {
-                            cmac(s, a[u], v[u]);
+                            cmac(q, a[u], v[u]);
                         }
                     }
                 }
@@ -858,6 +884,7 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
     }
 }
 
+
 // per-thread accumulators -> one grid total -> epi.finish (last block)
 template <class Epi, int NV>
 __device__ __forceinline__ void spmv_reduce(const Epi &epi, typename Epi::Acc (&acc)[NV], RedScratch red) {
@@ -887,6 +914,7 @@ __global__ void __launch_bounds__(kFlatThreads, kD64MinBlocks) k_spmv_d64b(MatVi
     flat_rows_d64<Epi, NV>(A, x, epi, acc, &seg[threadIdx.x >> 5]);
     if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
 }
+
 
 template <int W, class T, class Epi>
 __global__ void __launch_bounds__(kSpmvBlock) k_spmv(MatView<T> A, const T *__restrict__ x, Epi epi,

@@ -245,8 +245,7 @@ template <class V>
 __global__ void __launch_bounds__(kVecBlock) k_tq_update(int n, StateOf<V> *st, const TqExtra *q, V *__restrict__ d,
                                                          V *__restrict__ x, const V *__restrict__ u2,
                                                          V *__restrict__ u1, const V *__restrict__ w,
-                                                         const V *__restrict__ au, V *__restrict__ v,
-                                                         cudaGraphConditionalHandle h) {
+                                                         const V *__restrict__ au, V *__restrict__ v) {
     using A = Ar<V>;
     if (st->done) return;
     const typename A::S coef = A::scal(q->coef2), eta = A::scal(q->eta2x), beta = A::scal(st->beta);
@@ -260,10 +259,7 @@ __global__ void __launch_bounds__(kVecBlock) k_tq_update(int n, StateOf<V> *st, 
             v[i] = A::axpy(A::zero(), beta, A::axpy(au[i], beta, v[i]));
         }
     });
-    if (stop && blockIdx.x == 0 && threadIdx.x == 0) {
-        st->done = 1;
-        set_cond(h, 0);
-    }
+    if (stop && blockIdx.x == 0 && threadIdx.x == 0) st->done = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -340,7 +336,7 @@ static hz_status tq_build_graph(TqSolver *S, const hz_mat *A, cudaGraph_t g) {
     EpiTqW<V> ew;
     ew.st = st; ew.q = S->q; ew.ctl = S->dctl; ew.au = au; ew.d = d; ew.x = x; ew.w = w; ew.u1 = u1; ew.rh = rh;
     tq_spmv<V>(S, A, u2, ew, cs);
-    k_tq_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->q, d, x, u2, u1, w, au, v, h);
+    k_tq_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->q, d, x, u2, u1, w, au, v);
     tq_spmv<V>(S, A, u1, ev, cs);
     k_loop_guard<typename Ar<V>::St><<<1, 1, 0, cs>>>(st, S->dctl, 1, h);
     HZ_CUDA(cudaStreamEndCapture(cs, &body));

@@ -826,7 +826,7 @@ def main():
     props = M.props()
     line_roof = spmv_roofline(hz, torch, M, A, stream, props["spmv_kind"])
 
-    launches = sum(4 + 5 * it for it in iters)
+    launches = sum(4 + 6 * it for it in iters)   # start: x0, r = b - A x; per iteration F1..F5 and the loop guard; exit: true residual, copy-out
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,

@@ -123,8 +123,10 @@ enum {
     HZ_SPMV_FLAT64 = 6       /* binary64 (IEEE double FMAs), row blocks of complete rows with every
                                 lane summing one contiguous run of entries, rows that cross a
                                 run boundary finished from the runs' partial sums (the default
-                                without HZ_FLAG_FF); per-entry error within the binary64 bound
-                                of a sequential row sum */
+                                without HZ_FLAG_FF); groups of real values take two FMAs per
+                                entry (the skipped terms are exact zeros; 0 * inf still gives
+                                NaN); per-entry error within the binary64 bound of a row sum,
+                                (2 m + 1) 2^-53 sum_j |a_ij| |x_j| for a row of m entries */
 };
 
 typedef struct {

@@ -743,6 +743,10 @@ constexpr bool kD64TwoAcc = HZ_D64_TWO_ACC != 0;   // even / odd entries of a gr
 #define HZ_D64_REAL_GROUPS 1
 #endif
 constexpr bool kD64RealGroups = HZ_D64_REAL_GROUPS != 0;   // two FMAs per entry for real-valued groups
+#ifndef HZ_D64_PIPE
+#define HZ_D64_PIPE 1
+#endif
+constexpr bool kD64Pipe = HZ_D64_PIPE != 0;   // column stream one group ahead
 
 // a zero imaginary part (+0 or -0), by the bit pattern (integer pipe; a
 // binary64 compare would occupy the binary64 pipe like an FMA)
@@ -770,9 +774,37 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
     const uint64_t pol = pol_evict_first();
     const int lane = threadIdx.x & 31;
     const int step = gridDim.x * (blockDim.x >> 5);
-    for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < A.nfblk; b += step) {
-        const int r0 = __ldg(A.fblk + b), r1 = __ldg(A.fblk + b + 1);
-        const int kb = __ldg(A.fblk_k + b), ke = __ldg(A.fblk_k + b + 1);
+    // a row block's bounds and this lane's stretch [c0, c1) of its entries
+    // [kb, ke) (U entries per lane)
+    struct Blk {
+        int b, r0, r1, kb, ke, U, c0, c1;
+    };
+    auto blk = [&](int bb) {
+        Blk m{bb, 0, 0, 0, 0, 0, 0, 0};
+        if (bb < A.nfblk) {
+            m.r0 = __ldg(A.fblk + bb);
+            m.r1 = __ldg(A.fblk + bb + 1);
+            m.kb = __ldg(A.fblk_k + bb);
+            m.ke = __ldg(A.fblk_k + bb + 1);
+            m.U = (m.ke - m.kb + 31) >> 5;
+            m.c0 = min(m.ke, m.kb + lane * m.U);
+            m.c1 = min(m.ke, m.c0 + m.U);
+        }
+        return m;
+    };
+    // the columns of a group of entries [k0, k0 + kD64Group) clipped to [k0, c1)
+    auto cols = [&](int k0, int c1, int (&c)[kD64Group]) {
+#pragma unroll
+        for (int u = 0; u < kD64Group; ++u) c[u] = k0 + u < c1 ? ld_stream_l1(A.col + k0 + u, pol) : -1;
+    };
+    const int b0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    Blk cur = blk(b0), ahead = blk(b0 + step);
+    // the column stream runs one group ahead (into the next row block at the
+    // end of one), so a group's x gathers wait for one load, not two
+    int cn[kD64Group];
+    if (kD64Pipe) cols(cur.c0, cur.c1, cn);
+    for (int b = b0; b < A.nfblk; b += step) {
+        const int r0 = cur.r0, r1 = cur.r1, kb = cur.kb, ke = cur.ke;
         const int nr = r1 - r0;
         typename PreOf<Epi>::T pf{};
         if (lane < nr) {
@@ -781,9 +813,7 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
         }
         if (lane == 0) sg->rp[nr] = ke;
         __syncwarp();
-        // this lane's stretch [c0, c1) of the block's entries [kb, ke)
-        const int U = (ke - kb + 31) >> 5;
-        const int c0 = min(ke, kb + lane * U), c1 = min(ke, c0 + U);
+        const int U = cur.U, c0 = cur.c0, c1 = cur.c1;
         // the row holding c0: the last j < nr with rp[j] <= c0 (rows without
         // entries before it are skipped, since their rp equals the next one's)
         int j = 0;
@@ -813,11 +843,20 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
         for (int k0 = c0; k0 < c0 + U; k0 += kD64Group) {
             int c[kD64Group];
             double2 a[kD64Group], v[kD64Group];
+            if constexpr (kD64Pipe) {
+#pragma unroll
+                for (int u = 0; u < kD64Group; ++u) c[u] = cn[u];
+            } else {
+                cols(k0, c1, c);
+            }
 #pragma unroll
             for (int u = 0; u < kD64Group; ++u) {
                 const int k = k0 + u;
-                c[u] = k < c1 ? ld_stream_l1(A.col + k, pol) : -1;
                 a[u] = k < c1 ? ld_stream_l1(A.val + k, pol) : make_double2(0.0, 0.0);
+            }
+            if constexpr (kD64Pipe) {
+                if (k0 + kD64Group < c0 + U) cols(k0 + kD64Group, c1, cn);
+                else cols(ahead.c0, ahead.b < A.nfblk ? ahead.c1 : ahead.c0, cn);
             }
 #pragma unroll
             for (int u = 0; u < kD64Group; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_double2(0.0, 0.0);
@@ -861,6 +900,8 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
             if (all_real) run(std::true_type{});
             else run(std::false_type{});
         }
+        // a block without entries ran no group: the next block's columns
+        if (kD64Pipe && U == 0) cols(ahead.c0, ahead.b < A.nfblk ? ahead.c1 : ahead.c0, cn);
         if (c0 < c1) flush(j, seg0, c1);
         __syncwarp();
         // phase 2: lane j finishes row r0 + j
@@ -881,6 +922,8 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
             epi_row(epi, r0 + lane, y, acc, pf);
         }
         __syncwarp();
+        cur = ahead;
+        ahead = blk(b + 2 * step);
     }
 }
 

@@ -747,6 +747,10 @@ constexpr bool kD64RealGroups = HZ_D64_REAL_GROUPS != 0;   // two FMAs per entry
 #define HZ_D64_PIPE 1
 #endif
 constexpr bool kD64Pipe = HZ_D64_PIPE != 0;   // column stream one group ahead
+#ifndef HZ_D64_ROW_AHEAD
+#define HZ_D64_ROW_AHEAD 1
+#endif
+constexpr bool kD64RowAhead = HZ_D64_ROW_AHEAD != 0;   // row pointers and epilogue operands one block ahead
 
 // a zero imaginary part (+0 or -0), by the bit pattern (integer pipe; a
 // binary64 compare would occupy the binary64 pipe like an FMA)
@@ -800,19 +804,33 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
     const int b0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     Blk cur = blk(b0), ahead = blk(b0 + step);
     // the column stream runs one group ahead (into the next row block at the
-    // end of one), so a group's x gathers wait for one load, not two
+    // end of one), so a group's x gathers wait for one load, not two; each
+    // lane's row pointer and epilogue operand come one row block ahead
     int cn[kD64Group];
     if (kD64Pipe) cols(cur.c0, cur.c1, cn);
+    auto row_start = [&](const Blk &m) { return lane < m.r1 - m.r0 ? __ldg(A.rowptr + m.r0 + lane) : 0; };
+    auto row_pre = [&](const Blk &m) {
+        typename PreOf<Epi>::T q{};
+        if (lane < m.r1 - m.r0) q = epi_pre(epi, m.r0 + lane);
+        return q;
+    };
+    int rp_cur = kD64RowAhead ? row_start(cur) : 0;
+    typename PreOf<Epi>::T pf_cur = kD64RowAhead ? row_pre(cur) : typename PreOf<Epi>::T{};
     for (int b = b0; b < A.nfblk; b += step) {
         const int r0 = cur.r0, r1 = cur.r1, kb = cur.kb, ke = cur.ke;
         const int nr = r1 - r0;
-        typename PreOf<Epi>::T pf{};
-        if (lane < nr) {
-            sg->rp[lane] = __ldg(A.rowptr + r0 + lane);
-            pf = epi_pre(epi, r0 + lane);
+        if (!kD64RowAhead) {
+            rp_cur = row_start(cur);
+            pf_cur = row_pre(cur);
         }
+        const typename PreOf<Epi>::T pf = pf_cur;
+        if (lane < nr) sg->rp[lane] = rp_cur;
         if (lane == 0) sg->rp[nr] = ke;
         __syncwarp();
+        if (kD64RowAhead && ahead.b < A.nfblk) {
+            rp_cur = row_start(ahead);
+            pf_cur = row_pre(ahead);
+        }
         const int U = cur.U, c0 = cur.c0, c1 = cur.c1;
         // the row holding c0: the last j < nr with rp[j] <= c0 (rows without
         // entries before it are skipped, since their rp equals the next one's)

@@ -43,6 +43,14 @@ L2_BYTES = 129 * 1024 * 1024
 FALLBACK_HBM_GBS = 6800.0
 
 
+def spmv_flops(A):
+    """binary64 flops of one product y = A x with complex x: a complex
+    multiply-add (8 flops, four FMAs) per entry, two FMAs (4 flops) for an
+    entry whose imaginary part is zero"""
+    nreal = int(np.count_nonzero(A.val.imag == 0))
+    return 8 * (A.nnz - nreal) + 4 * nreal
+
+
 def spmv_bytes(n, nnz):
     """Algorithmic bytes of one CSR SpMV: values and columns once, row
     pointers once, x read once, y written once."""
@@ -113,7 +121,7 @@ def recorded_traffic(name):
         return None
 
 
-TRAFFIC_FILES = {4: "spmv_ffb_c2_traffic.txt", 6: "spmv_d64b_c2_traffic.txt"}
+TRAFFIC_FILES = {4: "spmv_ffb_c2_traffic.txt", 6: "spmv_d64b_c2_traffic.txt", 7: "spmv_d64p_c2_traffic.txt"}
 
 
 class ClockSampler:
@@ -231,7 +239,9 @@ SPMV_KINDS = {0: "binary64 CSR-vector (k_spmv)", 1: "binary64 SELL-C-sigma (k_sp
               2: "double-float CSR-vector (k_spmv_ff)", 3: "double-float SELL-C-sigma (k_spmv_ff<0>)",
               4: "double-float block-flat (k_spmv_ffb)",
               5: "double-float block-flat, bulk-copy staged (k_spmv_fft)",
-              6: "binary64 block-flat, contiguous lane runs (k_spmv_d64b)"}
+              6: "binary64 block-flat, contiguous lane runs (k_spmv_d64b)",
+              7: "binary64 block-flat on the packed stream (k_spmv_d64b<packed>)"}
+BINARY64_KINDS = (0, 1, 6, 7)
 # binary64 roof of GB300: the nominal FP64 rate of the profiling recipe's
 # table (1.25 TFLOP/s); an own FMA-throughput probe measured 1.05 TFLOP/s
 FP64_NOMINAL_TFLOPS = 1.25
@@ -272,6 +282,8 @@ def run_kernel_case(args):
     if case in ("spmv", "cspmv", "solve"):
         A, b = build_workload()
         M = hz.Matrix.from_csr(A, ff=args.arith == "ff", c64=case == "cspmv")
+        if args.spmv:
+            M.set_spmv(args.spmv, args.group)
         if case == "cspmv":
             x = torch.randn(A.n, dtype=torch.complex64, device=dev)
             for _ in range(3):
@@ -347,10 +359,10 @@ def compare_modes(hz, torch, full_c4, maxit):
         return out, e0.elapsed_time(e1)
 
     variants = {
-        "fp64_binary64": ("flat64", dict(mode="fp64")),
-        "mixed": ("flat64", dict(mode="mixed")),
-        "bicgstab4_binary64": ("flat64", dict(method="bicgstabl", ell=4)),
-        "tfqmr_binary64": ("flat64", dict(method="tfqmr")),
+        "fp64_binary64": ("flat64p", dict(mode="fp64")),
+        "mixed": ("flat64p", dict(mode="mixed")),
+        "bicgstab4_binary64": ("flat64p", dict(method="bicgstabl", ell=4)),
+        "tfqmr_binary64": ("flat64p", dict(method="tfqmr")),
         "fp64_double_float": ("ffflat", dict(mode="fp64")),
         "mixed_double_float": ("ffflat", dict(mode="mixed")),
         "fp64_double_float_jacobi": ("ffflat", dict(mode="fp64", precond="jacobi")),
@@ -366,7 +378,7 @@ def compare_modes(hz, torch, full_c4, maxit):
             (_, info), ms = timed(lambda: hz.zsolve(M, b, tol=1e-10, maxit=maxit, **kw))
             res[key].append((ms, info))
     batched = {}
-    for key, kind, mode in (("batched_fp64", "flat64", "fp64"), ("batched_mixed", "flat64", "mixed"),
+    for key, kind, mode in (("batched_fp64", "flat64p", "fp64"), ("batched_mixed", "flat64p", "mixed"),
                             ("batched_double_float", "ffflat", "fp64")):
         for M, g in zip(mats, groups):   # the batch runs double-float when every handle's kind is;
             M.set_spmv(kind, g)          # its row tile is each handle's autotuned group
@@ -628,10 +640,11 @@ def workload_config(A, maxit, arith="fp64", iters=None, status=None):
 def spmv_roofline(hz, torch, M, A, stream, kind):
     """Roofline object of the SpMV core of the handle's kind, timed alone.
 
-    A binary64 kind is bound by GB300's binary64 pipe (four FMAs per nonzero
-    at the FP64 rate cap the product near 0.44 of the HBM copy rate), so its
-    roofline is "alu": 8 flops per nonzero against the nominal FP64 rate;
-    the HBM fraction is given beside it.  A double-float kind is HBM-bound."""
+    A binary64 kind is bound by GB300's binary64 pipe, so its roofline is
+    "alu": the multiply-adds the product needs (8 flops per complex entry,
+    4 per entry whose imaginary part is zero, which takes two FMAs against
+    a complex x) over the launch time, against the nominal FP64 rate; the
+    HBM fraction is given beside it.  A double-float kind is HBM-bound."""
     sp_avg = time_spmv(hz, torch, M, A.n, stream)
     peak, peak_src = peaks()
     gbs = spmv_bytes(A.n, A.nnz) / (sp_avg / 1e3) / 1e9
@@ -639,13 +652,15 @@ def spmv_roofline(hz, torch, M, A, stream, kind):
     hbm = {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
            "frac_of_nominal_8000": gbs / 8000.0, "peak_source": f"{peak_src} (burst copy)"}
     desc = "%s SpMV through hz_zspmv alone, L2 flushed" % SPMV_KINDS.get(kind, kind)
-    if kind in (0, 1, 6):
-        tf = 8.0 * A.nnz / (sp_avg / 1e3) / 1e12
+    if kind in BINARY64_KINDS:
+        flops = spmv_flops(A)
+        tf = flops / (sp_avg / 1e3) / 1e12
         return {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                 "frac": tf / FP64_NOMINAL_TFLOPS, "traffic": traffic,
                 "alu": "binary64 FMA pipe; peak = nominal FP64 rate (1.25 TFLOP/s); own FMA probe: "
                        f"{FP64_PROBE_TFLOPS} TFLOP/s", "frac_of_probe": tf / FP64_PROBE_TFLOPS,
-                "kernel": desc, "algorithmic_flops_per_launch": 8 * A.nnz,
+                "kernel": desc, "algorithmic_flops_per_launch": flops,
+                "flops_if_every_entry_complex": 8 * A.nnz,
                 "algorithmic_bytes_per_launch": spmv_bytes(A.n, A.nnz), "launch_ms": sp_avg, "hbm": hbm}
     return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
             "traffic": traffic, "frac_of_nominal_8000": gbs / 8000.0,
@@ -725,7 +740,7 @@ def main():
     ap.add_argument("--kernel-case", default=None, choices=["spmv", "cspmv", "blas", "outer", "batched", "solve"],
                     help="profiling aid: run one small case of a kernel family and exit (see run_kernel_case)")
     ap.add_argument("--group", type=int, default=4, help="lanes per row of the CSR-vector kinds")
-    ap.add_argument("--spmv", default=None, choices=["csr", "sell", "ff", "sellff", "ffflat", "fftma"],
+    ap.add_argument("--spmv", default=None, choices=["csr", "sell", "ff", "sellff", "ffflat", "fftma", "flat64", "flat64p"],
                     help="force an SpMV variant (default: the handle's own choice)")
     args = ap.parse_args()
     if args.impl == "reference":

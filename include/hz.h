@@ -73,7 +73,7 @@ enum {
                                 binary32 parts (48 significant bits, NOT binary64) on the
                                 binary32 pipes.  The split keeps its 48 bits only for values
                                 of magnitude in [2^-100, 2^101): if any stored value lies
-                                outside, the handle keeps the binary64 kind HZ_SPMV_FLAT64
+                                outside, the handle keeps the binary64 kind HZ_SPMV_FLAT64P
                                 (hz_mat_query reports it).  hz_zspmv on a double-float kind
                                 needs x in the same range; the BiCGStab solve scales b and the
                                 operator by powers of two (exact) so that its vectors stay
@@ -120,13 +120,22 @@ enum {
     HZ_SPMV_FF_TMA = 5,      /* HZ_SPMV_FF_FLAT with the values and columns moved into shared
                                 memory by bulk asynchronous copies, one row block ahead of the
                                 arithmetic */
-    HZ_SPMV_FLAT64 = 6       /* binary64 (IEEE double FMAs), row blocks of complete rows with every
+    HZ_SPMV_FLAT64 = 6,      /* binary64 (IEEE double FMAs), row blocks of complete rows with every
                                 lane summing one contiguous run of entries, rows that cross a
                                 run boundary finished from the runs' partial sums (the default
-                                without HZ_FLAG_FF); groups of real values take two FMAs per
+                                without HZ_FLAG_FF where the packed copy below cannot be built:
+                                more than 2^31 slots); groups of real values take two FMAs per
                                 entry (the skipped terms are exact zeros; 0 * inf still gives
                                 NaN); per-entry error within the binary64 bound of a row sum,
                                 (2 m + 1) 2^-53 sum_j |a_ij| |x_j| for a row of m entries */
+    HZ_SPMV_FLAT64P = 7      /* HZ_SPMV_FLAT64 on a packed copy of the row blocks that the handle
+                                owns (built by hz_csr_create, rebuilt by hz_mat_refresh_values):
+                                step u of the 32 lane runs stored as 32 consecutive slots (column,
+                                real part), so every load is coalesced, and the imaginary parts
+                                stored only for groups of steps that have a nonzero one (a group
+                                without is known to be real before its loads; the same sums as
+                                HZ_SPMV_FLAT64).  Device memory: 20 bytes per slot, about nnz
+                                slots.  The default without HZ_FLAG_FF */
 };
 
 typedef struct {

@@ -23,7 +23,7 @@ HZ_MODE_FP64, HZ_MODE_MIXED = 0, 1
 HZ_PRECOND_NONE, HZ_PRECOND_JACOBI = 0, 1
 HZ_METHOD_BICGSTAB, HZ_METHOD_BICGSTABL, HZ_METHOD_TFQMR = 0, 1, 2
 (HZ_SPMV_CSR_VECTOR, HZ_SPMV_SELL, HZ_SPMV_FF, HZ_SPMV_SELL_FF, HZ_SPMV_FF_FLAT, HZ_SPMV_FF_TMA,
- HZ_SPMV_FLAT64) = 0, 1, 2, 3, 4, 5, 6
+ HZ_SPMV_FLAT64, HZ_SPMV_FLAT64P) = 0, 1, 2, 3, 4, 5, 6, 7
 
 # every symbol include/hz.h declares
 EXPORTS = (

@@ -500,13 +500,13 @@ static void spmv_on(const Solver *S, const hz_mat *A, const V *x, const Epi &e, 
         launch_spmv_ff(S->kind, S->group, mat_view<double2>(A), x, e, S->red, S->grid_spmv, cs, pdl);
     } else if constexpr (std::is_same<V, float2>::value) {
         // complex64 inner operator: block-flat when the handle runs a block-flat kind
-        if (A->fblk && d64_kind(S->kind) == HZ_SPMV_FLAT64)
+        if (A->fblk && is_flat64(d64_kind(A, S->kind)))
             launch_k(pdl, k_spmv_c64b<Epi>, S->grid_c64, kFlatThreads, cs, mat_view<float2>(A), x, e, S->red);
         else
-            launch_spmv<V>(d64_kind(S->kind),
+            launch_spmv<V>(d64_kind(A, S->kind),
                            S->group, mat_view<V>(A), x, e, S->red, S->grid_spmv_cv, cs, pdl);
     } else {
-        launch_spmv<V>(d64_kind(S->kind), S->group, mat_view<V>(A), x, e, S->red,
+        launch_spmv<V>(d64_kind(A, S->kind), S->group, mat_view<V>(A), x, e, S->red,
                        S->grid_spmv_cv, cs, pdl);
     }
 }
@@ -656,7 +656,7 @@ static hz_status get_solver(hz_mat *A, uint32_t mode, cudaStream_t s, Solver **o
         S->kind = A->spmv_kind;
         S->group = A->group;
         S->grid_spmv = spmv_grid(A, S->kind, S->group);
-        S->grid_spmv_cv = spmv_grid(A, d64_kind(S->kind), S->group);
+        S->grid_spmv_cv = spmv_grid(A, d64_kind(A, S->kind), S->group);
         S->grid_c64 = A->fblk ? c64_flat_grid(A) : 1;
         // HZ_PDL=1 (environment) captures F2..F5 as programmatic dependent
         // launches; measured slower on the C2 solve (185 vs 175 us per

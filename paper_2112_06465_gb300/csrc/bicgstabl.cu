@@ -433,7 +433,7 @@ static void bl_spmv(const BlSolver *S, const hz_mat *A, const V *x, const Epi &e
     if constexpr (std::is_same<V, float4>::value) {
         launch_spmv_ff(S->kind, S->group, mat_view<double2>(A), x, e, S->red, S->grid_spmv, cs);
     } else {
-        launch_spmv<V>(d64_kind(S->kind), S->group, mat_view<V>(A), x, e, S->red,
+        launch_spmv<V>(d64_kind(A, S->kind), S->group, mat_view<V>(A), x, e, S->red,
                        S->grid_spmv_cv, cs);
     }
 }
@@ -537,7 +537,7 @@ static hz_status bl_get_solver(hz_mat *A, int ell, BlSolver **out) {
     S->kind = A->spmv_kind;
     S->group = A->group;
     S->grid_spmv = spmv_grid(A, S->kind, S->group);
-    S->grid_spmv_cv = spmv_grid(A, d64_kind(S->kind), S->group);
+    S->grid_spmv_cv = spmv_grid(A, d64_kind(A, S->kind), S->group);
     S->grid_vec = stream_grid(d, (A->n + kVecUnroll - 1) / kVecUnroll, kVecBlock, 8);
     const int np = ell + ell * (ell + 1) / 2;
     S->grid_gram = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)2 * d.num_sms,

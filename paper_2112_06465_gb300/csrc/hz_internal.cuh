@@ -553,6 +553,20 @@ struct hz_mat {
     int32_t nfblk = 0;
     int32_t *fblk = nullptr;
     int32_t *fblk_k = nullptr;   // rowptr[fblk[b]] for b = 0 .. nfblk
+    // packed binary64 stream of the same row blocks (HZ_SPMV_FLAT64P): block
+    // b owns slots [pk_base[b], pk_base[b+1]), 32 per lane step u, slot
+    // pk_base[b] + 32 u + l holding entry u of lane l's run (padding past
+    // the run's end); groups of kD64Group steps, group pk_gbase[b] + g of
+    // block b keeping its imaginary parts at pk_im + pk_gim[..] (same slot
+    // order) or, with pk_gim < 0, none (every imaginary part is zero)
+    int64_t pk_slots = 0;
+    int32_t pk_groups = 0;
+    int32_t *pk_base = nullptr;    // [nfblk + 1]
+    int32_t *pk_gbase = nullptr;   // [nfblk + 1]
+    int32_t *pk_gim = nullptr;     // [pk_groups]
+    int32_t *pk_col = nullptr;     // [pk_slots]
+    double *pk_re = nullptr;       // [pk_slots]
+    double *pk_im = nullptr;       // [pk_slots] (complex groups only use it)
     int32_t nfblk_t = 0;       // the same for the bulk-copy kernel's smaller chunks
     int32_t *fblk_t = nullptr;
     // owned copy of col, 16-byte aligned and padded by 8 entries, that the

@@ -36,6 +36,97 @@ __global__ void k_sell_gather(int64_t slots, const int *__restrict__ src, const 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packed binary64 stream of the row blocks (HZ_SPMV_FLAT64P).  Built from
+// the CSR arrays at creation and on every value refresh by three kernels,
+// one warp per row block with the lane runs of the block-flat kernel
+// (lane l: entries [c0, c1), U per lane).
+
+// per group of kD64Group steps: 32 x its steps if one of its entries has a
+// nonzero imaginary part (the slots it needs in pk_im), else 0
+__global__ void k_pk_count(int nfblk, const int *__restrict__ fblk_k, const int *__restrict__ gbase,
+                           const double2 *__restrict__ val, int *__restrict__ gim) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nfblk; b += nw) {
+        const int kb = fblk_k[b], ke = fblk_k[b + 1], U = (ke - kb + 31) >> 5;
+        const int c0 = min(ke, kb + lane * U), c1 = min(ke, c0 + U), g0 = gbase[b];
+        for (int u0 = 0; u0 < U; u0 += kD64Group) {
+            const int ue = min(U, u0 + kD64Group);
+            bool cplx = false;
+            for (int u = u0; u < ue; ++u)
+                if (c0 + u < c1 && !zero_bits(val[c0 + u].y)) cplx = true;
+            const bool any = __any_sync(0xffffffffu, cplx);
+            if (lane == 0) gim[g0 + u0 / kD64Group] = any ? 32 * (ue - u0) : 0;
+        }
+    }
+}
+
+// the counts -> exclusive prefix sums, the offsets of the complex groups'
+// parts in pk_im (-1 for a real group); one CTA, chunks of consecutive groups
+// per thread, the chunk sums scanned in shared memory
+constexpr int kPkScanThreads = 1024;
+__global__ void __launch_bounds__(kPkScanThreads) k_pk_scan(int ng, int *__restrict__ gim) {
+    __shared__ int part[kPkScanThreads];
+    const int t = threadIdx.x;
+    const int per = (ng + kPkScanThreads - 1) / kPkScanThreads;
+    const int lo = min(ng, t * per), hi = min(ng, lo + per);
+    int sum = 0;
+    for (int i = lo; i < hi; ++i) sum += gim[i];
+    part[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < kPkScanThreads; off <<= 1) {   // inclusive scan (Hillis-Steele)
+        const int v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - sum;
+    for (int i = lo; i < hi; ++i) {
+        const int c = gim[i];
+        gim[i] = c ? run : -1;
+        run += c;
+    }
+}
+
+// slot pk_base[b] + 32 u + l <- entry u of lane l's run (column -1, value 0
+// past its end); imaginary parts of complex groups at their offset
+__global__ void k_pk_fill(int nfblk, const int *__restrict__ fblk_k, const int *__restrict__ base,
+                          const int *__restrict__ gbase, const int *__restrict__ gim, const int *__restrict__ col,
+                          const double2 *__restrict__ val, int *__restrict__ pcol, double *__restrict__ pre,
+                          double *__restrict__ pim) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nfblk; b += nw) {
+        const int kb = fblk_k[b], ke = fblk_k[b + 1], U = (ke - kb + 31) >> 5;
+        const int c0 = min(ke, kb + lane * U), c1 = min(ke, c0 + U), P = base[b], g0 = gbase[b];
+        for (int u = 0; u < U; ++u) {
+            const int k = c0 + u, slot = P + 32 * u + lane;
+            const bool in = k < c1;
+            const double2 a = in ? val[k] : make_double2(0.0, 0.0);
+            pcol[slot] = in ? col[k] : -1;
+            pre[slot] = a.x;
+            const int o = gim[g0 + u / kD64Group];
+            if (o >= 0) pim[o + 32 * (u % kD64Group) + lane] = a.y;
+        }
+    }
+}
+
+static hz_status pk_refresh(hz_mat *A, cudaStream_t s) {
+    if (!A->pk_re) return HZ_OK;
+    DevInfo d;
+    HZ_TRY(dev_info(&d));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)A->nfblk + 7) / 8, (int64_t)d.num_sms * 8));
+    k_pk_count<<<grid, 256, 0, s>>>(A->nfblk, A->fblk_k, A->pk_gbase, A->val, A->pk_gim);
+    HZ_CUDA(cudaGetLastError());
+    k_pk_scan<<<1, kPkScanThreads, 0, s>>>(A->pk_groups, A->pk_gim);
+    HZ_CUDA(cudaGetLastError());
+    k_pk_fill<<<grid, 256, 0, s>>>(A->nfblk, A->fblk_k, A->pk_base, A->pk_gbase, A->pk_gim, A->col, A->val,
+                                   A->pk_col, A->pk_re, A->pk_im);
+    HZ_CUDA(cudaGetLastError());
+    return HZ_OK;
+}
+
 // smallest and largest binary exponent (IEEE field minus bias) over the
 // nonzero real and imaginary parts of the values: out[0] = min, out[1] = max
 // (out[0] = INT_MAX, out[1] = INT_MIN on entry); a non-finite part counts as
@@ -85,6 +176,8 @@ MatView<double2> mat_view<double2>(const hz_mat *A) {
     v.nfblk = A->nfblk; v.fblk = A->fblk; v.fblk_k = A->fblk_k; v.nfblk_t = A->nfblk_t; v.fblk_t = A->fblk_t; v.colp = A->col_pad; v.fault = A->fault;
     v.nchunks = A->sell_nchunks; v.chunk_off = A->sell_chunk_off; v.chunk_w = A->sell_chunk_w;
     v.perm = A->sell_perm; v.scol = A->sell_col; v.sval = A->sell_val;
+    v.pk_base = A->pk_base; v.pk_gbase = A->pk_gbase; v.pk_gim = A->pk_gim; v.pk_col = A->pk_col;
+    v.pk_re = A->pk_re; v.pk_im = A->pk_im;
     return v;
 }
 
@@ -101,11 +194,14 @@ MatView<float2> mat_view<float2>(const hz_mat *A) {
 int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap) {
     DevInfo d;
     if (dev_info(&d) != HZ_OK) return 1;
-    if (kind == HZ_SPMV_FF_FLAT || kind == HZ_SPMV_FF_TMA || kind == HZ_SPMV_FLAT64) {
+    if (kind == HZ_SPMV_FF_FLAT || kind == HZ_SPMV_FF_TMA || is_flat64(kind)) {
         // persistent: exactly the CTAs that fit at once (blocks are taken
         // grid-stride, so CTAs beyond one wave would only add a tail)
-        static int occ_flat = 0, occ_tma = 0, occ_d64 = 0;
-        int &occ = kind == HZ_SPMV_FF_TMA ? occ_tma : kind == HZ_SPMV_FLAT64 ? occ_d64 : occ_flat;
+        static int occ_flat = 0, occ_tma = 0, occ_d64 = 0, occ_d64p = 0;
+        int &occ = kind == HZ_SPMV_FF_TMA ? occ_tma
+                   : kind == HZ_SPMV_FLAT64 ? occ_d64
+                   : kind == HZ_SPMV_FLAT64P ? occ_d64p
+                                             : occ_flat;
         if (occ == 0) {
             cudaError_t e;
             if (kind == HZ_SPMV_FF_TMA) {
@@ -113,7 +209,11 @@ int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap) {
                                      cudaSharedmemCarveoutMaxShared);
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_fft<EpiStore<double2>>, kFlatThreads, 0);
             } else if (kind == HZ_SPMV_FLAT64) {
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_d64b<EpiStore<double2>>, kFlatThreads, 0);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_d64b<EpiStore<double2>, false>,
+                                                                  kFlatThreads, 0);
+            } else if (kind == HZ_SPMV_FLAT64P) {
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_d64b<EpiStore<double2>, true>,
+                                                                  kFlatThreads, 0);
             } else {
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_ffb<EpiStore<double2>>, kFlatThreads, 0);
             }
@@ -227,7 +327,7 @@ static hz_status refresh(hz_mat *A, cudaStream_t s) {
             A->sell_slots, A->sell_src, A->val, A->sell_val, A->sell_val32, A->sell_vff);
         HZ_CUDA(cudaGetLastError());
     }
-    return HZ_OK;
+    return pk_refresh(A, s);
 }
 
 hz_status ensure_c64(hz_mat *A, cudaStream_t s) {
@@ -255,6 +355,7 @@ static hz_status autotune(hz_mat *A, cudaStream_t s) {
         for (int w : {2, 4, 8, 16, 32}) cand.push_back({HZ_SPMV_FF, w});
     if (A->sell_vff) cand.push_back({HZ_SPMV_SELL_FF, 0});
     if (A->fblk) cand.push_back({HZ_SPMV_FLAT64, 0});
+    if (A->pk_re) cand.push_back({HZ_SPMV_FLAT64P, 0});
     if (A->val_ff && A->fblk) cand.push_back({HZ_SPMV_FF_FLAT, 0});
     if (A->col_pad) cand.push_back({HZ_SPMV_FF_TMA, 0});
     float best = 1e30f, best_cv = 1e30f;   // over all kinds; over the binary64 CSR-vector groups
@@ -388,6 +489,7 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
     // kFlatRows complete rows with at most `cap` entries; a longer row is
     // a block of its own
     // (and, for dev_k, the first entry of every block boundary row)
+    std::vector<int> fb_keep;
     auto row_blocks = [&](int cap, int32_t **dev, int32_t *count, int32_t **dev_k) {
         std::vector<int> fb{0};
         for (int r = 0; r < n;) {
@@ -401,6 +503,7 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
             cudaMemcpy(*dev, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return false;
         if (!dev_k) return true;
+        fb_keep = fb;
         std::vector<int> fk(fb.size());
         for (size_t b = 0; b < fb.size(); ++b) fk[b] = rp[fb[b]];
         return cudaMalloc(dev_k, sizeof(int) * fk.size()) == cudaSuccess &&
@@ -410,7 +513,39 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
         set_error("hz_csr_create: allocation failed");
         return fail(HZ_ERR_ALLOC);
     }
-    A->spmv_kind = HZ_SPMV_FLAT64;
+    // the packed binary64 stream of these blocks: U = ceil(entries / 32)
+    // steps of 32 slots per block, groups of kD64Group steps (skipped when
+    // the slots would not fit 31-bit offsets)
+    {
+        const int nb = A->nfblk;
+        std::vector<int> pb(nb + 1), pg(nb + 1);
+        int64_t P = 0, G = 0;
+        for (int b = 0; b < nb; ++b) {
+            const int64_t U = ((int64_t)rp[fb_keep[b + 1]] - rp[fb_keep[b]] + 31) / 32;
+            pb[b] = (int)std::min<int64_t>(P, INT32_MAX);
+            pg[b] = (int)std::min<int64_t>(G, INT32_MAX);
+            P += 32 * U;
+            G += (U + kD64Group - 1) / kD64Group;
+        }
+        if (P < INT32_MAX - 32) {
+            pb[nb] = (int)P;
+            pg[nb] = (int)G;
+            A->pk_slots = P;
+            A->pk_groups = (int32_t)G;
+            if (cudaMalloc(&A->pk_base, sizeof(int) * (nb + 1)) != cudaSuccess ||
+                cudaMalloc(&A->pk_gbase, sizeof(int) * (nb + 1)) != cudaSuccess ||
+                cudaMalloc(&A->pk_gim, sizeof(int) * std::max<int64_t>(G, 1)) != cudaSuccess ||
+                cudaMalloc(&A->pk_col, sizeof(int) * std::max<int64_t>(P, 1)) != cudaSuccess ||
+                cudaMalloc(&A->pk_re, sizeof(double) * std::max<int64_t>(P, 1)) != cudaSuccess ||
+                cudaMalloc(&A->pk_im, sizeof(double) * std::max<int64_t>(P, 1)) != cudaSuccess ||
+                cudaMemcpy(A->pk_base, pb.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(A->pk_gbase, pg.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+                set_error("hz_csr_create: allocation failed");
+                return fail(HZ_ERR_ALLOC);
+            }
+        }
+    }
+    A->spmv_kind = A->pk_re ? HZ_SPMV_FLAT64P : HZ_SPMV_FLAT64;
     hz_status st;
     if (flags & HZ_FLAG_SELL) {
         if ((st = build_sell(A, s, rp, cl, 1024)) != HZ_OK) return fail(st);
@@ -474,7 +609,7 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
             in_range = h_er[0] >= kFFMinExp && h_er[1] <= kFFMaxExp;
         }
         A->ff_range_ok = in_range;
-        A->spmv_kind = in_range ? HZ_SPMV_FF_FLAT : HZ_SPMV_FLAT64;
+        A->spmv_kind = in_range ? HZ_SPMV_FF_FLAT : A->pk_re ? HZ_SPMV_FLAT64P : HZ_SPMV_FLAT64;
     }
     if ((st = refresh(A, s)) != HZ_OK) return fail(st);
     if (flags & HZ_FLAG_AUTOTUNE) {
@@ -504,6 +639,12 @@ extern "C" HZ_API hz_status hz_mat_destroy(hz_mat *A) {
     cudaFree(A->sell_vff);
     cudaFree(A->fblk);
     cudaFree(A->fblk_k);
+    cudaFree(A->pk_base);
+    cudaFree(A->pk_gbase);
+    cudaFree(A->pk_gim);
+    cudaFree(A->pk_col);
+    cudaFree(A->pk_re);
+    cudaFree(A->pk_im);
     cudaFree(A->fblk_t);
     cudaFree(A->col_pad);
     cudaFree(A->fault);
@@ -582,7 +723,7 @@ extern "C" HZ_API hz_status hz_cspmv(hz_mat *A, const hz_c *d_x, hz_c *d_y, void
     HZ_CHECK(d_x && d_y, "hz_cspmv: null vector");
     HZ_CHECK((const void *)d_x != (const void *)d_y, "hz_cspmv: x and y must not alias");
     HZ_TRY(ensure_c64(A, (cudaStream_t)stream));
-    if (A->fblk && d64_kind(A->spmv_kind) == HZ_SPMV_FLAT64) {
+    if (A->fblk && is_flat64(d64_kind(A, A->spmv_kind))) {
         // the block-flat kinds: the block-flat complex64 kernel
         EpiStore<float2> epi{(float2 *)d_y};
         HZ_CUDA(launch_k(false, k_spmv_c64b<EpiStore<float2>>, c64_flat_grid(A), kFlatThreads, (cudaStream_t)stream,
@@ -606,6 +747,11 @@ extern "C" HZ_API hz_status hz_mat_set_spmv(hz_mat *A, int32_t kind, int32_t gro
         return HZ_OK;
     }
     if (kind == HZ_SPMV_FLAT64) {
+        A->spmv_kind = kind;
+        return HZ_OK;
+    }
+    if (kind == HZ_SPMV_FLAT64P) {
+        HZ_CHECK(A->pk_re != nullptr, "hz_mat_set_spmv: the handle has no packed binary64 stream");
         A->spmv_kind = kind;
         return HZ_OK;
     }

@@ -101,6 +101,13 @@ struct MatView {
     // padded copy of col read by the bulk-copy kernel, and its fault word
     const int *colp;
     int *fault;
+    // packed binary64 stream of the row blocks (see hz_mat::pk_*)
+    const int *pk_base;
+    const int *pk_gbase;
+    const int *pk_gim;
+    const int *pk_col;
+    const double *pk_re;
+    const double *pk_im;
 };
 
 // Epilogue interface (every fused SpMV epilogue provides):
@@ -752,10 +759,10 @@ constexpr bool kD64Pipe = HZ_D64_PIPE != 0;   // column stream one group ahead
 #endif
 constexpr bool kD64RowAhead = HZ_D64_ROW_AHEAD != 0;   // row pointers and epilogue operands one block ahead
 
-// a zero imaginary part (+0 or -0), by the bit pattern (integer pipe; a
-// binary64 compare would occupy the binary64 pipe like an FMA)
-__device__ __forceinline__ bool zero_im(double2 a) {
-    return ((__double2hiint(a.y) & 0x7fffffff) | __double2loint(a.y)) == 0;
+// +0 or -0, by the bit pattern (integer pipe; a binary64 compare would
+// occupy the binary64 pipe like an FMA)
+__device__ __forceinline__ bool zero_bits(double v) {
+    return ((__double2hiint(v) & 0x7fffffff) | __double2loint(v)) == 0;
 }
 
 // finite (exponent field not all ones), by the bit pattern
@@ -766,25 +773,31 @@ __device__ __forceinline__ double2 ld_stream_l1(const double2 *ptr, uint64_t pol
     asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(ptr), "l"(pol));
     return v;
 }
+__device__ __forceinline__ double ld_stream_l1(const double *ptr, uint64_t pol) {
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
 __device__ __forceinline__ int ld_stream_l1(const int *ptr, uint64_t pol) {
     int v;
     asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
     return v;
 }
 
-template <class Epi, int NV>
+template <class Epi, int NV, bool PK>
 __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const double2 *__restrict__ x,
                                               const Epi &epi, typename Epi::Acc (&acc)[NV], D64Seg *sg) {
+    constexpr int G = kD64Group;
     const uint64_t pol = pol_evict_first();
     const int lane = threadIdx.x & 31;
     const int step = gridDim.x * (blockDim.x >> 5);
     // a row block's bounds and this lane's stretch [c0, c1) of its entries
-    // [kb, ke) (U entries per lane)
+    // [kb, ke) (U entries per lane); packed: its first slot P and first group gb
     struct Blk {
-        int b, r0, r1, kb, ke, U, c0, c1;
+        int b, r0, r1, kb, ke, U, c0, c1, P, gb;
     };
     auto blk = [&](int bb) {
-        Blk m{bb, 0, 0, 0, 0, 0, 0, 0};
+        Blk m{bb, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         if (bb < A.nfblk) {
             m.r0 = __ldg(A.fblk + bb);
             m.r1 = __ldg(A.fblk + bb + 1);
@@ -793,21 +806,36 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
             m.U = (m.ke - m.kb + 31) >> 5;
             m.c0 = min(m.ke, m.kb + lane * m.U);
             m.c1 = min(m.ke, m.c0 + m.U);
+            if constexpr (PK) {
+                m.P = __ldg(A.pk_base + bb);
+                m.gb = __ldg(A.pk_gbase + bb);
+            }
         }
         return m;
     };
-    // the columns of a group of entries [k0, k0 + kD64Group) clipped to [k0, c1)
-    auto cols = [&](int k0, int c1, int (&c)[kD64Group]) {
+    // the columns of steps [u0, u0 + G) of block m's lane runs (-1 past the
+    // run's end) and, packed, where the group keeps its imaginary parts
+    // (-1: nowhere, all are zero); CSR order: entries c0 + u0 + u
+    auto cols = [&](const Blk &m, int u0, int (&c)[G], int &gim) {
+        if constexpr (PK) {
 #pragma unroll
-        for (int u = 0; u < kD64Group; ++u) c[u] = k0 + u < c1 ? ld_stream_l1(A.col + k0 + u, pol) : -1;
+            for (int u = 0; u < G; ++u)
+                c[u] = u0 + u < m.U ? ld_stream_l1(A.pk_col + m.P + 32 * (u0 + u) + lane, pol) : -1;
+            gim = u0 < m.U ? __ldg(A.pk_gim + m.gb + u0 / G) : -1;
+        } else {
+            const int k0 = m.c0 + u0;
+#pragma unroll
+            for (int u = 0; u < G; ++u) c[u] = k0 + u < m.c1 ? ld_stream_l1(A.col + k0 + u, pol) : -1;
+            gim = 0;
+        }
     };
     const int b0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     Blk cur = blk(b0), ahead = blk(b0 + step);
     // the column stream runs one group ahead (into the next row block at the
     // end of one), so a group's x gathers wait for one load, not two; each
     // lane's row pointer and epilogue operand come one row block ahead
-    int cn[kD64Group];
-    if (kD64Pipe) cols(cur.c0, cur.c1, cn);
+    int cn[G], gn = -1;
+    if (kD64Pipe) cols(cur, 0, cn, gn);
     auto row_start = [&](const Blk &m) { return lane < m.r1 - m.r0 ? __ldg(A.rowptr + m.r0 + lane) : 0; };
     auto row_pre = [&](const Blk &m) {
         typename PreOf<Epi>::T q{};
@@ -858,37 +886,62 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
             else sg->full[jj] = t;
         };
 #pragma unroll 1
-        for (int k0 = c0; k0 < c0 + U; k0 += kD64Group) {
-            int c[kD64Group];
-            double2 a[kD64Group], v[kD64Group];
+        for (int u0 = 0; u0 < U; u0 += G) {
+            const int k0 = c0 + u0;
+            int c[G], gim;
+            double ar[G], ai[G];
+            double2 v[G];
             if constexpr (kD64Pipe) {
 #pragma unroll
-                for (int u = 0; u < kD64Group; ++u) c[u] = cn[u];
+                for (int u = 0; u < G; ++u) c[u] = cn[u];
+                gim = gn;
             } else {
-                cols(k0, c1, c);
+                cols(cur, u0, c, gim);
             }
+            if constexpr (PK) {
+                // coalesced: step u of all 32 lanes is 32 consecutive slots
 #pragma unroll
-            for (int u = 0; u < kD64Group; ++u) {
-                const int k = k0 + u;
-                a[u] = k < c1 ? ld_stream_l1(A.val + k, pol) : make_double2(0.0, 0.0);
+                for (int u = 0; u < G; ++u)
+                    ar[u] = u0 + u < U ? ld_stream_l1(A.pk_re + cur.P + 32 * (u0 + u) + lane, pol) : 0.0;
+                if (gim >= 0) {
+#pragma unroll
+                    for (int u = 0; u < G; ++u)
+                        ai[u] = u0 + u < U ? ld_stream_l1(A.pk_im + gim + 32 * u + lane, pol) : 0.0;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < G; ++u) ai[u] = 0.0;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < G; ++u) {
+                    const double2 a = k0 + u < c1 ? ld_stream_l1(A.val + k0 + u, pol) : make_double2(0.0, 0.0);
+                    ar[u] = a.x;
+                    ai[u] = a.y;
+                }
             }
             if constexpr (kD64Pipe) {
-                if (k0 + kD64Group < c0 + U) cols(k0 + kD64Group, c1, cn);
-                else cols(ahead.c0, ahead.b < A.nfblk ? ahead.c1 : ahead.c0, cn);
+                if (u0 + G < U) cols(cur, u0 + G, cn, gn);
+                else cols(ahead, 0, cn, gn);
             }
 #pragma unroll
-            for (int u = 0; u < kD64Group; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_double2(0.0, 0.0);
+            for (int u = 0; u < G; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_double2(0.0, 0.0);
             // a group of the warp whose values all have a zero imaginary part
             // needs two FMAs per entry, not four: the terms -Im(a) Im(x) and
-            // Im(a) Re(x) are exact zeros (decided on the values alone, after
-            // the gathers are issued, so neither waits for the other)
-            bool real = true;
+            // Im(a) Re(x) are exact zeros.  Packed, the stream says so; else
+            // it is decided on the values alone, after the gathers are
+            // issued, so neither waits for the other
+            bool all_real;
+            if constexpr (PK) {
+                all_real = gim < 0;
+            } else {
+                bool real = true;
 #pragma unroll
-            for (int u = 0; u < kD64Group; ++u) real = real && zero_im(a[u]);
-            const bool all_real = kD64RealGroups && __all_sync(0xffffffffu, real);
+                for (int u = 0; u < G; ++u) real = real && zero_bits(ai[u]);
+                all_real = kD64RealGroups && __all_sync(0xffffffffu, real);
+            }
             auto run = [&](auto real_tag) {
 #pragma unroll
-                for (int u = 0; u < kD64Group; ++u) {
+                for (int u = 0; u < G; ++u) {
                     const int k = k0 + u;
                     if (k < c1) {
                         while (k == nxt && j < nr - 1) {   // row j ends before entry k
@@ -903,14 +956,14 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
                         // accumulators: two dependent FMA chains per lane
                         double2 &q = (kD64TwoAcc && (u & 1)) ? s2 : s;
                         if constexpr (decltype(real_tag)::value) {
-                            q.x = fma(a[u].x, v[u].x, q.x);
-                            q.y = fma(a[u].x, v[u].y, q.y);
+                            q.x = fma(ar[u], v[u].x, q.x);
+                            q.y = fma(ar[u], v[u].y, q.y);
                             // the skipped 0 * Im(x) and 0 * Re(x) are NaN for a
                             // non-finite x: remembered and applied at the flush
                             nan_re = nan_re || !finite1(v[u].y);
                             nan_im = nan_im || !finite1(v[u].x);
                         } else {
-                            cmac(q, a[u], v[u]);
+                            cmac(q, make_double2(ar[u], ai[u]), v[u]);
                         }
                     }
                 }
@@ -919,7 +972,7 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
             else run(std::false_type{});
         }
         // a block without entries ran no group: the next block's columns
-        if (kD64Pipe && U == 0) cols(ahead.c0, ahead.b < A.nfblk ? ahead.c1 : ahead.c0, cn);
+        if (kD64Pipe && U == 0) cols(ahead, 0, cn, gn);
         if (c0 < c1) flush(j, seg0, c1);
         __syncwarp();
         // phase 2: lane j finishes row r0 + j
@@ -945,7 +998,6 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
     }
 }
 
-
 // per-thread accumulators -> one grid total -> epi.finish (last block)
 template <class Epi, int NV>
 __device__ __forceinline__ void spmv_reduce(const Epi &epi, typename Epi::Acc (&acc)[NV], RedScratch red) {
@@ -957,7 +1009,7 @@ __device__ __forceinline__ void spmv_reduce(const Epi &epi, typename Epi::Acc (&
 }
 
 // the block-flat binary64 kernel (kFlatThreads threads, row blocks, contiguous lane runs)
-template <class Epi>
+template <class Epi, bool PK = false>
 __global__ void __launch_bounds__(kFlatThreads, kD64MinBlocks) k_spmv_d64b(MatView<double2> A,
                                                                             const double2 *__restrict__ x, Epi epi,
                                                                             RedScratch red) {
@@ -972,7 +1024,7 @@ __global__ void __launch_bounds__(kFlatThreads, kD64MinBlocks) k_spmv_d64b(MatVi
     typename Epi::Acc acc[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
-    flat_rows_d64<Epi, NV>(A, x, epi, acc, &seg[threadIdx.x >> 5]);
+    flat_rows_d64<Epi, NV, PK>(A, x, epi, acc, &seg[threadIdx.x >> 5]);
     if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
 }
 
@@ -1230,7 +1282,11 @@ cudaError_t launch_spmv(int kind, int group, const MatView<T> &A, const T *x, co
                         RedScratch red, int grid, cudaStream_t s, bool pdl = false) {
     if constexpr (std::is_same<T, double2>::value) {
         if (kind == HZ_SPMV_FLAT64) {
-            launch_k(pdl, k_spmv_d64b<Epi>, grid, kFlatThreads, s, A, x, epi, red);
+            launch_k(pdl, k_spmv_d64b<Epi, false>, grid, kFlatThreads, s, A, x, epi, red);
+            return cudaGetLastError();
+        }
+        if (kind == HZ_SPMV_FLAT64P) {
+            launch_k(pdl, k_spmv_d64b<Epi, true>, grid, kFlatThreads, s, A, x, epi, red);
             return cudaGetLastError();
         }
     }
@@ -1288,13 +1344,17 @@ int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap = 8);
 
 // the binary64 (and complex64) kernel family that stands for a handle's
 // kind when a solver runs in binary64: the SELL kinds -> HZ_SPMV_SELL, the
-// CSR-vector kinds -> HZ_SPMV_CSR_VECTOR, the block-flat kinds ->
-// HZ_SPMV_FLAT64 (the row blocks exist for every handle)
-inline int d64_kind(int kind) {
+// CSR-vector kinds -> HZ_SPMV_CSR_VECTOR, HZ_SPMV_FLAT64 -> itself, the other
+// block-flat kinds -> HZ_SPMV_FLAT64P where the handle has its packed stream
+// (else HZ_SPMV_FLAT64; the row blocks exist for every handle)
+inline int d64_kind(const hz_mat *A, int kind) {
     if (kind == HZ_SPMV_SELL || kind == HZ_SPMV_SELL_FF) return HZ_SPMV_SELL;
     if (kind == HZ_SPMV_CSR_VECTOR || kind == HZ_SPMV_FF) return HZ_SPMV_CSR_VECTOR;
-    return HZ_SPMV_FLAT64;
+    if (kind == HZ_SPMV_FLAT64) return HZ_SPMV_FLAT64;
+    return A->pk_re ? HZ_SPMV_FLAT64P : HZ_SPMV_FLAT64;
 }
+// the binary64 block-flat kinds
+inline bool is_flat64(int kind) { return kind == HZ_SPMV_FLAT64 || kind == HZ_SPMV_FLAT64P; }
 
 template <class T>
 MatView<T> mat_view(const hz_mat *A);

@@ -299,7 +299,7 @@ static void tq_spmv(const TqSolver *S, const hz_mat *A, const V *x, const Epi &e
     if constexpr (std::is_same<V, float4>::value) {
         launch_spmv_ff(S->kind, S->group, mat_view<double2>(A), x, e, S->red, S->grid_spmv, cs);
     } else {
-        launch_spmv<V>(d64_kind(S->kind), S->group, mat_view<V>(A), x, e, S->red,
+        launch_spmv<V>(d64_kind(A, S->kind), S->group, mat_view<V>(A), x, e, S->red,
                        S->grid_spmv_cv, cs);
     }
 }
@@ -367,7 +367,7 @@ static hz_status tq_get_solver(hz_mat *A, TqSolver **out) {
     S->kind = A->spmv_kind;
     S->group = A->group;
     S->grid_spmv = spmv_grid(A, S->kind, S->group);
-    S->grid_spmv_cv = spmv_grid(A, d64_kind(S->kind), S->group);
+    S->grid_spmv_cv = spmv_grid(A, d64_kind(A, S->kind), S->group);
     S->grid_vec = stream_grid(dv, (A->n + kVecUnroll - 1) / kVecUnroll, kVecBlock, 8);
     const size_t nb = (size_t)A->n * 16;
     void **vecs[] = {&S->x, &S->w, &S->u1, &S->u2, &S->v, &S->d, &S->au1, &S->au, &S->rh};

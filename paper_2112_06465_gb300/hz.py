@@ -80,11 +80,11 @@ class Matrix:
         return {f: getattr(p, f) for f, _ in p._fields_}
 
     def set_spmv(self, kind="csr", group=4):
-        """Force the SpMV variant: ("csr" | "ff", lanes per row) or ("flat64" | "sell" |
-        "sellff" | "ffflat" | "fftma", ignored)."""
+        """Force the SpMV variant: ("csr" | "ff", lanes per row) or ("flat64p" | "flat64" |
+        "sell" | "sellff" | "ffflat" | "fftma", ignored)."""
         k = {"sell": _lib.HZ_SPMV_SELL, "ff": _lib.HZ_SPMV_FF, "sellff": _lib.HZ_SPMV_SELL_FF,
              "ffflat": _lib.HZ_SPMV_FF_FLAT, "fftma": _lib.HZ_SPMV_FF_TMA,
-             "flat64": _lib.HZ_SPMV_FLAT64}.get(kind, _lib.HZ_SPMV_CSR_VECTOR)
+             "flat64": _lib.HZ_SPMV_FLAT64, "flat64p": _lib.HZ_SPMV_FLAT64P}.get(kind, _lib.HZ_SPMV_CSR_VECTOR)
         check(_L.hz_mat_set_spmv(self.handle, k, int(group)))
 
     def check(self):

@@ -64,10 +64,11 @@ def c2_oracle_20(oracle, c2_system):
     return oracle.bicgstab(A, b, tol=1e-10, maxit=20)
 
 
-@pytest.mark.parametrize("kind", ["flat64", "ffflat"])
+@pytest.mark.parametrize("kind", ["flat64p", "flat64", "ffflat"])
 def test_bicgstab_c2_bench_configuration(hz, oracle, c2_system, c2_oracle_20, kind):
     """The benchmark's solve (C2 cylinder, x0 = 0, tol 1e-10; binary64 with
-    the block-flat FLAT64 product, and the double-float fast path) for its
+    the block-flat products FLAT64P (the default) and FLAT64, and the
+    double-float fast path) for its
     first 20 iterations against the oracle's.
 
     On this indefinite operator the BiCGStab trajectory is chaotic: in the
@@ -82,7 +83,7 @@ def test_bicgstab_c2_bench_configuration(hz, oracle, c2_system, c2_oracle_20, ki
     A, b = c2_system
     xo20, io = c2_oracle_20
     assert io.iters == 20 and io.status == 4
-    tight = 1e-11 if kind == "flat64" else 1e-9
+    tight = 1e-9 if kind == "ffflat" else 1e-11
     M = hz.Matrix.from_csr(A, ff=kind == "ffflat")
     M.set_spmv(kind)
     hist = torch.zeros(21, dtype=torch.float64, device="cuda")
@@ -141,7 +142,7 @@ def test_double_float_handle_keeps_binary64_outside_split_range(hz, oracle):
     for f in (2.0 ** 110, 2.0 ** -110):
         As = W.CSR(A.n, A.rowptr, A.col, A.val * f)
         M = hz.Matrix.from_csr(As, ff=True)
-        assert M.props()["spmv_kind"] == 6
+        assert M.props()["spmv_kind"] == 7
         x = K.vectors(A.n, 31)[0]
         y = host(hz.zspmv(M, dev(x)))
         m = np.diff(As.rowptr).astype(np.float64)
@@ -168,7 +169,7 @@ def test_bicgstab_manufactured_solution(hz, oracle):
     assert np.linalg.norm(host(x) - xs) / np.linalg.norm(xs) <= 1e-8
 
 
-@pytest.mark.parametrize("variant", [("flat64", 0), ("csr", 2), ("csr", 8), ("sell", 0), ("ff", 4), ("ff", 8),
+@pytest.mark.parametrize("variant", [("flat64p", 0), ("flat64", 0), ("csr", 2), ("csr", 8), ("sell", 0), ("ff", 4), ("ff", 8),
                                      ("sellff", 0), ("ffflat", 0), ("fftma", 0)])
 def test_bicgstab_cylinder_variants(hz, oracle, variant):
     A, b = K.small_cylinder()

@@ -35,7 +35,7 @@ def host(t):
     return t.cpu().numpy()
 
 
-BINARY64_KINDS = ("csr", "sell", "flat64")
+BINARY64_KINDS = ("csr", "sell", "flat64", "flat64p")
 
 
 def spmv_bound(A, x, kind):
@@ -62,7 +62,7 @@ def check_spmv(hz, oracle, A, x, variants):
     M.close()
 
 
-ALL_VARIANTS = [("flat64", 0), ("csr", 2), ("csr", 4), ("csr", 8), ("csr", 16), ("csr", 32), ("sell", 0),
+ALL_VARIANTS = [("flat64p", 0), ("flat64", 0), ("csr", 2), ("csr", 4), ("csr", 8), ("csr", 16), ("csr", 32), ("sell", 0),
                 ("ff", 2), ("ff", 4), ("ff", 8), ("ff", 16), ("ff", 32), ("sellff", 0), ("ffflat", 0),
                 ("fftma", 0)]
 
@@ -118,9 +118,10 @@ def test_spmv_hexcar(hz, oracle):
     A, b = W.h1_hexcar()
     x = K.vectors(A.n, 72)[0]
     ref = oracle.zspmv(A, x)
-    for ff, kind in ((False, "flat64"), (True, "ffflat")):
+    for ff, kind in ((False, "flat64p"), (False, "flat64"), (True, "ffflat")):
         M = hz.Matrix.from_csr(A, ff=ff)
-        assert M.props()["spmv_kind"] == (4 if ff else 6)
+        assert M.props()["spmv_kind"] == (4 if ff else 7)
+        M.set_spmv(kind)
         y = host(hz.zspmv(M, dev(x)))
         assert np.all(np.abs(y - ref) <= spmv_bound(A, x, kind)), kind
         M.close()
@@ -139,22 +140,57 @@ def test_spmv_real_valued_groups_and_nonfinite_x(hz, oracle):
     val[band] = A.val[band]                                   # complex values in 100 rows only
     Ar = W.CSR(A.n, A.rowptr, A.col, val)
     x = K.vectors(A.n, 82)[0]
-    check_spmv(hz, oracle, Ar, x, [("flat64", 0), ("csr", 4)])
+    check_spmv(hz, oracle, Ar, x, [("flat64p", 0), ("flat64", 0), ("csr", 4)])
     xb = x.copy()
     xb[17] = complex(np.inf, 1.0)
     xb[2900] = complex(0.5, np.nan)
     M = hz.Matrix.from_csr(Ar)
-    y = host(hz.zspmv(M, dev(xb)))
     ref = oracle.zspmv(Ar, xb)
-    assert np.array_equal(np.isnan(y.real), np.isnan(ref.real))
-    assert np.array_equal(np.isnan(y.imag), np.isnan(ref.imag))
-    assert np.array_equal(np.isinf(y.real), np.isinf(ref.real))
     ok = np.isfinite(ref)
     m = np.diff(Ar.rowptr).astype(np.float64)
     xf = np.where(np.isfinite(xb), xb, 0)
     bound = (2 * m + 2) * 2.0 ** -52 * K.row_abs_scale(Ar, xf)
-    assert np.all(np.abs(y[ok] - ref[ok]) <= bound[ok])
+    for kind in ("flat64p", "flat64"):
+        M.set_spmv(kind)
+        y = host(hz.zspmv(M, dev(xb)))
+        assert np.array_equal(np.isnan(y.real), np.isnan(ref.real)), kind
+        assert np.array_equal(np.isnan(y.imag), np.isnan(ref.imag)), kind
+        assert np.array_equal(np.isinf(y.real), np.isinf(ref.real)), kind
+        assert np.all(np.abs(y[ok] - ref[ok]) <= bound[ok]), kind
     M.close()
+
+
+def test_spmv_packed_stream_follows_value_refresh(hz, oracle):
+    """The packed binary64 stream records which groups of entries are real
+    when it is built; new values that make real groups complex (and complex
+    groups real) must reach it through hz_mat_refresh_values.  Checked
+    against the oracle on the new values, for a matrix that starts all real
+    and one that starts all complex."""
+    A = K.random_csr(3000, 91, max_row=30, long_rows=(700,))
+    x = K.vectors(A.n, 92)[0]
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    for start_real in (True, False):
+        v0 = A.val.real.astype(np.complex128) if start_real else A.val.copy()
+        vd = dev(v0)
+        M = hz.Matrix(dev(A.rowptr), dev(A.col), vd)
+        assert M.props()["spmv_kind"] == 7
+        y = host(hz.zspmv(M, dev(x)))
+        A0 = W.CSR(A.n, A.rowptr, A.col, v0)
+        assert np.all(np.abs(y - oracle.zspmv(A0, x)) <= spmv_bound(A0, x, "flat64p"))
+        # rows 1000..1199 and the long row swap kinds: complex <-> real
+        flip = ((rows >= 1000) & (rows < 1200)) | (np.diff(A.rowptr)[rows] == 700)
+        v1 = v0.copy()
+        v1[flip] = A.val[flip] if start_real else A.val[flip].real
+        vd.copy_(torch.as_tensor(v1))
+        M.refresh_values()
+        A1 = W.CSR(A.n, A.rowptr, A.col, v1)
+        y = host(hz.zspmv(M, dev(x)))
+        assert np.all(np.abs(y - oracle.zspmv(A1, x)) <= spmv_bound(A1, x, "flat64p")), start_real
+        # the packed stream holds the same numbers in another order: the
+        # products equal those of FLAT64 (same FMAs, same order) bit for bit
+        M.set_spmv("flat64")
+        assert np.array_equal(host(hz.zspmv(M, dev(x))), y)
+        M.close()
 
 
 def test_spmv_wide_band_fallback(hz, oracle):
@@ -241,7 +277,7 @@ def test_spmv_c2_full_size_sampled(hz, oracle):
     x = K.vectors(A.n, 2002)[0]
     ref = oracle.zspmv(A, x)
     scale = K.row_abs_scale(A, x)
-    for ff, kind in ((False, "flat64"), (False, "csr"), (True, "ffflat")):
+    for ff, kind in ((False, "flat64p"), (False, "flat64"), (False, "csr"), (True, "ffflat")):
         M = hz.Matrix.from_csr(A, ff=ff)
         M.set_spmv(kind, 4)
         y = host(hz.zspmv(M, dev(x)))
@@ -266,7 +302,7 @@ def test_spmv_c3_full_size(hz, oracle):
         M = hz.Matrix.from_csr(A, ff=ff, c64=ff)
         y = host(hz.zspmv(M, xd))
         err = np.abs(y - ref)
-        assert np.all(err <= spmv_bound(A, x, "ffflat" if ff else "flat64")), (ff, float((err / scale).max()))
+        assert np.all(err <= spmv_bound(A, x, "ffflat" if ff else "flat64p")), (ff, float((err / scale).max()))
         if ff:
             x32 = x.astype(np.complex64)
             y32 = host(hz.cspmv(M, dev(x32)))

@@ -13,6 +13,12 @@
 // whose wait is bounded in time (it reports HZ_ERR_TIMEOUT instead of
 // hanging if a CTA never arrives).
 //
+// In binary64 an SpMV item is kBBlock / 32 row blocks of the handle's
+// block-flat layout, one per warp, each summed in contiguous lane runs (the
+// core of the single-system HZ_SPMV_FLAT64 kernel, groups of kBFlatG steps);
+// the double-float and complex64 products keep W lanes per row (the handle's
+// autotuned CSR-vector group) over runs of rows.
+//
 // The kernel is written once over the vector format V: complex128 in
 // binary64 (double2), or complex128 in double-float on the binary32 pipes
 // (float4, when every handle of the batch was created with HZ_FLAG_FF): the
@@ -34,17 +40,38 @@
 #include <vector>
 
 #include "arith.cuh"
+#include "spmv.cuh"
 
 namespace hz {
 
 constexpr int kBBlock = 256;
+#ifndef HZ_BATCHED_MIN_BLOCKS
+#define HZ_BATCHED_MIN_BLOCKS 3
+#endif
+// resident CTAs per SM asked of the register allocator (the cooperative grid
+// is as many CTAs as fit, up to four per SM): the binary64 kernel with its
+// block-flat products, the double-float one, the mixed one
+constexpr int kBMinBlocks = HZ_BATCHED_MIN_BLOCKS;
+template <class V> struct BMin { static constexpr int value = std::is_same<V, double2>::value ? kBMinBlocks : 3; };
+constexpr int kBMinBlocksMixed = 4;
+#ifndef HZ_BATCHED_FLAT_G
+#define HZ_BATCHED_FLAT_G 2
+#endif
+// binary64 batches: products on the block-flat core with groups of kBFlatG
+// steps (unpacked; few registers, so the cooperative grid keeps two CTAs per
+// SM), 0 = the W-lane CSR-vector rows
+constexpr int kBFlatG = HZ_BATCHED_FLAT_G;
 constexpr int kBVecItem = kBBlock * 4;     // elements per vector item
 constexpr int kBMaxSys = 1024;             // systems per launch (shared-memory tables)
 
 struct BSys {
     int n, W, rows_per_item;
-    int sp_item0, sp_items;      // SpMV items [sp_item0, sp_item0 + sp_items)
+    int sp_item0, sp_items;      // SpMV items [sp_item0, sp_item0 + sp_items) (W lanes per row)
+    int fl_item0, fl_items;      // binary64 SpMV items: kBBlock / 32 row blocks each, one per warp
     int vc_item0, vc_items;      // vector items
+    int nfblk;                   // the handle's row blocks and packed binary64 stream
+    const int *fblk, *fblk_k, *pk_base, *pk_gbase, *pk_gim, *pk_col;
+    const double *pk_re, *pk_im;
     const int *rowptr;
     const int *col;
     const double2 *val;
@@ -436,6 +463,33 @@ __device__ void spmv_item(int phase, const BSys &sy, int r0, int r1, typename Ar
     }
 }
 
+// the phase epilogue as a block-flat SpMV epilogue
+struct BEpi {
+    using Acc = double;
+    int phase;
+    const BSys *sy;
+    __device__ void row(int i, double2 y, Acc (&acc)[3]) const { row_epilogue<double2>(phase, *sy, i, y, acc); }
+};
+
+// binary64 SpMV item `local` of one system: warp w takes row block
+// kBBlock / 32 * local + w with the block-flat core (the caller's CSR arrays,
+// groups of kBFlatG steps), rows finished with the phase epilogue
+__device__ void spmv_item_flat(int phase, const BSys &sy, int local, double (&acc)[3]) {
+    __shared__ D64Seg seg[kBBlock / 32];
+    const BVecs<double2> w = bvecs<double2>(sy);
+    const double2 *x = phase == P_F2 ? w.p : phase == P_F4 ? w.s : w.x;
+    MatView<double2> A{};
+    A.n = sy.n; A.rowptr = sy.rowptr; A.col = sy.col; A.val = sy.val;
+    A.nfblk = sy.nfblk; A.fblk = sy.fblk; A.fblk_k = sy.fblk_k;
+    A.pk_base = sy.pk_base; A.pk_gbase = sy.pk_gbase; A.pk_gim = sy.pk_gim; A.pk_col = sy.pk_col;
+    A.pk_re = sy.pk_re; A.pk_im = sy.pk_im;
+    const BEpi epi{phase, &sy};
+    constexpr int wpi = kBBlock / 32;
+    const int b0 = local * wpi + (int)(threadIdx.x >> 5), bend = min(sy.nfblk, (local + 1) * wpi);
+    flat_rows_d64<BEpi, 3, false, (kBFlatG > 0 ? kBFlatG : 1)>(A, x, epi, acc, &seg[threadIdx.x >> 5], b0, wpi,
+                                                               bend);
+}
+
 template <class V>
 __device__ void vec_item(int phase, const BSys &sy, const BState *S, int e0, int e1, typename Ar<V>::Acc (&acc)[3]) {
     using A = Ar<V>;
@@ -485,8 +539,9 @@ __device__ void vec_item(int phase, const BSys &sy, const BState *S, int e0, int
     }
 }
 
-// one phase over the systems in the block's active table
-template <class V>
+// one phase over the systems in the block's active table (Flat: binary64
+// products on the block-flat core, item lists I_FLAT)
+template <class V, bool Flat = false>
 __device__ void run_phase(int phase, const BCtl *c, const BSys *sys, BState *st, double *partials, const int *act,
                           const int *pref, int nact) {
     const bool spmv = phase == P_INIT || phase == P_F2 || phase == P_F4 || phase == P_TRUE || phase == P_OUT;
@@ -516,16 +571,21 @@ __device__ void run_phase(int phase, const BCtl *c, const BSys *sys, BState *st,
         for (int q = 0; q < 3; ++q) Ar<V>::acc_zero(va[q]);
         double acc[3];
         if (spmv) {
-            const int r0 = local * sy.rows_per_item, r1 = min(sy.n, r0 + sy.rows_per_item);
-            switch (sy.W) {
-                case 2: spmv_item<2, V>(phase, sy, r0, r1, va); break;
-                case 4: spmv_item<4, V>(phase, sy, r0, r1, va); break;
-                case 8: spmv_item<8, V>(phase, sy, r0, r1, va); break;
-                case 16: spmv_item<16, V>(phase, sy, r0, r1, va); break;
-                default: spmv_item<32, V>(phase, sy, r0, r1, va); break;
+            constexpr bool kFlat = Flat && std::is_same<V, double2>::value;
+            if constexpr (kFlat) {
+                spmv_item_flat(phase, sy, local, va);
+            } else {
+                const int r0 = local * sy.rows_per_item, r1 = min(sy.n, r0 + sy.rows_per_item);
+                switch (sy.W) {
+                    case 2: spmv_item<2, V>(phase, sy, r0, r1, va); break;
+                    case 4: spmv_item<4, V>(phase, sy, r0, r1, va); break;
+                    case 8: spmv_item<8, V>(phase, sy, r0, r1, va); break;
+                    case 16: spmv_item<16, V>(phase, sy, r0, r1, va); break;
+                    default: spmv_item<32, V>(phase, sy, r0, r1, va); break;
+                }
             }
-            const int nit = sy.sp_items;
-            const int g = sy.sp_item0 + local;
+            const int nit = kFlat ? sy.fl_items : sy.sp_items;
+            const int g = (kFlat ? sy.fl_item0 : sy.sp_item0) + local;
             if constexpr (Ar<V>::kFF) {
                 if (phase == P_F4) item_done_ff<3>(phase, c, sy, S, partials, g, sy.sp_item0, nit, va);
                 else if (phase == P_TRUE) item_done_ff<1>(phase, c, sy, S, partials, g, sy.sp_item0, nit, va);
@@ -533,13 +593,14 @@ __device__ void run_phase(int phase, const BCtl *c, const BSys *sys, BState *st,
             } else {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) acc[q] = (double)Ar<V>::total(va[q]);
-                if (phase == P_F4 || phase == P_OUT) item_done<3>(phase, c, sy, S, partials, g, sy.sp_item0, nit, acc);
+                const int i0 = kFlat ? sy.fl_item0 : sy.sp_item0;
+                if (phase == P_F4 || phase == P_OUT) item_done<3>(phase, c, sy, S, partials, g, i0, nit, acc);
                 else if (phase == P_TRUE) {
                     double a1[1] = {acc[0]};
-                    item_done<1>(phase, c, sy, S, partials, g, sy.sp_item0, nit, a1);
+                    item_done<1>(phase, c, sy, S, partials, g, i0, nit, a1);
                 } else {
                     double a2[2] = {acc[0], acc[1]};
-                    item_done<2>(phase, c, sy, S, partials, g, sy.sp_item0, nit, a2);
+                    item_done<2>(phase, c, sy, S, partials, g, i0, nit, a2);
                 }
             }
         } else {
@@ -583,14 +644,16 @@ __device__ __forceinline__ bool bactive(int which, const BState &S) {
     }
 }
 
-__device__ int build_active(int spmv_items, const BCtl *c, const BSys *sys, const BState *st, int *act,
+enum { I_VEC = 0, I_SPMV = 1, I_FLAT = 2 };   // item lists: vector tiles, W-lane SpMV rows, binary64 row blocks
+
+__device__ int build_active(int items, const BCtl *c, const BSys *sys, const BState *st, int *act,
                             int *pref, int which) {
     __shared__ int nact;
     __shared__ int cnt[kBMaxSys];
     const int nsys = c->nsys;
     for (int s = threadIdx.x; s < nsys; s += kBBlock) {
         const bool run = bactive(which, st[s]);
-        cnt[s] = run ? (spmv_items ? sys[s].sp_items : sys[s].vc_items) : -1;
+        cnt[s] = run ? (items == I_FLAT ? sys[s].fl_items : items == I_SPMV ? sys[s].sp_items : sys[s].vc_items) : -1;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -609,60 +672,62 @@ __device__ int build_active(int spmv_items, const BCtl *c, const BSys *sys, cons
 }
 
 template <class V>
-__global__ void __launch_bounds__(kBBlock) k_batched(BCtl *c, const BSys *sys, BState *st, double *partials) {
+__global__ void __launch_bounds__(kBBlock, BMin<V>::value) k_batched(BCtl *c, const BSys *sys, BState *st, double *partials) {
     __shared__ int act[kBMaxSys];
     __shared__ int pref_sp[kBMaxSys + 1];
     __shared__ int pref_vc[kBMaxSys + 1];
     constexpr bool kFF = !std::is_same<V, double2>::value;
+    constexpr bool kFl = !kFF && kBFlatG > 0;   // binary64 products on the block-flat core
+    constexpr int kSp = kFl ? I_FLAT : I_SPMV;
     int nact;
     if constexpr (kFF) {   // the iterate into the double-float workspace
-        nact = build_active(0, c, sys, st, act, pref_vc, A_ALL);
-        run_phase<V>(P_LOAD, c, sys, st, partials, act, pref_vc, nact);
+        nact = build_active(I_VEC, c, sys, st, act, pref_vc, A_ALL);
+        run_phase<V, kFl>(P_LOAD, c, sys, st, partials, act, pref_vc, nact);
         if (!bgrid_sync(c)) return;
     }
-    nact = build_active(1, c, sys, st, act, pref_sp, A_ALL);
-    run_phase<V>(P_INIT, c, sys, st, partials, act, pref_sp, nact);
+    nact = build_active(kSp, c, sys, st, act, pref_sp, A_ALL);
+    run_phase<V, kFl>(P_INIT, c, sys, st, partials, act, pref_sp, nact);
     if (!bgrid_sync(c)) return;
     for (int guard = 0; guard <= c->maxit + 1; ++guard) {
-        nact = build_active(1, c, sys, st, act, pref_sp, A_RUNNING);
+        nact = build_active(kSp, c, sys, st, act, pref_sp, A_RUNNING);
         if (nact == 0) break;
-        build_active(0, c, sys, st, act, pref_vc, A_RUNNING);
-        run_phase<V>(P_F1, c, sys, st, partials, act, pref_vc, nact);
+        build_active(I_VEC, c, sys, st, act, pref_vc, A_RUNNING);
+        run_phase<V, kFl>(P_F1, c, sys, st, partials, act, pref_vc, nact);
         if (!bgrid_sync(c)) return;
-        run_phase<V>(P_F2, c, sys, st, partials, act, pref_sp, nact);
+        run_phase<V, kFl>(P_F2, c, sys, st, partials, act, pref_sp, nact);
         if (!bgrid_sync(c)) return;
-        run_phase<V>(P_F3, c, sys, st, partials, act, pref_vc, nact);
+        run_phase<V, kFl>(P_F3, c, sys, st, partials, act, pref_vc, nact);
         if (!bgrid_sync(c)) return;
-        run_phase<V>(P_F4, c, sys, st, partials, act, pref_sp, nact);
+        run_phase<V, kFl>(P_F4, c, sys, st, partials, act, pref_sp, nact);
         if (!bgrid_sync(c)) return;
-        run_phase<V>(P_F5, c, sys, st, partials, act, pref_vc, nact);
+        run_phase<V, kFl>(P_F5, c, sys, st, partials, act, pref_vc, nact);
         if (!bgrid_sync(c)) return;
     }
-    nact = build_active(1, c, sys, st, act, pref_sp, A_ALL);
-    run_phase<V>(P_TRUE, c, sys, st, partials, act, pref_sp, nact);
+    nact = build_active(kSp, c, sys, st, act, pref_sp, A_ALL);
+    run_phase<V, kFl>(P_TRUE, c, sys, st, partials, act, pref_sp, nact);
     if constexpr (kFF) {   // the solution back to the caller's x
         if (!bgrid_sync(c)) return;
-        nact = build_active(0, c, sys, st, act, pref_vc, A_ALL);
-        run_phase<V>(P_STORE, c, sys, st, partials, act, pref_vc, nact);
+        nact = build_active(I_VEC, c, sys, st, act, pref_vc, A_ALL);
+        run_phase<V, kFl>(P_STORE, c, sys, st, partials, act, pref_vc, nact);
     }
 }
 
 // mixed-precision sweep: every system refines in binary64 around complex64
 // inner BiCGStab solves, each at its own stage (see the file comment)
-__global__ void __launch_bounds__(kBBlock) k_batched_mixed(BCtl *c, const BSys *sys, BState *st, double *partials) {
+__global__ void __launch_bounds__(kBBlock, kBMinBlocksMixed) k_batched_mixed(BCtl *c, const BSys *sys, BState *st, double *partials) {
     __shared__ int act[kBMaxSys];
     __shared__ int pref_sp[kBMaxSys + 1];
     __shared__ int pref_vc[kBMaxSys + 1];
-    int nact = build_active(1, c, sys, st, act, pref_sp, A_UNFINISHED);
+    int nact = build_active(I_SPMV, c, sys, st, act, pref_sp, A_UNFINISHED);
     run_phase<double2>(P_OUT, c, sys, st, partials, act, pref_sp, nact);
     if (!bgrid_sync(c)) return;
     // every round advances each system by one inner iteration or one
     // refinement step, so a system leaves within maxit + max_outer + 1 rounds
     const int cap = c->maxit + c->max_outer + 2;
     for (int round = 0; round <= cap; ++round) {
-        const int nin = build_active(1, c, sys, st, act, pref_sp, A_INNER);
+        const int nin = build_active(I_SPMV, c, sys, st, act, pref_sp, A_INNER);
         if (nin > 0) {
-            build_active(0, c, sys, st, act, pref_vc, A_INNER);
+            build_active(I_VEC, c, sys, st, act, pref_vc, A_INNER);
             run_phase<float2>(P_F1, c, sys, st, partials, act, pref_vc, nin);
             if (!bgrid_sync(c)) return;
             run_phase<float2>(P_F2, c, sys, st, partials, act, pref_sp, nin);
@@ -674,20 +739,20 @@ __global__ void __launch_bounds__(kBBlock) k_batched_mixed(BCtl *c, const BSys *
             run_phase<float2>(P_F5, c, sys, st, partials, act, pref_vc, nin);
             if (!bgrid_sync(c)) return;
         }
-        const int nup = build_active(0, c, sys, st, act, pref_vc, A_UPDATE);
+        const int nup = build_active(I_VEC, c, sys, st, act, pref_vc, A_UPDATE);
         if (nin == 0 && nup == 0) break;
         if (nup > 0) {
             run_phase<double2>(P_UPD, c, sys, st, partials, act, pref_vc, nup);
             if (!bgrid_sync(c)) return;
-            build_active(1, c, sys, st, act, pref_sp, A_UPDATE);
+            build_active(I_SPMV, c, sys, st, act, pref_sp, A_UPDATE);
             run_phase<double2>(P_OUT, c, sys, st, partials, act, pref_sp, nup);
             if (!bgrid_sync(c)) return;
         }
     }
-    nact = build_active(0, c, sys, st, act, pref_vc, A_BEST);
+    nact = build_active(I_VEC, c, sys, st, act, pref_vc, A_BEST);
     run_phase<double2>(P_BEST, c, sys, st, partials, act, pref_vc, nact);
     if (!bgrid_sync(c)) return;
-    nact = build_active(1, c, sys, st, act, pref_sp, A_ALL);
+    nact = build_active(I_SPMV, c, sys, st, act, pref_sp, A_ALL);
     run_phase<double2>(P_TRUE, c, sys, st, partials, act, pref_sp, nact);
 }
 
@@ -708,7 +773,7 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
     HZ_CHECK(A && d_b && d_x && h_info, "hz_zsolve_batched: null argument");
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<BSys> hs(nsys);
-    int64_t sp = 0, vc = 0, vec_elems = 0;
+    int64_t sp = 0, fl = 0, vc = 0, vec_elems = 0;
     // double-float when every handle carries the split values and runs a
     // double-float SpMV kind; binary64 otherwise
     // (a mixed batch refines in binary64 around complex64 inner solves)
@@ -730,16 +795,22 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
         y.rows_per_item = (kBBlock / y.W) * 4;
         y.sp_item0 = (int)sp;
         y.sp_items = (y.n + y.rows_per_item - 1) / y.rows_per_item;
+        y.fl_item0 = (int)fl;
+        y.fl_items = (A[k]->nfblk + kBBlock / 32 - 1) / (kBBlock / 32);
+        y.nfblk = A[k]->nfblk; y.fblk = A[k]->fblk; y.fblk_k = A[k]->fblk_k;
+        y.pk_base = A[k]->pk_base; y.pk_gbase = A[k]->pk_gbase; y.pk_gim = A[k]->pk_gim;
+        y.pk_col = A[k]->pk_col; y.pk_re = A[k]->pk_re; y.pk_im = A[k]->pk_im;
         y.vc_item0 = (int)vc;
         y.vc_items = (y.n + kBVecItem - 1) / kBVecItem;
         y.rowptr = A[k]->rowptr; y.col = A[k]->col; y.val = A[k]->val; y.vff = A[k]->val_ff;
         y.val32 = A[k]->val32;
         y.b = (const double2 *)d_b[k]; y.x = (double2 *)d_x[k]; y.xw = nullptr;
         sp += y.sp_items;
+        fl += y.fl_items;
         vc += y.vc_items;
         vec_elems += y.n;
     }
-    HZ_CHECK(sp < INT32_MAX / 4 && vc < INT32_MAX / 4, "hz_zsolve_batched: batch too large");
+    HZ_CHECK(sp < INT32_MAX / 4 && fl < INT32_MAX / 4 && vc < INT32_MAX / 4, "hz_zsolve_batched: batch too large");
     // workspace: 6 vectors per system, item partials, states, controls
     double2 *work = nullptr;
     float2 *work32 = nullptr;
@@ -752,7 +823,7 @@ extern "C" HZ_API hz_status hz_zsolve_batched(int32_t nsys, hz_mat *const *A, co
     };
     if (cudaMalloc(&work, sizeof(double2) * std::max<int64_t>(nvec * vec_elems, 1)) != cudaSuccess ||
         cudaMalloc(&work32, sizeof(float2) * std::max<int64_t>(nvec32 * vec_elems, 1)) != cudaSuccess ||
-        cudaMalloc(&partials, sizeof(double) * 4 * std::max<int64_t>(std::max(sp, vc), 1)) != cudaSuccess ||
+        cudaMalloc(&partials, sizeof(double) * 4 * std::max<int64_t>(std::max(std::max(sp, fl), vc), 1)) != cudaSuccess ||
         cudaMalloc(&st, sizeof(BState) * nsys) != cudaSuccess || cudaMalloc(&dsys, sizeof(BSys) * nsys) != cudaSuccess ||
         cudaMalloc(&ctl, sizeof(BCtl)) != cudaSuccess) {
         cleanup();

@@ -784,13 +784,17 @@ __device__ __forceinline__ int ld_stream_l1(const int *ptr, uint64_t pol) {
     return v;
 }
 
-template <class Epi, int NV, bool PK>
+// The warp takes row blocks b0, b0 + step, ... below bend (a kernel of its
+// own: grid-stride over all blocks; the batched solver: one block per warp
+// of a work item).
+// G: steps per group (the packed stream's groups are kD64Group steps).
+template <class Epi, int NV, bool PK, int G = kD64Group>
 __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const double2 *__restrict__ x,
-                                              const Epi &epi, typename Epi::Acc (&acc)[NV], D64Seg *sg) {
-    constexpr int G = kD64Group;
+                                              const Epi &epi, typename Epi::Acc (&acc)[NV], D64Seg *sg, int b0,
+                                              int step, int bend) {
+    static_assert(!PK || G == kD64Group, "the packed stream is laid out in groups of kD64Group steps");
     const uint64_t pol = pol_evict_first();
     const int lane = threadIdx.x & 31;
-    const int step = gridDim.x * (blockDim.x >> 5);
     // a row block's bounds and this lane's stretch [c0, c1) of its entries
     // [kb, ke) (U entries per lane); packed: its first slot P and first group gb
     struct Blk {
@@ -798,7 +802,7 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
     };
     auto blk = [&](int bb) {
         Blk m{bb, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-        if (bb < A.nfblk) {
+        if (bb < bend) {
             m.r0 = __ldg(A.fblk + bb);
             m.r1 = __ldg(A.fblk + bb + 1);
             m.kb = __ldg(A.fblk_k + bb);
@@ -829,7 +833,6 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
             gim = 0;
         }
     };
-    const int b0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     Blk cur = blk(b0), ahead = blk(b0 + step);
     // the column stream runs one group ahead (into the next row block at the
     // end of one), so a group's x gathers wait for one load, not two; each
@@ -844,7 +847,7 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
     };
     int rp_cur = kD64RowAhead ? row_start(cur) : 0;
     typename PreOf<Epi>::T pf_cur = kD64RowAhead ? row_pre(cur) : typename PreOf<Epi>::T{};
-    for (int b = b0; b < A.nfblk; b += step) {
+    for (int b = b0; b < bend; b += step) {
         const int r0 = cur.r0, r1 = cur.r1, kb = cur.kb, ke = cur.ke;
         const int nr = r1 - r0;
         if (!kD64RowAhead) {
@@ -855,7 +858,7 @@ __device__ __forceinline__ void flat_rows_d64(const MatView<double2> &A, const d
         if (lane < nr) sg->rp[lane] = rp_cur;
         if (lane == 0) sg->rp[nr] = ke;
         __syncwarp();
-        if (kD64RowAhead && ahead.b < A.nfblk) {
+        if (kD64RowAhead && ahead.b < bend) {
             rp_cur = row_start(ahead);
             pf_cur = row_pre(ahead);
         }
@@ -1024,7 +1027,9 @@ __global__ void __launch_bounds__(kFlatThreads, kD64MinBlocks) k_spmv_d64b(MatVi
     typename Epi::Acc acc[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
-    flat_rows_d64<Epi, NV, PK>(A, x, epi, acc, &seg[threadIdx.x >> 5]);
+    const int wpc = blockDim.x >> 5;
+    flat_rows_d64<Epi, NV, PK>(A, x, epi, acc, &seg[threadIdx.x >> 5], blockIdx.x * wpc + (threadIdx.x >> 5),
+                               gridDim.x * wpc, A.nfblk);
     if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
 }
 

@@ -352,6 +352,31 @@ def test_batched_uneven_systems(hz, oracle, ff):
         assert abs(infos[k].iters - io.iters) <= max(5, 0.05 * io.iters), (k, infos[k].iters, io.iters)
 
 
+def test_batched_block_flat_ragged_rows(hz, oracle):
+    """The binary64 batch runs its products on each handle's row blocks: a
+    diagonally dominant ragged matrix whose long rows (700 and 1300 entries)
+    fill row blocks of their own and whose short rows share them, solved in
+    one batch with an FD box and a cylinder, against the oracle."""
+    R = K.random_csr(3000, 97, max_row=30, long_rows=(700, 1300))
+    m = sp.csr_matrix((R.val, R.col, R.rowptr), shape=(R.n, R.n))
+    d = np.asarray(abs(m).sum(axis=1)).ravel() + 1.0
+    m = (m + sp.diags(d * (1.0 + 0.1j))).tocsr()
+    m.sort_indices()
+    Ar = W.CSR(R.n, m.indptr.astype(np.int32), m.indices.astype(np.int32), m.data.astype(np.complex128))
+    Ac, bc = K.small_cylinder()
+    systems = [Ar, W.fd_helmholtz_box(11, kh=0.3, damping=0.05), Ac]
+    bs = [K.vectors(Ar.n, 4400)[0], K.vectors(systems[1].n, 4401)[0], bc]
+    mats = [hz.Matrix.from_csr(A) for A in systems]
+    xs, infos = hz.zsolve_batched(mats, [dev(b) for b in bs], tol=1e-10, maxit=3000)
+    for k, (A, b, x, info) in enumerate(zip(systems, bs, xs, infos)):
+        xo, io = oracle.bicgstab(A, b, tol=1e-10, maxit=3000)
+        assert info.status == io.status, (k, info, io.status)
+        assert k == 2 or io.status == 0
+        if io.status == 0:
+            assert true_relres(oracle, A, host(x), b) <= 1e-10
+            assert np.linalg.norm(host(x) - xo) / np.linalg.norm(xo) <= 1e-8
+
+
 def test_batched_mixed_uneven_systems(hz, oracle):
     """The mixed-precision batch (complex64 inner BiCGStab, binary64
     refinement, each system at its own stage) against the oracle's

@@ -513,25 +513,73 @@ __device__ void vec_item(int phase, const BSys &sy, const BState *S, int e0, int
             return;
         }
     }
-    for (int i = e0 + threadIdx.x; i < e1; i += kBBlock) {
+    // the BiCGStab passes: each thread loads the operands of all its
+    // elements of the item before the first store (the stores may alias
+    // nothing here, but the compiler cannot know, and would otherwise wait
+    // out one memory round trip per element); loads are clamped into the item
+    // (complex64: all four elements at once; 16-byte formats two at a time)
+    constexpr int U = std::is_same<V, float2>::value ? kBVecItem / kBBlock : 2;
+    static_assert((kBVecItem / kBBlock) % U == 0, "whole stages per item");
+    if (phase == P_F1 || phase == P_F3 || (phase == P_F5 && !half)) {
+        for (int i0 = e0 + (int)threadIdx.x; i0 < e0 + kBVecItem; i0 += U * kBBlock) {
+        auto at = [&](int u) { return min(i0 + u * kBBlock, e1 - 1); };
+        auto in = [&](int u) { return i0 + u * kBBlock < e1; };
         if (phase == P_F1) {
-            w.p[i] = A::axpy(w.r[i], beta, A::axmy(w.p[i], omega, w.v[i]));
-        } else if (phase == P_F3) {
-            const V o = A::axmy(w.r[i], alpha, w.v[i]);
-            w.s[i] = o;
-            A::nrm2(acc[0], o);
-        } else if (phase == P_F5) {
-            V xi = A::axpy(w.x[i], alpha, w.p[i]);
-            if (half) {
-                w.x[i] = xi;
-                continue;
+            V a[U], b[U], q[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                a[u] = w.r[at(u)];
+                b[u] = w.p[at(u)];
+                q[u] = w.v[at(u)];
             }
-            const V si = w.s[i];
-            w.x[i] = A::axpy(xi, omega, si);
-            const V ri = A::axmy(si, omega, w.t[i]);
-            w.r[i] = ri;
-            A::dotc(acc[0], acc[1], w.rh[i], ri);
-            A::nrm2(acc[2], ri);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (in(u)) w.p[at(u)] = A::axpy(a[u], beta, A::axmy(b[u], omega, q[u]));
+            continue;
+        }
+        if (phase == P_F3) {
+            V a[U], q[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                a[u] = w.r[at(u)];
+                q[u] = w.v[at(u)];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (in(u)) {
+                    const V o = A::axmy(a[u], alpha, q[u]);
+                    w.s[at(u)] = o;
+                    A::nrm2(acc[0], o);
+                }
+            continue;
+        }
+        if (phase == P_F5 && !half) {
+            V xs[U], ps[U], ss[U], ts[U], hs[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                xs[u] = w.x[at(u)];
+                ps[u] = w.p[at(u)];
+                ss[u] = w.s[at(u)];
+                ts[u] = w.t[at(u)];
+                hs[u] = w.rh[at(u)];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (in(u)) {
+                    w.x[at(u)] = A::axpy(A::axpy(xs[u], alpha, ps[u]), omega, ss[u]);
+                    const V ri = A::axmy(ss[u], omega, ts[u]);
+                    w.r[at(u)] = ri;
+                    A::dotc(acc[0], acc[1], hs[u], ri);
+                    A::nrm2(acc[2], ri);
+                }
+            continue;
+        }
+        }
+        return;
+    }
+    for (int i = e0 + threadIdx.x; i < e1; i += kBBlock) {
+        if (phase == P_F5) {   // the half step: x += alpha p
+            w.x[i] = A::axpy(w.x[i], alpha, w.p[i]);
         } else if constexpr (!std::is_same<V, float2>::value) {
             if (phase == P_LOAD) w.x[i] = A::from_c128(sy.x[i]);
             else if (phase == P_STORE) sy.x[i] = A::to_c128(w.x[i]);

@@ -324,19 +324,20 @@ def run_kernel_case(args):
     print(json.dumps({"kernel_case": case, "arith": args.arith}))
 
 
-def compare_modes(hz, torch, full_c4, maxit):
+def compare_modes(hz, torch, full_c4, maxit, all_variants=False):
     """Mixed precision and the batched sweep against the plain complex128
     solver on the C4 frequency-sweep systems, each to relative residual 1e-10.
 
-    Every system is solved (x0 = 0) by: the binary64 solver (CSR-vector
-    SpMV), the double-float complex128 solver (block-flat SpMV), the mixed
-    solver (complex64 inner BiCGStab, binary64 outer refinement), the
-    double-float solver with Jacobi right preconditioning, double-float
-    BiCGStab(4) and TFQMR (iterations in steps of two products with A) and,
-    for all systems at once, the persistent batched solver in binary64 and
-    in double-float.  Times are CUDA
-    events around each call, after one untimed call of each kind (graph
-    capture).  Speedups are over the systems every variant solved."""
+    Every system is solved (x0 = 0) by the binary64 BiCGStab solver, the
+    mixed solver (complex64 inner BiCGStab, binary64 outer refinement) and
+    binary64 TFQMR, and all systems at once by the persistent batched solver
+    in binary64 and in mixed precision.  all_variants adds binary64
+    BiCGStab(4) and the double-float variants (BiCGStab, mixed, Jacobi,
+    BiCGStab(4), TFQMR, batched).  full_c4: all 64 systems (else the boxes
+    and the smallest cylinder, 32 systems).  Times are CUDA events around
+    each call, after one untimed call of each kind with a two-iteration cap
+    (graph capture, module loading).  Speedups are over the systems every
+    variant solved."""
     import workloads as W
     from workloads import configs as WC
     cyl = WC.C4_CYLINDERS if full_c4 else WC.C4_CYLINDERS[:1]
@@ -345,7 +346,8 @@ def compare_modes(hz, torch, full_c4, maxit):
     mats, bs = [], []
     for name, A, b in systems:
         # autotune: times the SpMV kinds and CSR-vector groups on this matrix;
-        # the batched solver's row tile per geometry is the group it keeps
+        # the batched solver's row tile (complex64 / double-float products)
+        # per geometry is the group it keeps
         M = hz.Matrix.from_csr(A, ff=True, c64=True, autotune=True)
         mats.append(M)
         bs.append(torch.as_tensor(b).to("cuda"))
@@ -361,28 +363,33 @@ def compare_modes(hz, torch, full_c4, maxit):
     variants = {
         "fp64_binary64": ("flat64p", dict(mode="fp64")),
         "mixed": ("flat64p", dict(mode="mixed")),
-        "bicgstab4_binary64": ("flat64p", dict(method="bicgstabl", ell=4)),
         "tfqmr_binary64": ("flat64p", dict(method="tfqmr")),
-        "fp64_double_float": ("ffflat", dict(mode="fp64")),
-        "mixed_double_float": ("ffflat", dict(mode="mixed")),
-        "fp64_double_float_jacobi": ("ffflat", dict(mode="fp64", precond="jacobi")),
-        "bicgstab4_double_float": ("ffflat", dict(method="bicgstabl", ell=4)),
-        "tfqmr_double_float": ("ffflat", dict(method="tfqmr")),
     }
+    if all_variants:
+        variants.update({
+            "bicgstab4_binary64": ("flat64p", dict(method="bicgstabl", ell=4)),
+            "fp64_double_float": ("ffflat", dict(mode="fp64")),
+            "mixed_double_float": ("ffflat", dict(mode="mixed")),
+            "fp64_double_float_jacobi": ("ffflat", dict(mode="fp64", precond="jacobi")),
+            "bicgstab4_double_float": ("ffflat", dict(method="bicgstabl", ell=4)),
+            "tfqmr_double_float": ("ffflat", dict(method="tfqmr")),
+        })
+    batched_variants = [("batched_fp64", "flat64p", "fp64"), ("batched_mixed", "flat64p", "mixed")]
+    if all_variants:
+        batched_variants.append(("batched_double_float", "ffflat", "fp64"))
     res = {k: [] for k in variants}
     groups = [M.props()["group"] for M in mats]
     for M, b, g in zip(mats, bs, groups):
         for key, (kind, kw) in variants.items():
             M.set_spmv(kind, g)
-            hz.zsolve(M, b, tol=1e-10, maxit=maxit, **kw)          # graph capture
+            hz.zsolve(M, b, tol=1e-10, maxit=2, **kw)          # graph capture
             (_, info), ms = timed(lambda: hz.zsolve(M, b, tol=1e-10, maxit=maxit, **kw))
             res[key].append((ms, info))
     batched = {}
-    for key, kind, mode in (("batched_fp64", "flat64p", "fp64"), ("batched_mixed", "flat64p", "mixed"),
-                            ("batched_double_float", "ffflat", "fp64")):
+    for key, kind, mode in batched_variants:
         for M, g in zip(mats, groups):   # the batch runs double-float when every handle's kind is;
             M.set_spmv(kind, g)          # its row tile is each handle's autotuned group
-        hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit, mode=mode)
+        hz.zsolve_batched(mats, bs, tol=1e-10, maxit=2, mode=mode)
         batched[key] = timed(lambda: hz.zsolve_batched(mats, bs, tol=1e-10, maxit=maxit, mode=mode))
     binfos = batched["batched_fp64"][0][1]
     ok_all = [all(res[k][i][1].converged for k in variants) and binfos[i].converged
@@ -410,7 +417,7 @@ def compare_modes(hz, torch, full_c4, maxit):
         k: base / max(out[k]["s_on_common"], 1e-12) for k in variants if k != "fp64_binary64"}
     out["speedup_vs_fp64_binary64_all_systems"] = {
         k: out["fp64_binary64"]["s_total"] / out[k]["s_total"]
-        for k in list(variants)[1:] + ["batched_fp64", "batched_mixed", "batched_double_float"]}
+        for k in list(variants)[1:] + [b[0] for b in batched_variants]}
     # the systems that the binary64 solver and the mixed and batched solvers
     # all solve: time to rel.res 1e-10 on exactly those
     ok_mb = [res["fp64_binary64"][i][1].converged and res["mixed"][i][1].converged
@@ -731,8 +738,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the mixed / batched / double-float comparison on the C4 sweep")
-    ap.add_argument("--c4-full", action="store_true",
-                    help="compare on all 64 C4 systems (default: the boxes and the smallest cylinder)")
+    ap.add_argument("--c4-subset", action="store_true",
+                    help="compare on 32 C4 systems (the boxes and the smallest cylinder; default: all 64)")
+    ap.add_argument("--compare-all", action="store_true",
+                    help="compare also binary64 BiCGStab(4) and the double-float variants")
     ap.add_argument("--compare-maxit", type=int, default=3000)
     ap.add_argument("--spmv-only", action="store_true",
                     help="profiling aid: build C2, run three SpMV launches of the chosen "
@@ -860,7 +869,7 @@ def main():
     if rank == 0 and not ff and not args.no_secondary:
         line["double_float"] = double_float_entry(hz, torch, A, rp, cl, vl, bd, args, stream)
     if rank == 0 and not args.no_compare:
-        line["compare"] = compare_modes(hz, torch, args.c4_full, args.compare_maxit)
+        line["compare"] = compare_modes(hz, torch, not args.c4_subset, args.compare_maxit, args.compare_all)
         line["spmv_h1"] = spmv_h1(hz, torch, stream)
         line["spmv_c64_c2"] = spmv_c64_c2(hz, torch, A, stream)
         line["adjoint_c5"] = adjoint_c5(hz, torch, stream)

@@ -67,7 +67,8 @@ enum {
     HZ_FLAG_C64 = 4u,        /* also build the complex64 copy used by the mixed solver */
     HZ_FLAG_AUTOTUNE = 8u,   /* time the SpMV variants once on this matrix and keep the fastest;
                                 `group` becomes the fastest binary64 CSR-vector group (the row
-                                tile of this matrix in hz_zsolve_batched) whichever kind wins */
+                                tile of this matrix in hz_zsolve_batched's complex64 and
+                                double-float products) whichever kind wins */
     HZ_FLAG_FF = 16u         /* also build the double-float split of the values and use the
                                 double-float SpMV: every binary64 value is carried as hi + lo
                                 binary32 parts (48 significant bits, NOT binary64) on the
@@ -349,7 +350,9 @@ HZ_API hz_status hz_zsolve_opts(hz_mat *A, const hz_z *d_b, hz_z *d_x,
  * and update, complex64 inner BiCGStab to 1e-5 with at most 1000 iterations,
  * at most 50 refinement steps, maxit capping the inner iterations in total,
  * the best iterate kept), each system at its own stage; the handles' complex64
- * copies are made on demand (synchronising).  d_x[s] holds x0 on entry and
+ * copies are made on demand (synchronising).  Binary64 products run on each
+ * handle's row blocks (the block-flat core of HZ_SPMV_FLAT64), complex64 and
+ * double-float ones with `group` lanes per row.  d_x[s] holds x0 on entry and
  * the solution on exit.  h_info has nsys entries.  Synchronises `stream`.
  * Errors: HZ_ERR_ARG (nsys outside 0..1024, unknown mode, null pointers),
  * HZ_ERR_ALLOC, HZ_ERR_TIMEOUT (a grid-barrier wait expired).

@@ -578,7 +578,7 @@ def adjoint_c5(hz, torch, stream, reps=10):
     _, ms_bwd = timed(lambda: loss.backward())
     fwd_info = x.grad_fn.fwd_info if hasattr(x.grad_fn, "fwd_info") else None
     conv = {"workload": "C5 inverse problem at 32^3 (n = 32,768), TFQMR binary64 to 1e-12",
-            "forward_ms": ms_fwd, "backward_ms": ms_bwd, "loss": float(loss),
+            "forward_ms": ms_fwd, "backward_ms": ms_bwd, "loss": float(loss.detach()),
             "forward_iters": fwd_info.iters if fwd_info else None}
     M32.close()
 

@@ -630,6 +630,11 @@ def adjoint_c5(hz, torch, stream, reps=10):
                         "outer_on_pattern": {"us": 1e3 * ms_outer, "algorithmic_bytes": ob,
                                              "gbs": ob / (ms_outer / 1e3) / 1e9,
                                              "frac": ob / (ms_outer / 1e3) / 1e9 / peak,
+                                             # one complex product per entry: 4 binary64
+                                             # pipe operations, the kernel's real limit
+                                             "fp64_lane_ops": 4 * nnz,
+                                             "frac_of_fp64_probe_rate":
+                                                 4 * nnz / (ms_outer / 1e3) / (FP64_PROBE_TFLOPS / 2 * 1e12),
                                              "note": "L2 flushed before each launch; the 29 MB it writes fits in L2"},
                         "diag_grad": {"us": 1e3 * ms_diag, "gbs": 48 * n / (ms_diag / 1e3) / 1e9,
                                       "l2_resident": True}}}

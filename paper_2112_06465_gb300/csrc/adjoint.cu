@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "hz_internal.cuh"
+#include "spmv.cuh"   // kFlatCap: the entries of a row block with more than one row
 
 namespace hz {
 
@@ -38,9 +39,11 @@ __global__ void __launch_bounds__(256) k_outer_pattern(int n, const int *__restr
 // complete rows and <= 512 entries, or one longer row): one warp per block,
 // lane l takes entries kb + l, kb + l + 32, ... so that every lane of every
 // binary64 instruction is busy (the binary64 pipe is the limit here: four
-// multiply-adds per entry) and the writes of g are coalesced; each lane
-// walks the block's row pointers (shared memory) forward to the row of its
-// next entry.
+// multiply-adds per entry) and the writes of g are coalesced.  The row of
+// each entry comes from a per-warp table in shared memory (one byte per
+// entry, filled by the lane that owns the row), so an entry costs one table
+// read instead of a walk over the row pointers; a block with one row (the
+// only kind longer than kFlatCap entries) needs no table.
 constexpr int kOpThreads = 128;
 constexpr int kOpGroup = 8;
 __global__ void __launch_bounds__(kOpThreads) k_outer_flat(int nfblk, const int *__restrict__ fblk,
@@ -50,8 +53,10 @@ __global__ void __launch_bounds__(kOpThreads) k_outer_flat(int nfblk, const int 
                                                            const double2 *__restrict__ mu,
                                                            const double2 *__restrict__ x, double2 *__restrict__ g) {
     __shared__ int rps[kOpThreads / 32][33];
+    __shared__ unsigned char rows_s[kOpThreads / 32][kFlatCap];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int *rp = rps[w];
+    unsigned char *rowof = rows_s[w];
     const int step = gridDim.x * (kOpThreads / 32);
     for (int b = blockIdx.x * (kOpThreads / 32) + w; b < nfblk; b += step) {
         const int r0 = __ldg(fblk + b), r1 = __ldg(fblk + b + 1);
@@ -60,7 +65,11 @@ __global__ void __launch_bounds__(kOpThreads) k_outer_flat(int nfblk, const int 
         if (lane < nr) rp[lane] = __ldg(rowptr + r0 + lane);
         if (lane == 0) rp[nr] = ke;
         __syncwarp();
-        int j = 0;   // row (offset in the block) of this lane's current entry
+        if (nr > 1) {   // (then ke - kb <= kFlatCap)
+            if (lane < nr)
+                for (int k = rp[lane]; k < rp[lane + 1]; ++k) rowof[k - kb] = (unsigned char)lane;
+            __syncwarp();
+        }
         // kOpGroup entries per lane at a time: their column loads, x gathers
         // and mu loads are all issued before the first product
         for (int k0 = kb + lane; k0 < ke; k0 += 32 * kOpGroup) {
@@ -72,17 +81,20 @@ __global__ void __launch_bounds__(kOpThreads) k_outer_flat(int nfblk, const int 
                 c[u] = k < ke ? __ldg(col + k) : -1;
             }
 #pragma unroll
-            for (int u = 0; u < kOpGroup; ++u) {
+            for (int u = 0; u < kOpGroup; ++u) {   // mu by row: needs no column
                 const int k = k0 + 32 * u;
-                while (j < nr - 1 && rp[j + 1] <= k) ++j;
-                m[u] = c[u] >= 0 ? __ldg(mu + r0 + j) : make_double2(0.0, 0.0);
-                xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_double2(0.0, 0.0);
+                const int j = (nr > 1 && k < ke) ? rowof[k - kb] : 0;
+                m[u] = k < ke ? __ldg(mu + r0 + j) : make_double2(0.0, 0.0);
             }
+#pragma unroll
+            for (int u = 0; u < kOpGroup; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_double2(0.0, 0.0);
 #pragma unroll
             for (int u = 0; u < kOpGroup; ++u) {
                 if (c[u] < 0) continue;
-                const double2 p = cmul(m[u], xv[u]);
-                g[k0 + 32 * u] = make_double2(-p.x, p.y);
+                // -conj(mu x) = (Im mu Im x - Re mu Re x, Re mu Im x + Im mu Re x):
+                // the sign rides on the operands, four binary64 operations
+                const double2 a = m[u], v = xv[u];
+                g[k0 + 32 * u] = make_double2(fma(a.y, v.y, -a.x * v.x), fma(a.x, v.y, a.y * v.x));
             }
         }
         __syncwarp();

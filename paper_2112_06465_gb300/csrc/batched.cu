@@ -53,7 +53,10 @@ constexpr int kBBlock = 256;
 // block-flat products, the double-float one, the mixed one
 constexpr int kBMinBlocks = HZ_BATCHED_MIN_BLOCKS;
 template <class V> struct BMin { static constexpr int value = std::is_same<V, double2>::value ? kBMinBlocks : 3; };
-constexpr int kBMinBlocksMixed = 4;
+#ifndef HZ_BATCHED_MIXED_MIN_BLOCKS
+#define HZ_BATCHED_MIXED_MIN_BLOCKS 4
+#endif
+constexpr int kBMinBlocksMixed = HZ_BATCHED_MIXED_MIN_BLOCKS;
 #ifndef HZ_BATCHED_FLAT_G
 #define HZ_BATCHED_FLAT_G 2
 #endif

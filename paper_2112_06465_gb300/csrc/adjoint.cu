@@ -15,6 +15,13 @@
 
 namespace hz {
 
+// -conj(a b) = (Im a Im b - Re a Re b, Re a Im b + Im a Re b), with the sign
+// on the FMA operands: four binary64 operations (negating the finished
+// product would take a fifth on the binary64 pipe)
+__device__ __forceinline__ double2 neg_conj_mul(double2 a, double2 b) {
+    return make_double2(fma(a.y, b.y, -a.x * b.x), fma(a.x, b.y, a.y * b.x));
+}
+
 // W lanes per row (W near the mean row length, so short rows do not leave
 // most of a warp idle): every stored entry (i, j) gets -conj(mu_i x_j); the
 // row's entries are read and written contiguously by its W lanes
@@ -28,9 +35,7 @@ __global__ void __launch_bounds__(256) k_outer_pattern(int n, const int *__restr
         const double2 m = __ldg(mu + i);
         const int beg = __ldg(rowptr + i), end = __ldg(rowptr + i + 1);
         for (int k = beg + lane; k < end; k += W) {
-            const double2 xj = __ldg(x + __ldg(col + k));
-            const double2 p = cmul(m, xj);
-            g[k] = make_double2(-p.x, p.y);
+            g[k] = neg_conj_mul(m, __ldg(x + __ldg(col + k)));
         }
     }
 }
@@ -91,10 +96,7 @@ __global__ void __launch_bounds__(kOpThreads) k_outer_flat(int nfblk, const int 
 #pragma unroll
             for (int u = 0; u < kOpGroup; ++u) {
                 if (c[u] < 0) continue;
-                // -conj(mu x) = (Im mu Im x - Re mu Re x, Re mu Im x + Im mu Re x):
-                // the sign rides on the operands, four binary64 operations
-                const double2 a = m[u], v = xv[u];
-                g[k0 + 32 * u] = make_double2(fma(a.y, v.y, -a.x * v.x), fma(a.x, v.y, a.y * v.x));
+                g[k0 + 32 * u] = neg_conj_mul(m[u], xv[u]);
             }
         }
         __syncwarp();
@@ -123,9 +125,8 @@ __global__ void k_set_diag(int n, const int *__restrict__ pos, const double2 *__
 __global__ void k_diag_grad(int n, const double2 *__restrict__ mu, const double2 *__restrict__ x, double2 c,
                             double2 *__restrict__ gt) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double2 p = cmul(mu[i], x[i]);
-        const double2 ga = make_double2(-p.x, p.y);          // -conj(mu_i x_i)
-        gt[i] = cmul(cconj(c), ga);
+        // conj(c) (-conj(mu_i x_i)) = -conj(c mu_i x_i)
+        gt[i] = neg_conj_mul(c, cmul(mu[i], x[i]));
     }
 }
 

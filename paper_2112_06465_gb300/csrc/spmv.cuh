@@ -703,7 +703,11 @@ __device__ __forceinline__ void flat_rows_ff_tma(const MatView<double2> &A, cons
 }
 
 // ---------------------------------------------------------------------------
-// Block-flat binary64 core with contiguous lane runs (HZ_SPMV_FLAT64).
+// Block-flat binary64 core with contiguous lane runs (HZ_SPMV_FLAT64 on the
+// caller's CSR arrays; HZ_SPMV_FLAT64P, the default, on the handle's packed
+// copy of the row blocks, whose slots hold step u of the 32 lane runs
+// side by side so every load is coalesced, and whose groups without a
+// nonzero imaginary part store none).
 //
 // On GB300 the binary64 pipe retires about 1.7 lanes per SM per clock, and a
 // warp instruction occupies it for the same time whether 32 lanes or one are

@@ -663,7 +663,7 @@ static hz_status get_solver(hz_mat *A, uint32_t mode, cudaStream_t s, Solver **o
         // iteration), so plain launches are the default
         const char *pdl_env = getenv("HZ_PDL");
         S->pdl = pdl_env && atoi(pdl_env) != 0;
-        S->grid_vec = stream_grid(d, (A->n + kVecUnroll - 1) / kVecUnroll, kVecBlock, 8);
+        S->grid_vec = vec_grid(d, A->n);
         hz_status st = HZ_OK;
         // the double-float iteration runs on A scaled to unit size, so that
         // A p and A s stay inside the binary32 exponent range

@@ -538,7 +538,7 @@ static hz_status bl_get_solver(hz_mat *A, int ell, BlSolver **out) {
     S->group = A->group;
     S->grid_spmv = spmv_grid(A, S->kind, S->group);
     S->grid_spmv_cv = spmv_grid(A, d64_kind(A, S->kind), S->group);
-    S->grid_vec = stream_grid(d, (A->n + kVecUnroll - 1) / kVecUnroll, kVecBlock, 8);
+    S->grid_vec = vec_grid(d, A->n);
     const int np = ell + ell * (ell + 1) / 2;
     S->grid_gram = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)2 * d.num_sms,
                                                                   (int64_t)kMaxRedBlocks * kMaxRedValues / (2 * np),

@@ -95,35 +95,50 @@ struct Info {
     int zero_x, pad;
 };
 
+// Element walkers of the vector kernels.  Thread t of the T = gridDim.x *
+// blockDim.x threads takes elements t, t + T, t + 2T, ..., kVecUnroll (or U)
+// of them per pass, so consecutive threads touch consecutive elements and a
+// grid larger than n / kVecUnroll threads spreads a short vector over more
+// SMs (vec_grid below) instead of leaving its blocks idle.
 template <class F>
 __device__ __forceinline__ void vec_tiles(int n, F f) {
-    const int tile = kVecUnroll * blockDim.x;
-    for (int base = blockIdx.x * tile; base < n; base += gridDim.x * tile) {
+    const int T = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x + threadIdx.x; base < n; base += kVecUnroll * T) {
 #pragma unroll
         for (int u = 0; u < kVecUnroll; ++u) {
-            const int i = base + u * blockDim.x + threadIdx.x;
+            const int i = base + u * T;
             if (i < n) f(i);
         }
     }
 }
 
-// Tile walker that issues every load of a tile before the first compute:
+// The same walk issuing every load of a pass before the first compute:
 // load(i) returns the element's inputs (indices are clamped to n-1, so the
 // loads need no branch), comp(i, in) computes and stores for i < n.
 template <int U = kVecUnroll, class Ld, class Cp>
 __device__ __forceinline__ void vec_tiles_staged(int n, Ld load, Cp comp) {
     using In = decltype(load(0));
-    const int tile = U * blockDim.x;
-    for (int base = blockIdx.x * tile; base < n; base += gridDim.x * tile) {
+    const int T = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x + threadIdx.x; base < n; base += U * T) {
         In in[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) in[u] = load(min(base + u * (int)blockDim.x + (int)threadIdx.x, n - 1));
+        for (int u = 0; u < U; ++u) in[u] = load(min(base + u * T, n - 1));
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int i = base + u * blockDim.x + threadIdx.x;
+            const int i = base + u * T;
             if (i < n) comp(i, in[u]);
         }
     }
+}
+
+// grid of the vector kernels over n elements: kVecUnroll elements per
+// thread for long vectors; a short vector gets at least two blocks per SM
+// (down to one element per thread), since its binary64 work would otherwise
+// sit on a few SMs
+inline int vec_grid(const DevInfo &d, int n) {
+    const int64_t per_unroll = ((int64_t)n + (int64_t)kVecUnroll * kVecBlock - 1) / ((int64_t)kVecUnroll * kVecBlock);
+    const int64_t spread = std::min<int64_t>(((int64_t)n + kVecBlock - 1) / kVecBlock, 2 * (int64_t)d.num_sms);
+    return stream_grid(d, std::max(per_unroll, spread) * kVecBlock, kVecBlock, 8);
 }
 
 template <class V> struct In2 { V a, b; };

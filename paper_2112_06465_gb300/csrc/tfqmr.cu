@@ -22,7 +22,7 @@
 // u, v, w, d, A u and rho, tau by the same factor if x is updated with
 // eta / G (G the accumulated factor) and the bound uses tau / G.  When
 // ||v||^2 or tau^2 passes 2^120 the next iteration first scales those
-// vectors by 2^-64 (exact) and the scalars with them.
+// vectors by 2^-64 (exact) and the scalars with them (inside Q1).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -152,26 +152,40 @@ struct EpiTqV : EpiBase<V> {
     }
 };
 
-// Q1: u2 = u1 - alpha v, w -= alpha A u1, ||w||^2 -> half step 2j+1
+// Q1: u2 = u1 - alpha v, w -= alpha A u1, ||w||^2 -> half step 2j+1.
+// With the range guard's flag set, u1, v, w, d and A u1 are first scaled by
+// 2^-64 (exact) element by element, in place (the same thread reads and
+// writes each element, so no other kernel is needed)
 template <class V>
 __global__ void __launch_bounds__(kVecBlock) k_tq_half1(int n, StateOf<V> *st, TqExtra *q, V *__restrict__ u2,
-                                                        const V *__restrict__ u1, const V *__restrict__ v,
-                                                        V *__restrict__ w, const V *__restrict__ au1,
-                                                        RedScratch red) {
+                                                        V *__restrict__ u1, V *__restrict__ v, V *__restrict__ w,
+                                                        V *__restrict__ d, V *__restrict__ au1, RedScratch red) {
     using A = Ar<V>;
     if (st->done) return;
     const typename A::S alpha = A::scal(st->alpha);
+    const bool pend = q->pend != 0;   // read by every block before the last one resets it
     typename A::Acc acc[1];
     A::acc_zero(acc[0]);
     vec_tiles(n, [&](int i) {
-        u2[i] = A::axmy(u1[i], alpha, v[i]);
-        const V wi = A::axmy(w[i], alpha, au1[i]);
+        V u1i = u1[i], vi = v[i], wi = w[i], ai = au1[i];
+        if (pend) {
+            u1i = A::pow2(u1i, kTqShrink);
+            vi = A::pow2(vi, kTqShrink);
+            wi = A::pow2(wi, kTqShrink);
+            ai = A::pow2(ai, kTqShrink);
+            u1[i] = u1i;
+            v[i] = vi;
+            au1[i] = ai;
+            d[i] = A::pow2(d[i], kTqShrink);
+        }
+        u2[i] = A::axmy(u1i, alpha, vi);
+        wi = A::axmy(wi, alpha, ai);
         w[i] = wi;
         A::nrm2(acc[0], wi);
     });
     typename A::R tot[1];
     if (vec_reduce<V, 1>(acc, red, tot) && threadIdx.x == 0) {
-        if (q->pend) {   // the vectors were scaled by k_tq_rescale before this kernel
+        if (q->pend) {   // the vectors were scaled above
             q->pend = 0;
             q->tau *= kTqShrink;
             st->rho = make_double2(st->rho.x * kTqShrink, st->rho.y * kTqShrink);
@@ -180,21 +194,6 @@ __global__ void __launch_bounds__(kVecBlock) k_tq_half1(int n, StateOf<V> *st, T
         tq_half_step(st, q, (double)tot[0], q->coef1, q->eta1);
         q->eta1x = make_double2(q->eta1.x * q->xs, q->eta1.y * q->xs);
     }
-}
-
-// range guard: scale u1, v, w, d and A u1 by 2^-64 (exact) when flagged
-template <class V>
-__global__ void __launch_bounds__(kVecBlock) k_tq_rescale(int n, const StateOf<V> *st, const TqExtra *q,
-                                                          V *__restrict__ u1, V *__restrict__ v, V *__restrict__ w,
-                                                          V *__restrict__ d, V *__restrict__ au1) {
-    if (st->done || !q->pend) return;
-    vec_tiles(n, [&](int i) {
-        u1[i] = Ar<V>::pow2(u1[i], kTqShrink);
-        v[i] = Ar<V>::pow2(v[i], kTqShrink);
-        w[i] = Ar<V>::pow2(w[i], kTqShrink);
-        d[i] = Ar<V>::pow2(d[i], kTqShrink);
-        au1[i] = Ar<V>::pow2(au1[i], kTqShrink);
-    });
 }
 
 // Q2 epilogue: au = A u2; d/x update of half step 2j+1; w -= alpha au;
@@ -331,8 +330,7 @@ static hz_status tq_build_graph(TqSolver *S, const hz_mat *A, cudaGraph_t g) {
     cudaGraph_t body;
     HZ_TRY(add_while(g, leaves, h, &wn, &body));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
-    k_tq_rescale<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->q, u1, v, w, d, au1);
-    k_tq_half1<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->q, u2, u1, v, w, au1, S->red);
+    k_tq_half1<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->q, u2, u1, v, w, d, au1, S->red);
     EpiTqW<V> ew;
     ew.st = st; ew.q = S->q; ew.ctl = S->dctl; ew.au = au; ew.d = d; ew.x = x; ew.w = w; ew.u1 = u1; ew.rh = rh;
     tq_spmv<V>(S, A, u2, ew, cs);
@@ -368,7 +366,7 @@ static hz_status tq_get_solver(hz_mat *A, TqSolver **out) {
     S->group = A->group;
     S->grid_spmv = spmv_grid(A, S->kind, S->group);
     S->grid_spmv_cv = spmv_grid(A, d64_kind(A, S->kind), S->group);
-    S->grid_vec = stream_grid(dv, (A->n + kVecUnroll - 1) / kVecUnroll, kVecBlock, 8);
+    S->grid_vec = vec_grid(dv, A->n);
     const size_t nb = (size_t)A->n * 16;
     void **vecs[] = {&S->x, &S->w, &S->u1, &S->u2, &S->v, &S->d, &S->au1, &S->au, &S->rh};
     for (void **p : vecs) HZ_TQ_ALLOC(*p, nb);

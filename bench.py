@@ -272,7 +272,8 @@ def run_kernel_case(args):
     elements, twice; outer: the adjoint outer product on C5 64^3, three
     times; batched: a four-box binary64 sweep, 100 iterations, twice; solve:
     two C2 solves of HZ_PROFILE_UNROLL iterations (set HZ_PROFILE_UNROLL=k so
-    the iteration kernels are plain graph nodes)."""
+    the iteration kernels are plain graph nodes) with --solve-method,
+    --solve-mode and --precond."""
     import numpy as np
     import torch
     import paper_2112_06465_gb300 as hz
@@ -281,7 +282,7 @@ def run_kernel_case(args):
     case = args.kernel_case
     if case in ("spmv", "cspmv", "solve"):
         A, b = build_workload()
-        M = hz.Matrix.from_csr(A, ff=args.arith == "ff", c64=case == "cspmv")
+        M = hz.Matrix.from_csr(A, ff=args.arith == "ff", c64=case == "cspmv" or args.solve_mode == "mixed")
         if args.spmv:
             M.set_spmv(args.spmv, args.group)
         if case == "cspmv":
@@ -295,8 +296,13 @@ def run_kernel_case(args):
         else:
             bd = torch.as_tensor(b).to(dev)
             k = int(os.environ.get("HZ_PROFILE_UNROLL", "3"))
+            kw = dict(method=args.solve_method, mode=args.solve_mode, precond=args.precond)
+            it = k
+            if args.solve_method == "bicgstabl":   # maxit counts BiCG steps, l = 4 per iteration
+                kw["ell"] = 4
+                it = 4 * k
             for _ in range(2):
-                hz.zsolve(M, bd, tol=1e-10, maxit=k)
+                hz.zsolve(M, bd, tol=1e-10, maxit=it, **kw)
     elif case == "blas":
         n = 100_000_000
         x = torch.randn(n, dtype=torch.complex128, device=dev)
@@ -753,6 +759,12 @@ def main():
                          "arithmetic (--arith, --group) and exit without timing")
     ap.add_argument("--kernel-case", default=None, choices=["spmv", "cspmv", "blas", "outer", "batched", "solve"],
                     help="profiling aid: run one small case of a kernel family and exit (see run_kernel_case)")
+    ap.add_argument("--solve-method", default="bicgstab", choices=["bicgstab", "tfqmr", "bicgstabl"],
+                    help="--kernel-case solve: the Krylov method (bicgstabl with l = 4)")
+    ap.add_argument("--solve-mode", default="fp64", choices=["fp64", "mixed"],
+                    help="--kernel-case solve: plain binary64 or mixed precision")
+    ap.add_argument("--precond", default="none", choices=["none", "jacobi"],
+                    help="--kernel-case solve: right preconditioner")
     ap.add_argument("--group", type=int, default=4, help="lanes per row of the CSR-vector kinds")
     ap.add_argument("--spmv", default=None, choices=["csr", "sell", "ff", "sellff", "ffflat", "fftma", "flat64", "flat64p"],
                     help="force an SpMV variant (default: the handle's own choice)")

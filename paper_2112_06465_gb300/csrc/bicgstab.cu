@@ -323,8 +323,8 @@ struct EpiOuter : EpiBase<V> {
         } else {
             in->done = 1;
         }
-        cudaGraphSetConditional(h_inner, (!done && !in->done) ? 1 : 0);
-        cudaGraphSetConditional(h_outer, done ? 0 : 1);
+        set_cond(h_inner, (!done && !in->done) ? 1 : 0);
+        set_cond(h_outer, done ? 0 : 1);
     }
 };
 
@@ -542,12 +542,8 @@ static hz_status build_fp64_graph(Solver *S, const hz_mat *A, cudaGraph_t g) {
     V *x = (V *)S->x, *r = (V *)S->r, *rh = (V *)S->rh, *p = (V *)S->p, *v = (V *)S->v, *s = (V *)S->s,
       *t = (V *)S->t;
     StateOf<V> *st = (StateOf<V> *)S->st;
-    // HZ_PROFILE_UNROLL=k (environment) builds a plain graph with k copies of
-    // the iteration and no conditional node, for profilers that do not
-    // descend into conditional bodies; the kernels are the same (once the
-    // solve is done, the remaining copies exit at their first instruction)
-    const char *unroll_env = getenv("HZ_PROFILE_UNROLL");
-    const int unroll = unroll_env ? atoi(unroll_env) : 0;
+    // HZ_PROFILE_UNROLL=k: k straight-line copies of the iteration (krylov.cuh)
+    const int unroll = profile_unroll();
     cudaGraphConditionalHandle h = 0;
     if (unroll <= 0) HZ_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, mode));
@@ -589,11 +585,27 @@ static hz_status build_mixed_graph(Solver *S, const hz_mat *A, cudaGraph_t g) {
     const int n = S->n;
     std::vector<cudaGraphNode_t> leaves;
     V *x = (V *)S->x;
-    cudaGraphConditionalHandle ho, hi;
-    HZ_CUDA(cudaGraphConditionalHandleCreate(&ho, g, 1, cudaGraphCondAssignDefault));
+    const int unroll = profile_unroll();
+    cudaGraphConditionalHandle ho = 0, hi = 0;
+    if (unroll <= 0) HZ_CUDA(cudaGraphConditionalHandleCreate(&ho, g, 1, cudaGraphCondAssignDefault));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, mode));
     cudaMemcpyAsync(S->dctl, S->hctl, sizeof(Ctl), cudaMemcpyHostToDevice, cs);
     k_mixed_start<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->dctl, S->ost, S->total, x);
+    if (unroll > 0) {   // one refinement step with `unroll` inner iterations, straight-line
+        EpiOuter<V> eo;
+        eo.ost = S->ost; eo.in = S->st32; eo.info = S->dinfo; eo.ctl = S->dctl; eo.r = S->r32; eo.rh = S->rh32;
+        eo.p = S->p32; eo.v = S->v32; eo.d = S->d32; eo.total_inner = S->total; eo.h_outer = 0; eo.h_inner = 0;
+        spmv_on<V>(S, A, x, eo, cs);
+        for (int k = 0; k < unroll; ++k)
+            launch_iteration<float2>(S, A, S->st32, S->d32, S->r32, S->rh32, S->p32, S->v32, S->s32, S->t32,
+                                     S->total, 0, cs);
+        k_mixed_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->ost, x, (V *)S->xbest, S->d32);
+        k_mixed_copy_out<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->dctl, S->ost, S->total, S->dinfo, x,
+                                                              (const V *)S->xbest, A->fault);
+        cudaMemcpyAsync(S->hinfo, S->dinfo, sizeof(Info), cudaMemcpyDeviceToHost, cs);
+        HZ_CUDA(cudaStreamEndCapture(cs, &g));
+        return HZ_OK;
+    }
     HZ_TRY(capture_leaves(cs, &leaves));
     HZ_CUDA(cudaStreamEndCapture(cs, &g));
     cudaGraphNode_t wo;

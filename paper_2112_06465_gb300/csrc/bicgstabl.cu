@@ -447,36 +447,44 @@ static hz_status bl_build_graph(BlSolver *S, const hz_mat *A, cudaGraph_t g) {
     auto Rv = [&](int i) { return R + (size_t)i * n; };
     auto Uv = [&](int i) { return U + (size_t)i * n; };
     StateOf<V> *st = (StateOf<V> *)S->st;
-    cudaGraphConditionalHandle h;
+    const int unroll = profile_unroll();
+    cudaGraphConditionalHandle h = 0;
     std::vector<cudaGraphNode_t> leaves;
-    HZ_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    if (unroll <= 0) HZ_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, mode));
     cudaMemcpyAsync(S->dctl, S->hctl, sizeof(Ctl), cudaMemcpyHostToDevice, cs);
     k_init_x<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->dctl, x);
     EpiBlInit<V> ei;
     ei.st = st; ei.info = S->dinfo; ei.ctl = S->dctl; ei.r0 = Rv(0); ei.rh = rh; ei.u0 = Uv(0); ei.h = h;
     bl_spmv<V>(S, A, x, ei, cs);
-    HZ_TRY(capture_leaves(cs, &leaves));
-    HZ_CUDA(cudaStreamEndCapture(cs, &g));
-    cudaGraphNode_t wn;
-    cudaGraph_t body;
-    HZ_TRY(add_while(g, leaves, h, &wn, &body));
-    HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
-    for (int j = 0; j < ell; ++j) {
-        k_bl_u<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, j, st, U, R);
-        EpiBlU<V> eu;
-        eu.st = st; eu.u_next = Uv(j + 1); eu.rh = rh; eu.s = S->op_scale;
-        bl_spmv<V>(S, A, Uv(j), eu, cs);
-        k_bl_r<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, j, st, S->dctl, R, U, x, S->red);
-        EpiBlR<V> er;
-        er.st = st; er.r_next = Rv(j + 1); er.rh = rh; er.want_rho = j + 1 < ell; er.s = S->op_scale;
-        bl_spmv<V>(S, A, Rv(j), er, cs);
+    auto iteration = [&]() {
+        for (int j = 0; j < ell; ++j) {
+            k_bl_u<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, j, st, U, R);
+            EpiBlU<V> eu;
+            eu.st = st; eu.u_next = Uv(j + 1); eu.rh = rh; eu.s = S->op_scale;
+            bl_spmv<V>(S, A, Uv(j), eu, cs);
+            k_bl_r<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, j, st, S->dctl, R, U, x, S->red);
+            EpiBlR<V> er;
+            er.st = st; er.r_next = Rv(j + 1); er.rh = rh; er.want_rho = j + 1 < ell; er.s = S->op_scale;
+            bl_spmv<V>(S, A, Rv(j), er, cs);
+        }
+        k_bl_gram<V><<<S->grid_gram, kVecBlock, 0, cs>>>(n, ell, st, R, S->red, S->ex);
+        k_bl_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, ell, st, S->dctl, x, R, U, rh, S->ex, S->red);
+    };
+    if (unroll > 0) {
+        for (int k = 0; k < unroll; ++k) iteration();
+    } else {
+        HZ_TRY(capture_leaves(cs, &leaves));
+        HZ_CUDA(cudaStreamEndCapture(cs, &g));
+        cudaGraphNode_t wn;
+        cudaGraph_t body;
+        HZ_TRY(add_while(g, leaves, h, &wn, &body));
+        HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
+        iteration();
+        k_loop_guard<typename Ar<V>::St><<<1, 1, 0, cs>>>(st, S->dctl, 1, h);
+        HZ_CUDA(cudaStreamEndCapture(cs, &body));
+        HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, &wn, nullptr, 1, mode));
     }
-    k_bl_gram<V><<<S->grid_gram, kVecBlock, 0, cs>>>(n, ell, st, R, S->red, S->ex);
-    k_bl_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, ell, st, S->dctl, x, R, U, rh, S->ex, S->red);
-    k_loop_guard<typename Ar<V>::St><<<1, 1, 0, cs>>>(st, S->dctl, 1, h);
-    HZ_CUDA(cudaStreamEndCapture(cs, &body));
-    HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, &wn, nullptr, 1, mode));
     EpiTrue<V> et;
     et.st = st; et.info = S->dinfo; et.ctl = S->dctl;
     bl_spmv<V>(S, A, x, et, cs);

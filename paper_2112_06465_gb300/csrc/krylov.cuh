@@ -5,6 +5,7 @@
 // copy-out steps and the CUDA-graph capture helpers.
 #pragma once
 
+#include <cstdlib>
 #include <vector>
 
 #include "spmv.cuh"
@@ -251,6 +252,16 @@ static inline hz_status capture_leaves(cudaStream_t s, std::vector<cudaGraphNode
     HZ_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd));
     leaves->assign(deps, deps + nd);
     return HZ_OK;
+}
+
+// HZ_PROFILE_UNROLL=k (environment, read when a solver graph is built): the
+// graph holds k straight-line copies of its loop body instead of a WHILE
+// node, for profilers that do not descend into conditional bodies.  The
+// kernels are the same; condition handles are 0, so nothing sets a
+// condition, and once a solve is done the remaining copies exit at once.
+static inline int profile_unroll() {
+    const char *e = getenv("HZ_PROFILE_UNROLL");
+    return e ? atoi(e) : 0;
 }
 
 static inline hz_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,

@@ -311,9 +311,10 @@ static hz_status tq_build_graph(TqSolver *S, const hz_mat *A, cudaGraph_t g) {
     V *x = (V *)S->x, *w = (V *)S->w, *u1 = (V *)S->u1, *u2 = (V *)S->u2, *v = (V *)S->v, *d = (V *)S->d,
       *au1 = (V *)S->au1, *au = (V *)S->au, *rh = (V *)S->rh;
     StateOf<V> *st = (StateOf<V> *)S->st;
-    cudaGraphConditionalHandle h;
+    const int unroll = profile_unroll();
+    cudaGraphConditionalHandle h = 0;
     std::vector<cudaGraphNode_t> leaves;
-    HZ_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    if (unroll <= 0) HZ_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
     HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, mode));
     cudaMemcpyAsync(S->dctl, S->hctl, sizeof(Ctl), cudaMemcpyHostToDevice, cs);
     k_init_x<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, S->dctl, x);
@@ -324,21 +325,28 @@ static hz_status tq_build_graph(TqSolver *S, const hz_mat *A, cudaGraph_t g) {
     EpiTqV<V> ev;
     ev.st = st; ev.q = S->q; ev.ctl = S->dctl; ev.au1 = au1; ev.v = v; ev.rh = rh; ev.h = h;
     tq_spmv<V>(S, A, u1, ev, cs);   // v_0 = A u_1, alpha; sets the loop condition
-    HZ_TRY(capture_leaves(cs, &leaves));
-    HZ_CUDA(cudaStreamEndCapture(cs, &g));
-    cudaGraphNode_t wn;
-    cudaGraph_t body;
-    HZ_TRY(add_while(g, leaves, h, &wn, &body));
-    HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
-    k_tq_half1<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->q, u2, u1, v, w, d, au1, S->red);
     EpiTqW<V> ew;
     ew.st = st; ew.q = S->q; ew.ctl = S->dctl; ew.au = au; ew.d = d; ew.x = x; ew.w = w; ew.u1 = u1; ew.rh = rh;
-    tq_spmv<V>(S, A, u2, ew, cs);
-    k_tq_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->q, d, x, u2, u1, w, au, v);
-    tq_spmv<V>(S, A, u1, ev, cs);
-    k_loop_guard<typename Ar<V>::St><<<1, 1, 0, cs>>>(st, S->dctl, 1, h);
-    HZ_CUDA(cudaStreamEndCapture(cs, &body));
-    HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, &wn, nullptr, 1, mode));
+    auto iteration = [&]() {
+        k_tq_half1<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->q, u2, u1, v, w, d, au1, S->red);
+        tq_spmv<V>(S, A, u2, ew, cs);
+        k_tq_update<V><<<S->grid_vec, kVecBlock, 0, cs>>>(n, st, S->q, d, x, u2, u1, w, au, v);
+        tq_spmv<V>(S, A, u1, ev, cs);
+    };
+    if (unroll > 0) {
+        for (int k = 0; k < unroll; ++k) iteration();
+    } else {
+        HZ_TRY(capture_leaves(cs, &leaves));
+        HZ_CUDA(cudaStreamEndCapture(cs, &g));
+        cudaGraphNode_t wn;
+        cudaGraph_t body;
+        HZ_TRY(add_while(g, leaves, h, &wn, &body));
+        HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
+        iteration();
+        k_loop_guard<typename Ar<V>::St><<<1, 1, 0, cs>>>(st, S->dctl, 1, h);
+        HZ_CUDA(cudaStreamEndCapture(cs, &body));
+        HZ_CUDA(cudaStreamBeginCaptureToGraph(cs, g, &wn, nullptr, 1, mode));
+    }
     EpiTrue<V> et;
     et.st = st; et.info = S->dinfo; et.ctl = S->dctl;
     tq_spmv<V>(S, A, x, et, cs);

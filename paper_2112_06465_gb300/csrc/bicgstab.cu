@@ -671,8 +671,9 @@ static hz_status get_solver(hz_mat *A, uint32_t mode, cudaStream_t s, Solver **o
         S->grid_spmv_cv = spmv_grid(A, d64_kind(A, S->kind), S->group);
         S->grid_c64 = A->fblk ? c64_flat_grid(A) : 1;
         // HZ_PDL=1 (environment) captures F2..F5 as programmatic dependent
-        // launches; measured slower on the C2 solve (185 vs 175 us per
-        // iteration), so plain launches are the default
+        // launches; measured no faster on a 24^3 box (41.5 vs 41.9 us per
+        // iteration) and slower on a 64^3 box (99 vs 93 us) and on C2
+        // (191 vs 187 us), so plain launches are the default
         const char *pdl_env = getenv("HZ_PDL");
         S->pdl = pdl_env && atoi(pdl_env) != 0;
         S->grid_vec = vec_grid(d, A->n);

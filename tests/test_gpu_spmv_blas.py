@@ -227,7 +227,7 @@ def test_spmv_autotune(hz, oracle):
     for ff in (False, True):
         M = hz.Matrix.from_csr(A, ff=ff, sell=True, autotune=True)
         props = M.props()
-        assert props["spmv_kind"] in ((0, 1, 6) if not ff else (0, 1, 2, 3, 4, 5, 6))
+        assert props["spmv_kind"] in ((0, 1, 6, 7) if not ff else (0, 1, 2, 3, 4, 5, 6, 7))
         y = host(hz.zspmv(M, dev(x)))
         assert (np.abs(y - ref) / scale).max() <= TOL, props
         xs, info = hz.zsolve(M, dev(b), tol=1e-10, maxit=3000)

@@ -282,7 +282,8 @@ def run_kernel_case(args):
     case = args.kernel_case
     if case in ("spmv", "cspmv", "solve"):
         A, b = build_workload()
-        M = hz.Matrix.from_csr(A, ff=args.arith == "ff", c64=case == "cspmv" or args.solve_mode == "mixed")
+        M = hz.Matrix.from_csr(A, ff=args.arith == "ff", c64=case == "cspmv" or args.solve_mode == "mixed",
+                               sell=args.spmv in ("sell", "sellff"))
         if args.spmv:
             M.set_spmv(args.spmv, args.group)
         if case == "cspmv":

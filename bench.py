@@ -714,6 +714,34 @@ def double_float_entry(hz, torch, A, rp, cl, vl, bd, args, stream, steps=3):
     return out
 
 
+def c3_precision(hz, torch, stream, iters=1000):
+    """C3 (the precision configuration): the mixed solver against the plain
+    binary64 solver on the same 2M-unknown cylinder.  Neither reaches 1e-10
+    on this operator (the method stagnates), so both run the same budget of
+    BiCGStab iterations from x0 = 0 (the mixed solver's inner iterations in
+    total) and report time, time per iteration and the true relative
+    residual reached."""
+    import workloads as W
+    A, b = W.c3_cylinder_large()
+    M = hz.Matrix.from_csr(A, c64=True)
+    bd = torch.as_tensor(b).to("cuda")
+    out = {"workload": "C3 jittered P1-FEM cylinder nr=60 ntheta=128 nz=256 k=20 (%d unknowns, %d nonzeros)"
+                       % (A.n, A.nnz), "iteration_budget": iters}
+    for key, kw in (("binary64", dict(mode="fp64")), ("mixed", dict(mode="mixed"))):
+        hz.zsolve(M, bd, tol=1e-10, maxit=2, **kw)          # graph capture
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, info = hz.zsolve(M, bd, tol=1e-10, maxit=iters, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[key] = {"s": ms / 1e3, "iters": info.iters, "iter_us": 1e3 * ms / max(info.iters, 1),
+                    "status": info.status_name, "relres_true": info.relres_true,
+                    "outer": getattr(info, "outer", None)}
+    M.close()
+    return out
+
+
 def cpu_baseline_entry(A, b, iters):
     """The oracle's BiCGStab on the host cores: the plain single-thread
     build and the OpenMP build (fixed-order chunk sums) on every core this
@@ -755,6 +783,8 @@ def main():
     ap.add_argument("--compare-all", action="store_true",
                     help="compare also binary64 BiCGStab(4) and the double-float variants")
     ap.add_argument("--compare-maxit", type=int, default=3000)
+    ap.add_argument("--c3", action="store_true",
+                    help="also run the C3 precision configuration (mixed vs binary64 on 2M unknowns)")
     ap.add_argument("--spmv-only", action="store_true",
                     help="profiling aid: build C2, run three SpMV launches of the chosen "
                          "arithmetic (--arith, --group) and exit without timing")
@@ -892,6 +922,8 @@ def main():
         line["spmv_c64_c2"] = spmv_c64_c2(hz, torch, A, stream)
         line["adjoint_c5"] = adjoint_c5(hz, torch, stream)
         line["blas_sweep"] = blas_sweep(hz, torch, stream)
+    if rank == 0 and args.c3:
+        line["c3_precision"] = c3_precision(hz, torch, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_entry(A, b, args.cpu_iters)
     if rank == 0:

@@ -501,7 +501,7 @@ static void spmv_on(const Solver *S, const hz_mat *A, const V *x, const Epi &e, 
     } else if constexpr (std::is_same<V, float2>::value) {
         // complex64 inner operator: block-flat when the handle runs a block-flat kind
         if (A->fblk && is_flat64(d64_kind(A, S->kind)))
-            launch_k(pdl, k_spmv_c64b<Epi>, S->grid_c64, kFlatThreads, cs, mat_view<float2>(A), x, e, S->red);
+            launch_k(pdl, k_spmv_c64b<Epi>, S->grid_c64, kFlatThreads, cs, c64_view(A, S->kind), x, e, S->red);
         else
             launch_spmv<V>(d64_kind(A, S->kind),
                            S->group, mat_view<V>(A), x, e, S->red, S->grid_spmv_cv, cs, pdl);

@@ -132,6 +132,11 @@ __device__ __forceinline__ float4 ld_stream(const float4 *ptr, uint64_t pol) {
         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(ptr), "l"(pol));
     return v;
 }
+__device__ __forceinline__ float ld_stream(const float *ptr, uint64_t pol) {
+    float v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
 __device__ __forceinline__ int ld_stream(const int *ptr, uint64_t pol) {
     int v;
     asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
@@ -202,6 +207,10 @@ __device__ __forceinline__ double widen_d(float f) {
 // O(1) vector)
 constexpr int kFFMinExp = -100;
 constexpr int kFFMaxExp = 100;
+
+// entries per chunk of the packed complex64 stream (hz_mat::c64_*)
+constexpr int kC64ChunkLog = 8;
+constexpr int kC64Chunk = 1 << kC64ChunkLog;
 
 __device__ __forceinline__ float4 split_ff(double2 d) {
     float4 r;
@@ -544,6 +553,16 @@ struct hz_mat {
     float4 *sell_vff = nullptr;          // [slots] double-float split, if SELL and FF
     // complex64 copy
     float2 *val32 = nullptr;
+    // packed complex64 stream of the block-flat complex64 kernel under
+    // HZ_SPMV_FLAT64P (built with val32 when the handle has the packed
+    // binary64 stream): c64_re[k] = Re(val32[k]); the entries fall in chunks
+    // of kC64Chunk consecutive positions, and a chunk c with a nonzero
+    // binary32 imaginary part keeps them at c64_im + c64_imo[c] (same
+    // order), a chunk whose imaginary parts are all +0 none (c64_imo[c] < 0)
+    int64_t c64_chunks = 0;
+    float *c64_re = nullptr;     // [nnz]
+    float *c64_im = nullptr;     // [c64_chunks * kC64Chunk] (complex chunks only use it)
+    int32_t *c64_imo = nullptr;  // [c64_chunks]
     // double-float split of the values (hi_re, lo_re, hi_im, lo_im) and the
     // handle's x scratch for hz_zspmv on that path
     float4 *val_ff = nullptr;

@@ -127,6 +127,91 @@ static hz_status pk_refresh(hz_mat *A, cudaStream_t s) {
     return HZ_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Packed complex64 stream (hz_mat::c64_*), built with the complex64 copy on
+// creation and every value refresh: one CTA of kC64Chunk threads per chunk.
+
+// val32 and c64_re from the binary64 values; per chunk kC64Chunk if one of
+// its binary32 imaginary parts is not +0 (the slots it needs in c64_im),
+// else 0
+__global__ void __launch_bounds__(kC64Chunk) k_to_c64_pk(int nnz, int nchunks, const double2 *__restrict__ in,
+                                                         float2 *__restrict__ out, float *__restrict__ re,
+                                                         int *__restrict__ cnt) {
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int64_t k = (int64_t)c * kC64Chunk + threadIdx.x;
+        bool cplx = false;
+        if (k < nnz) {
+            const float2 v = to_c64(in[k]);
+            out[k] = v;
+            re[k] = v.x;
+            cplx = __float_as_uint(v.y) != 0u;
+        }
+        const int any = __syncthreads_or(cplx);
+        if (threadIdx.x == 0) cnt[c] = any ? kC64Chunk : 0;
+    }
+}
+
+// the imaginary parts of the complex chunks at their offsets (k_pk_scan
+// turned the counts into offsets, -1 for a real chunk)
+__global__ void __launch_bounds__(kC64Chunk) k_c64_im(int nnz, int nchunks, const float2 *__restrict__ v32,
+                                                      const int *__restrict__ imo, float *__restrict__ im) {
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int o = imo[c];
+        const int64_t k = (int64_t)c * kC64Chunk + threadIdx.x;
+        if (o >= 0 && k < nnz) im[o + threadIdx.x] = v32[k].y;
+    }
+}
+
+static hz_status c64_refresh(hz_mat *A, cudaStream_t s) {
+    if (!A->val32 || !A->nnz) return HZ_OK;
+    DevInfo d;
+    HZ_TRY(dev_info(&d));
+    if (!A->c64_re) {
+        k_to_c64<<<stream_grid(d, A->nnz, 256, 8), 256, 0, s>>>(A->nnz, A->val, A->val32);
+        HZ_CUDA(cudaGetLastError());
+        return HZ_OK;
+    }
+    const int nc = (int)A->c64_chunks;
+    const int grid = std::max(1, std::min(nc, d.num_sms * 8));
+    k_to_c64_pk<<<grid, kC64Chunk, 0, s>>>(A->nnz, nc, A->val, A->val32, A->c64_re, A->c64_imo);
+    HZ_CUDA(cudaGetLastError());
+    k_pk_scan<<<1, kPkScanThreads, 0, s>>>(nc, A->c64_imo);
+    HZ_CUDA(cudaGetLastError());
+    k_c64_im<<<grid, kC64Chunk, 0, s>>>(A->nnz, nc, A->val32, A->c64_imo, A->c64_im);
+    HZ_CUDA(cudaGetLastError());
+    return HZ_OK;
+}
+
+// the complex64 copy (and its SELL slots), and the packed complex64 stream
+// when the handle has the packed binary64 stream and the chunks' slots fit
+// 31-bit offsets; false on an allocation failure
+static bool alloc_c64(hz_mat *A) {
+    bool ok = cudaMalloc(&A->val32, sizeof(float2) * std::max(A->nnz, 1)) == cudaSuccess &&
+              (!A->sell_val ||
+               cudaMalloc(&A->sell_val32, sizeof(float2) * std::max<int64_t>(A->sell_slots, 1)) == cudaSuccess);
+    const int64_t nc = ((int64_t)A->nnz + kC64Chunk - 1) / kC64Chunk;
+    if (ok && A->pk_re && A->nnz && nc * kC64Chunk < INT32_MAX) {
+        A->c64_chunks = nc;
+        ok = cudaMalloc(&A->c64_re, sizeof(float) * A->nnz) == cudaSuccess &&
+             cudaMalloc(&A->c64_im, sizeof(float) * nc * kC64Chunk) == cudaSuccess &&
+             cudaMalloc(&A->c64_imo, sizeof(int) * nc) == cudaSuccess;
+    }
+    if (!ok) {   // all or nothing: a handle never holds part of the copy
+        cudaFree(A->val32);
+        cudaFree(A->sell_val32);
+        cudaFree(A->c64_re);
+        cudaFree(A->c64_im);
+        cudaFree(A->c64_imo);
+        A->val32 = nullptr;
+        A->sell_val32 = nullptr;
+        A->c64_re = A->c64_im = nullptr;
+        A->c64_imo = nullptr;
+        A->c64_chunks = 0;
+        cudaGetLastError();   // clear the allocation error
+    }
+    return ok;
+}
+
 // smallest and largest binary exponent (IEEE field minus bias) over the
 // nonzero real and imaginary parts of the values: out[0] = min, out[1] = max
 // (out[0] = INT_MAX, out[1] = INT_MIN on entry); a non-finite part counts as
@@ -188,6 +273,16 @@ MatView<float2> mat_view<float2>(const hz_mat *A) {
     v.nfblk = A->nfblk; v.fblk = A->fblk; v.fblk_k = A->fblk_k;
     v.nchunks = A->sell_nchunks; v.chunk_off = A->sell_chunk_off; v.chunk_w = A->sell_chunk_w;
     v.perm = A->sell_perm; v.scol = A->sell_col; v.sval = A->sell_val32;
+    return v;
+}
+
+MatView<float2> c64_view(const hz_mat *A, int kind) {
+    MatView<float2> v = mat_view<float2>(A);
+    if (A->c64_re && d64_kind(A, kind) == HZ_SPMV_FLAT64P) {
+        v.c64_re = A->c64_re;
+        v.c64_im = A->c64_im;
+        v.c64_imo = A->c64_imo;
+    }
     return v;
 }
 
@@ -314,10 +409,7 @@ static hz_status build_sell(hz_mat *A, cudaStream_t s, const std::vector<int> &r
 static hz_status refresh(hz_mat *A, cudaStream_t s) {
     DevInfo d;
     HZ_TRY(dev_info(&d));
-    if (A->val32 && A->nnz) {
-        k_to_c64<<<stream_grid(d, A->nnz, 256, 8), 256, 0, s>>>(A->nnz, A->val, A->val32);
-        HZ_CUDA(cudaGetLastError());
-    }
+    HZ_TRY(c64_refresh(A, s));
     if (A->val_ff && A->nnz) {
         k_split_ff<<<stream_grid(d, A->nnz, 256, 8), 256, 0, s>>>(A->nnz, A->val, A->val_ff);
         HZ_CUDA(cudaGetLastError());
@@ -332,8 +424,10 @@ static hz_status refresh(hz_mat *A, cudaStream_t s) {
 
 hz_status ensure_c64(hz_mat *A, cudaStream_t s) {
     if (A->val32) return HZ_OK;
-    HZ_CUDA(cudaMalloc(&A->val32, sizeof(float2) * std::max(A->nnz, 1)));
-    if (A->sell_val) HZ_CUDA(cudaMalloc(&A->sell_val32, sizeof(float2) * std::max<int64_t>(A->sell_slots, 1)));
+    if (!alloc_c64(A)) {
+        set_error("hz_cspmv: allocation of the complex64 copy failed");
+        return HZ_ERR_ALLOC;
+    }
     HZ_TRY(refresh(A, s));
     HZ_CUDA(cudaStreamSynchronize(s));
     return HZ_OK;
@@ -552,9 +646,7 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
         A->spmv_kind = HZ_SPMV_SELL;
     }
     if (flags & HZ_FLAG_C64) {
-        if (cudaMalloc(&A->val32, sizeof(float2) * std::max(nnz, 1)) != cudaSuccess ||
-            (A->sell_val && cudaMalloc(&A->sell_val32, sizeof(float2) * std::max<int64_t>(A->sell_slots, 1)) !=
-                                cudaSuccess)) {
+        if (!alloc_c64(A)) {
             set_error("hz_csr_create: allocation failed");
             return fail(HZ_ERR_ALLOC);
         }
@@ -650,6 +742,9 @@ extern "C" HZ_API hz_status hz_mat_destroy(hz_mat *A) {
     cudaFree(A->fault);
     cudaFree(A->sell_val32);
     cudaFree(A->val32);
+    cudaFree(A->c64_re);
+    cudaFree(A->c64_im);
+    cudaFree(A->c64_imo);
     cudaFree(A->val_ff);
     cudaFree(A->x_ff);
     cudaFree(A->diag_pos);
@@ -668,7 +763,7 @@ extern "C" HZ_API hz_status hz_mat_query(const hz_mat *A, hz_mat_props *p) {
     p->group = A->group;
     p->sell_slots = A->sell_slots;
     p->sell_sigma = A->sell_sigma;
-    p->has_c64 = A->val32 != nullptr;
+    p->has_c64 = A->c64_re ? 2 : A->val32 ? 1 : 0;
     return HZ_OK;
 }
 
@@ -727,7 +822,7 @@ extern "C" HZ_API hz_status hz_cspmv(hz_mat *A, const hz_c *d_x, hz_c *d_y, void
         // the block-flat kinds: the block-flat complex64 kernel
         EpiStore<float2> epi{(float2 *)d_y};
         HZ_CUDA(launch_k(false, k_spmv_c64b<EpiStore<float2>>, c64_flat_grid(A), kFlatThreads, (cudaStream_t)stream,
-                         mat_view<float2>(A), (const float2 *)d_x, epi, RedScratch{}));
+                         c64_view(A, A->spmv_kind), (const float2 *)d_x, epi, RedScratch{}));
         return HZ_OK;
     }
     const int kind = (A->spmv_kind == HZ_SPMV_SELL || A->spmv_kind == HZ_SPMV_SELL_FF) ? HZ_SPMV_SELL

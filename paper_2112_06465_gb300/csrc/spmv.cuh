@@ -108,6 +108,11 @@ struct MatView {
     const int *pk_col;
     const double *pk_re;
     const double *pk_im;
+    // packed complex64 stream (see hz_mat::c64_*); null unless the
+    // complex64 view of a HZ_SPMV_FLAT64P handle (c64_view)
+    const float *c64_re;
+    const float *c64_im;
+    const int *c64_imo;
 };
 
 // Epilogue interface (every fused SpMV epilogue provides):
@@ -1126,7 +1131,10 @@ __global__ void __launch_bounds__(kFlatThreads) k_spmv_fft(MatView<double2> A, c
 // double-float kernel with complex64 values (the mixed solver's inner
 // operator) and plain binary32 arithmetic: phase 1 forms a_k x_col(k) (four
 // FMA-pipe operations) into the warp's slab, phase 2 sums each row in
-// storage order.
+// storage order.  With the packed stream (A.c64_re set) a value is read as
+// its real part plus, in a chunk with a nonzero imaginary part, that part
+// (8 bytes per entry of a real chunk instead of 12); a real chunk's
+// imaginary parts are +0 in both forms, so the products are bit-identical.
 template <class Epi, int NV>
 __device__ __forceinline__ void flat_rows_c64(const MatView<float2> &A, const float2 *__restrict__ x, const Epi &epi,
                                               typename Epi::Acc (&acc)[NV], float2 *slab) {
@@ -1163,11 +1171,22 @@ __device__ __forceinline__ void flat_rows_c64(const MatView<float2> &A, const fl
         q.kend = min(m.ke, m.kb + kFlatCap);
         return q;
     };
-    auto load_cols = [&](const Group &q, int (&c)[kFlatGroup]) {
+    const bool packed = A.c64_re != nullptr;
+    // a group's 32 kFlatGroup consecutive entries span at most two chunks
+    static_assert(32 * kFlatGroup <= kC64Chunk, "a group must span at most two complex64 chunks");
+    // columns one group ahead and, packed, the imaginary-part offsets of the
+    // group's first chunk and (if it reaches it) the next
+    auto load_cols = [&](const Group &q, int (&c)[kFlatGroup], int2 &o) {
 #pragma unroll
         for (int u = 0; u < kFlatGroup; ++u) {
             const int k = q.kg + lane + 32 * u;
             c[u] = (q.b < A.nfblk && k < q.kend) ? ld_stream(A.col + k, pol) : -1;
+        }
+        o = make_int2(-1, -1);
+        if (packed && q.b < A.nfblk) {
+            const int c0 = q.kg >> kC64ChunkLog;
+            o.x = __ldg(A.c64_imo + c0);
+            if (((min(q.kend, q.kg + 32 * kFlatGroup) - 1) >> kC64ChunkLog) > c0) o.y = __ldg(A.c64_imo + c0 + 1);
         }
     };
     const int b0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -1175,16 +1194,24 @@ __device__ __forceinline__ void flat_rows_c64(const MatView<float2> &A, const fl
     Group cur = block_group(block_meta(b0));
     Meta ahead = block_meta(b0 + step);
     int cn[kFlatGroup];
-    load_cols(cur, cn);
+    int2 on;
+    load_cols(cur, cn, on);
     float2 carry = make_float2(0.f, 0.f);   // long-row carry (lane 0)
     for (;;) {
         int c[kFlatGroup];
         float2 a[kFlatGroup], v[kFlatGroup];
+        const int2 oc = on;
 #pragma unroll
         for (int u = 0; u < kFlatGroup; ++u) {
             c[u] = cn[u];
             const int k = cur.kg + lane + 32 * u;
-            a[u] = c[u] >= 0 ? ld_stream(A.val + k) : make_float2(0.f, 0.f);
+            if (packed) {
+                const int o = (k >> kC64ChunkLog) == (cur.kg >> kC64ChunkLog) ? oc.x : oc.y;
+                a[u].x = c[u] >= 0 ? ld_stream(A.c64_re + k, pol) : 0.f;
+                a[u].y = c[u] >= 0 && o >= 0 ? ld_stream(A.c64_im + o + (k & (kC64Chunk - 1)), pol) : 0.f;
+            } else {
+                a[u] = c[u] >= 0 ? ld_stream(A.val + k) : make_float2(0.f, 0.f);
+            }
         }
 #pragma unroll
         for (int u = 0; u < kFlatGroup; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float2(0.f, 0.f);
@@ -1204,7 +1231,7 @@ __device__ __forceinline__ void flat_rows_c64(const MatView<float2> &A, const fl
             nxt = block_group(ahead);
             ahead = block_meta(nxt.b + step);
         }
-        load_cols(nxt, cn);
+        load_cols(nxt, cn, on);
 #pragma unroll
         for (int u = 0; u < kFlatGroup; ++u)
             if (c[u] >= 0) prod[cur.kg - cur.kc + lane + 32 * u] = cmul(a[u], v[u]);
@@ -1256,6 +1283,9 @@ __global__ void __launch_bounds__(kFlatThreads) k_spmv_c64b(MatView<float2> A, c
 
 // grid of k_spmv_c64b: the CTAs that fit at once
 int c64_flat_grid(const hz_mat *A);
+// complex64 view of a handle for a kernel kind: mat_view<float2> plus the
+// packed complex64 stream when the kind resolves to HZ_SPMV_FLAT64P
+MatView<float2> c64_view(const hz_mat *A, int kind);
 
 // binary64 -> double-float split of a vector (xff[i] = split_ff(x[i])), on stream s
 cudaError_t split_ff_vec(int n, const double2 *x, float4 *xff, cudaStream_t s);

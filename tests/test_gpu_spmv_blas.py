@@ -315,15 +315,64 @@ def test_spmv_c3_full_size(hz, oracle):
 
 @pytest.mark.parametrize("ff", [False, True])
 def test_cspmv_complex64(hz, oracle, ff):
-    """CSR-vector (plain handle) and block-flat (double-float handle) complex64
-    products, including rows longer than one 512-entry block."""
-    for A, x in ((K.small_cylinder()[0], None), (K.random_csr(3000, 6, max_row=12, long_rows=(2500, 1300)), None)):
+    """Complex64 products, including rows longer than one 512-entry block:
+    the block-flat kernel on the packed complex64 copy (the handle's default
+    kind, plain or double-float), on the plain copy (FLAT64) and CSR-vector.
+    The packed copy holds the same values, so its products equal FLAT64's
+    bit for bit."""
+    for A in (K.small_cylinder()[0], K.random_csr(3000, 6, max_row=12, long_rows=(2500, 1300))):
         x = K.vectors(A.n, 5)[0].astype(np.complex64)
         M = hz.Matrix.from_csr(A, c64=True, ff=ff)
-        y = host(hz.cspmv(M, dev(x)))
+        assert M.props()["has_c64"] == 2
         ref = oracle.cspmv(A, x)
         scale = K.row_abs_scale(A, x.astype(np.complex128))
-        assert np.all(np.abs(y - ref) <= 4e-6 * scale)
+        ys = {}
+        for kind in ("default", "flat64", "csr"):
+            if kind != "default":
+                M.set_spmv(kind, 4)
+            ys[kind] = host(hz.cspmv(M, dev(x)))
+            assert np.all(np.abs(ys[kind] - ref) <= 4e-6 * scale), kind
+        assert np.array_equal(ys["default"], ys["flat64"])
+        M.close()
+
+
+def test_cspmv_packed_chunks_follow_value_refresh(hz, oracle):
+    """The packed complex64 copy stores imaginary parts only for chunks of
+    256 consecutive nonzeros with one whose binary32 bits are not +0.  A real
+    matrix with a band of complex rows, one -0 imaginary part (kept: its
+    bits are not +0), one of 1e-60 (+0 in binary32: the chunk stays real)
+    and a ragged last chunk; then a value refresh that swaps the band's rows
+    and a long row between real and complex.  Each product equals the
+    unpacked FLAT64 kernel's bit for bit and the oracle's within the binary32
+    bound."""
+    A = K.random_csr(5000, 93, max_row=20, long_rows=(900,))
+    assert A.nnz % 256 != 0
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    v0 = A.val.real.astype(np.complex128)
+    band = (rows >= 2000) & (rows < 2100)
+    v0[band] = A.val[band]
+    v0[10] = complex(v0[10].real, -0.0)
+    v0[3000] = complex(v0[3000].real, 1e-60)
+    v0[-1] = A.val[-1]                                        # complex entry in the ragged last chunk
+    flip = band | (np.diff(A.rowptr)[rows] == 900)
+    v1 = v0.copy()
+    v1[flip] = np.where(band[flip], A.val[flip].real, A.val[flip])
+    x = K.vectors(A.n, 94)[0].astype(np.complex64)
+    vd = dev(v0)
+    M = hz.Matrix(dev(A.rowptr), dev(A.col), vd, c64=True)
+    assert M.props()["spmv_kind"] == 7 and M.props()["has_c64"] == 2
+    for v in (v0, v1):
+        if v is v1:
+            vd.copy_(torch.as_tensor(v1))
+            M.refresh_values()
+        Av = W.CSR(A.n, A.rowptr, A.col, v)
+        M.set_spmv("flat64p")
+        y = host(hz.cspmv(M, dev(x)))
+        ref = oracle.cspmv(Av, x)
+        assert np.all(np.abs(y - ref) <= 4e-6 * K.row_abs_scale(Av, x.astype(np.complex128)))
+        M.set_spmv("flat64")
+        assert np.array_equal(host(hz.cspmv(M, dev(x))), y)
+    M.close()
 
 
 # --------------------------------------------------------------------------- BLAS-1

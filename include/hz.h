@@ -66,7 +66,7 @@ enum {
     HZ_FLAG_SELL = 2u,       /* also build a SELL-C-sigma copy and use it for SpMV */
     HZ_FLAG_C64 = 4u,        /* also build the complex64 copy used by the mixed solver (8 bytes
                                 per nonzero; with the packed binary64 copy of HZ_SPMV_FLAT64P
-                                also a packed complex64 copy, 4 to 8 bytes per nonzero) */
+                                also its binary32 real parts, 4 bytes per nonzero) */
     HZ_FLAG_AUTOTUNE = 8u,   /* time the SpMV variants once on this matrix and keep the fastest;
                                 `group` becomes the fastest binary64 CSR-vector group (the row
                                 tile of this matrix in hz_zsolve_batched's complex64 and
@@ -150,7 +150,7 @@ typedef struct {
     int64_t sell_slots;      /* padded slots of the SELL copy (0 if none) */
     int32_t sell_sigma;      /* sorting window of the SELL copy */
     int32_t has_c64;         /* 0: no complex64 copy; 1: the complex64 copy; 2: that copy and
-                                its packed form (HZ_SPMV_FLAT64P handles) */
+                                its real parts (handles with the HZ_SPMV_FLAT64P copy) */
 } hz_mat_props;
 
 /*
@@ -226,10 +226,10 @@ HZ_API hz_status hz_zspmv(const hz_mat *A, const hz_z *d_x, hz_z *d_y, void *str
  * copy of the values (created on demand; synchronises on first use).  On the
  * block-flat kinds the block-flat complex64 kernel runs; under
  * HZ_SPMV_FLAT64P (and HZ_SPMV_FF_FLAT / HZ_SPMV_FF_TMA, whose complex64
- * product it is) it reads the packed complex64 copy: real parts, and imaginary parts
- * only for chunks of 256 consecutive nonzeros that have a nonzero one, 8
- * bytes per nonzero of a real chunk instead of 12; the products are the
- * same bit for bit. */
+ * product it is) a group of 256 consecutive nonzeros whose binary32
+ * imaginary parts are all +0 reads their real parts alone (8 bytes per
+ * nonzero with its column instead of 12); the products are the same bit for
+ * bit. */
 HZ_API hz_status hz_cspmv(hz_mat *A, const hz_c *d_x, hz_c *d_y, void *stream);
 
 /* *d_result = sum_i conj(x_i) y_i (Section 5, dot product; conjugated form). */

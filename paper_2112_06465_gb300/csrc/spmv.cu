@@ -128,37 +128,24 @@ static hz_status pk_refresh(hz_mat *A, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Packed complex64 stream (hz_mat::c64_*), built with the complex64 copy on
-// creation and every value refresh: one CTA of kC64Chunk threads per chunk.
-
-// val32 and c64_re from the binary64 values; per chunk kC64Chunk if one of
-// its binary32 imaginary parts is not +0 (the slots it needs in c64_im),
-// else 0
-__global__ void __launch_bounds__(kC64Chunk) k_to_c64_pk(int nnz, int nchunks, const double2 *__restrict__ in,
+// Real parts of the complex64 copy and the chunk flags (hz_mat::c64_*),
+// built with the copy on creation and every value refresh: one CTA of
+// kC64Chunk threads per chunk writes val32, c64_re and the chunk's flag (1
+// if one of its binary32 imaginary parts is not +0)
+__global__ void __launch_bounds__(kC64Chunk) k_to_c64_re(int nnz, int nchunks, const double2 *__restrict__ in,
                                                          float2 *__restrict__ out, float *__restrict__ re,
-                                                         int *__restrict__ cnt) {
+                                                         int *__restrict__ cplx) {
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const int64_t k = (int64_t)c * kC64Chunk + threadIdx.x;
-        bool cplx = false;
+        bool nz = false;
         if (k < nnz) {
             const float2 v = to_c64(in[k]);
             out[k] = v;
             re[k] = v.x;
-            cplx = __float_as_uint(v.y) != 0u;
+            nz = __float_as_uint(v.y) != 0u;
         }
-        const int any = __syncthreads_or(cplx);
-        if (threadIdx.x == 0) cnt[c] = any ? kC64Chunk : 0;
-    }
-}
-
-// the imaginary parts of the complex chunks at their offsets (k_pk_scan
-// turned the counts into offsets, -1 for a real chunk)
-__global__ void __launch_bounds__(kC64Chunk) k_c64_im(int nnz, int nchunks, const float2 *__restrict__ v32,
-                                                      const int *__restrict__ imo, float *__restrict__ im) {
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const int o = imo[c];
-        const int64_t k = (int64_t)c * kC64Chunk + threadIdx.x;
-        if (o >= 0 && k < nnz) im[o + threadIdx.x] = v32[k].y;
+        const int any = __syncthreads_or(nz);
+        if (threadIdx.x == 0) cplx[c] = any ? 1 : 0;
     }
 }
 
@@ -166,46 +153,51 @@ static hz_status c64_refresh(hz_mat *A, cudaStream_t s) {
     if (!A->val32 || !A->nnz) return HZ_OK;
     DevInfo d;
     HZ_TRY(dev_info(&d));
-    if (!A->c64_re) {
+    if (A->c64_re) {
+        const int nc = (int)A->c64_chunks;
+        k_to_c64_re<<<std::max(1, std::min(nc, d.num_sms * 8)), kC64Chunk, 0, s>>>(A->nnz, nc, A->val, A->val32,
+                                                                                  A->c64_re, A->c64_cplx);
+    } else {
         k_to_c64<<<stream_grid(d, A->nnz, 256, 8), 256, 0, s>>>(A->nnz, A->val, A->val32);
-        HZ_CUDA(cudaGetLastError());
-        return HZ_OK;
     }
-    const int nc = (int)A->c64_chunks;
-    const int grid = std::max(1, std::min(nc, d.num_sms * 8));
-    k_to_c64_pk<<<grid, kC64Chunk, 0, s>>>(A->nnz, nc, A->val, A->val32, A->c64_re, A->c64_imo);
-    HZ_CUDA(cudaGetLastError());
-    k_pk_scan<<<1, kPkScanThreads, 0, s>>>(nc, A->c64_imo);
-    HZ_CUDA(cudaGetLastError());
-    k_c64_im<<<grid, kC64Chunk, 0, s>>>(A->nnz, nc, A->val32, A->c64_imo, A->c64_im);
     HZ_CUDA(cudaGetLastError());
     return HZ_OK;
 }
 
-// the complex64 copy (and its SELL slots), and the packed complex64 stream
-// when the handle has the packed binary64 stream and the chunks' slots fit
-// 31-bit offsets; false on an allocation failure
+// whether the block-flat complex64 kernel reads the real parts: counted
+// from the chunk flags when the copy is created (synchronises s)
+static hz_status c64_choose(hz_mat *A, cudaStream_t s) {
+    A->c64_use_re = false;
+    if (!A->c64_re) return HZ_OK;
+    std::vector<int> f(A->c64_chunks);
+    HZ_CUDA(cudaMemcpyAsync(f.data(), A->c64_cplx, sizeof(int) * f.size(), cudaMemcpyDeviceToHost, s));
+    HZ_CUDA(cudaStreamSynchronize(s));
+    const int64_t cplx = std::count_if(f.begin(), f.end(), [](int v) { return v != 0; });
+    A->c64_use_re = 4 * (A->c64_chunks - cplx) >= 3 * A->c64_chunks;
+    return HZ_OK;
+}
+
+// the complex64 copy (and its SELL slots), and its real parts and chunk
+// flags when the handle has the packed binary64 stream; all or nothing,
+// false on an allocation failure
 static bool alloc_c64(hz_mat *A) {
     bool ok = cudaMalloc(&A->val32, sizeof(float2) * std::max(A->nnz, 1)) == cudaSuccess &&
               (!A->sell_val ||
                cudaMalloc(&A->sell_val32, sizeof(float2) * std::max<int64_t>(A->sell_slots, 1)) == cudaSuccess);
-    const int64_t nc = ((int64_t)A->nnz + kC64Chunk - 1) / kC64Chunk;
-    if (ok && A->pk_re && A->nnz && nc * kC64Chunk < INT32_MAX) {
-        A->c64_chunks = nc;
+    if (ok && A->pk_re && A->nnz) {
+        A->c64_chunks = ((int64_t)A->nnz + kC64Chunk - 1) / kC64Chunk;
         ok = cudaMalloc(&A->c64_re, sizeof(float) * A->nnz) == cudaSuccess &&
-             cudaMalloc(&A->c64_im, sizeof(float) * nc * kC64Chunk) == cudaSuccess &&
-             cudaMalloc(&A->c64_imo, sizeof(int) * nc) == cudaSuccess;
+             cudaMalloc(&A->c64_cplx, sizeof(int) * A->c64_chunks) == cudaSuccess;
     }
-    if (!ok) {   // all or nothing: a handle never holds part of the copy
+    if (!ok) {
         cudaFree(A->val32);
         cudaFree(A->sell_val32);
         cudaFree(A->c64_re);
-        cudaFree(A->c64_im);
-        cudaFree(A->c64_imo);
+        cudaFree(A->c64_cplx);
         A->val32 = nullptr;
         A->sell_val32 = nullptr;
-        A->c64_re = A->c64_im = nullptr;
-        A->c64_imo = nullptr;
+        A->c64_re = nullptr;
+        A->c64_cplx = nullptr;
         A->c64_chunks = 0;
         cudaGetLastError();   // clear the allocation error
     }
@@ -278,10 +270,9 @@ MatView<float2> mat_view<float2>(const hz_mat *A) {
 
 MatView<float2> c64_view(const hz_mat *A, int kind) {
     MatView<float2> v = mat_view<float2>(A);
-    if (A->c64_re && d64_kind(A, kind) == HZ_SPMV_FLAT64P) {
+    if (A->c64_use_re && d64_kind(A, kind) == HZ_SPMV_FLAT64P) {
         v.c64_re = A->c64_re;
-        v.c64_im = A->c64_im;
-        v.c64_imo = A->c64_imo;
+        v.c64_cplx = A->c64_cplx;
     }
     return v;
 }
@@ -324,14 +315,9 @@ int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap) {
     return stream_grid(d, threads, kSpmvBlock, blocks_per_sm_cap);
 }
 
-int c64_flat_grid(const hz_mat *A) {
+int c64_flat_grid(const hz_mat *A, int occ) {
     DevInfo d;
     if (dev_info(&d) != HZ_OK) return 1;
-    static int occ = 0;
-    if (occ == 0 &&
-        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_c64b<EpiStore<float2>>, kFlatThreads, 0) !=
-             cudaSuccess || occ < 1))
-        occ = 1;
     const int64_t g = std::min<int64_t>(A->nfblk, (int64_t)d.num_sms * occ);
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
 }
@@ -429,6 +415,7 @@ hz_status ensure_c64(hz_mat *A, cudaStream_t s) {
         return HZ_ERR_ALLOC;
     }
     HZ_TRY(refresh(A, s));
+    HZ_TRY(c64_choose(A, s));
     HZ_CUDA(cudaStreamSynchronize(s));
     return HZ_OK;
 }
@@ -704,6 +691,7 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
         A->spmv_kind = in_range ? HZ_SPMV_FF_FLAT : A->pk_re ? HZ_SPMV_FLAT64P : HZ_SPMV_FLAT64;
     }
     if ((st = refresh(A, s)) != HZ_OK) return fail(st);
+    if ((st = c64_choose(A, s)) != HZ_OK) return fail(st);
     if (flags & HZ_FLAG_AUTOTUNE) {
         if ((st = autotune(A, s)) != HZ_OK) return fail(st);
     }
@@ -743,8 +731,7 @@ extern "C" HZ_API hz_status hz_mat_destroy(hz_mat *A) {
     cudaFree(A->sell_val32);
     cudaFree(A->val32);
     cudaFree(A->c64_re);
-    cudaFree(A->c64_im);
-    cudaFree(A->c64_imo);
+    cudaFree(A->c64_cplx);
     cudaFree(A->val_ff);
     cudaFree(A->x_ff);
     cudaFree(A->diag_pos);
@@ -763,7 +750,7 @@ extern "C" HZ_API hz_status hz_mat_query(const hz_mat *A, hz_mat_props *p) {
     p->group = A->group;
     p->sell_slots = A->sell_slots;
     p->sell_sigma = A->sell_sigma;
-    p->has_c64 = A->c64_re ? 2 : A->val32 ? 1 : 0;
+    p->has_c64 = A->c64_use_re ? 2 : A->val32 ? 1 : 0;
     return HZ_OK;
 }
 
@@ -821,8 +808,11 @@ extern "C" HZ_API hz_status hz_cspmv(hz_mat *A, const hz_c *d_x, hz_c *d_y, void
     if (A->fblk && is_flat64(d64_kind(A, A->spmv_kind))) {
         // the block-flat kinds: the block-flat complex64 kernel
         EpiStore<float2> epi{(float2 *)d_y};
-        HZ_CUDA(launch_k(false, k_spmv_c64b<EpiStore<float2>>, c64_flat_grid(A), kFlatThreads, (cudaStream_t)stream,
-                         c64_view(A, A->spmv_kind), (const float2 *)d_x, epi, RedScratch{}));
+        const MatView<float2> V = c64_view(A, A->spmv_kind);
+        const bool re = V.c64_re != nullptr;
+        HZ_CUDA(launch_k(false, re ? k_spmv_c64b<EpiStore<float2>, true> : k_spmv_c64b<EpiStore<float2>, false>,
+                         c64_flat_grid(A, c64_flat_occupancy<EpiStore<float2>>(re)), kFlatThreads,
+                         (cudaStream_t)stream, V, (const float2 *)d_x, epi, RedScratch{}));
         return HZ_OK;
     }
     const int kind = (A->spmv_kind == HZ_SPMV_SELL || A->spmv_kind == HZ_SPMV_SELL_FF) ? HZ_SPMV_SELL

@@ -64,9 +64,7 @@ typedef enum {
 enum {
     HZ_FLAG_VALIDATE = 1u,   /* check rowptr monotone, rowptr[n]==nnz, cols in range (host copy) */
     HZ_FLAG_SELL = 2u,       /* also build a SELL-C-sigma copy and use it for SpMV */
-    HZ_FLAG_C64 = 4u,        /* also build the complex64 copy used by the mixed solver (8 bytes
-                                per nonzero; with the packed binary64 copy of HZ_SPMV_FLAT64P
-                                also its binary32 real parts, 4 bytes per nonzero) */
+    HZ_FLAG_C64 = 4u,        /* also build the complex64 copy used by the mixed solver */
     HZ_FLAG_AUTOTUNE = 8u,   /* time the SpMV variants once on this matrix and keep the fastest;
                                 `group` becomes the fastest binary64 CSR-vector group (the row
                                 tile of this matrix in hz_zsolve_batched's complex64 and
@@ -149,8 +147,7 @@ typedef struct {
     int32_t group;           /* lanes per row for HZ_SPMV_CSR_VECTOR */
     int64_t sell_slots;      /* padded slots of the SELL copy (0 if none) */
     int32_t sell_sigma;      /* sorting window of the SELL copy */
-    int32_t has_c64;         /* 0: no complex64 copy; 1: the complex64 copy; 2: that copy and
-                                its real parts (handles with the HZ_SPMV_FLAT64P copy) */
+    int32_t has_c64;
 } hz_mat_props;
 
 /*
@@ -223,13 +220,7 @@ HZ_API hz_status hz_mat_refresh_values(hz_mat *A, void *stream);
 HZ_API hz_status hz_zspmv(const hz_mat *A, const hz_z *d_x, hz_z *d_y, void *stream);
 
 /* y = A32 x in complex64 with binary32 sums, using the handle's complex64
- * copy of the values (created on demand; synchronises on first use).  On the
- * block-flat kinds the block-flat complex64 kernel runs; under
- * HZ_SPMV_FLAT64P (and HZ_SPMV_FF_FLAT / HZ_SPMV_FF_TMA, whose complex64
- * product it is) a group of 256 consecutive nonzeros whose binary32
- * imaginary parts are all +0 reads their real parts alone (8 bytes per
- * nonzero with its column instead of 12); the products are the same bit for
- * bit. */
+ * copy of the values (created on demand; synchronises on first use). */
 HZ_API hz_status hz_cspmv(hz_mat *A, const hz_c *d_x, hz_c *d_y, void *stream);
 
 /* *d_result = sum_i conj(x_i) y_i (Section 5, dot product; conjugated form). */

@@ -500,11 +500,8 @@ static void spmv_on(const Solver *S, const hz_mat *A, const V *x, const Epi &e, 
         launch_spmv_ff(S->kind, S->group, mat_view<double2>(A), x, e, S->red, S->grid_spmv, cs, pdl);
     } else if constexpr (std::is_same<V, float2>::value) {
         // complex64 inner operator: block-flat when the handle runs a block-flat kind
-        if (A->fblk && is_flat64(d64_kind(A, S->kind))) {
-            const MatView<float2> view = c64_view(A, S->kind);
-            launch_k(pdl, view.c64_re ? k_spmv_c64b<Epi, true> : k_spmv_c64b<Epi, false>, S->grid_c64, kFlatThreads,
-                     cs, view, x, e, S->red);
-        }
+        if (A->fblk && is_flat64(d64_kind(A, S->kind)))
+            launch_k(pdl, k_spmv_c64b<Epi>, S->grid_c64, kFlatThreads, cs, mat_view<float2>(A), x, e, S->red);
         else
             launch_spmv<V>(d64_kind(A, S->kind),
                            S->group, mat_view<V>(A), x, e, S->red, S->grid_spmv_cv, cs, pdl);
@@ -672,11 +669,7 @@ static hz_status get_solver(hz_mat *A, uint32_t mode, cudaStream_t s, Solver **o
         S->group = A->group;
         S->grid_spmv = spmv_grid(A, S->kind, S->group);
         S->grid_spmv_cv = spmv_grid(A, d64_kind(A, S->kind), S->group);
-        if (A->fblk) {   // the CTAs that fit at once, for both complex64 products of the iteration
-            const bool re = c64_view(A, S->kind).c64_re != nullptr;
-            S->grid_c64 = c64_flat_grid(A, std::min(c64_flat_occupancy<EpiSigma<float2>>(re),
-                                                    c64_flat_occupancy<EpiOmega<float2>>(re)));
-        }
+        S->grid_c64 = A->fblk ? c64_flat_grid(A) : 1;
         // HZ_PDL=1 (environment) captures F2..F5 as programmatic dependent
         // launches; measured no faster on a 24^3 box (41.5 vs 41.9 us per
         // iteration) and slower on a 64^3 box (99 vs 93 us) and on C2

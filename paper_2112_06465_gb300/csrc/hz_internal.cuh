@@ -132,11 +132,6 @@ __device__ __forceinline__ float4 ld_stream(const float4 *ptr, uint64_t pol) {
         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(ptr), "l"(pol));
     return v;
 }
-__device__ __forceinline__ float ld_stream(const float *ptr, uint64_t pol) {
-    float v;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(ptr), "l"(pol));
-    return v;
-}
 __device__ __forceinline__ int ld_stream(const int *ptr, uint64_t pol) {
     int v;
     asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
@@ -207,10 +202,6 @@ __device__ __forceinline__ double widen_d(float f) {
 // O(1) vector)
 constexpr int kFFMinExp = -100;
 constexpr int kFFMaxExp = 100;
-
-// entries per chunk of the complex64 copy's real/complex flags (hz_mat::c64_*)
-constexpr int kC64ChunkLog = 8;
-constexpr int kC64Chunk = 1 << kC64ChunkLog;
 
 __device__ __forceinline__ float4 split_ff(double2 d) {
     float4 r;
@@ -553,19 +544,6 @@ struct hz_mat {
     float4 *sell_vff = nullptr;          // [slots] double-float split, if SELL and FF
     // complex64 copy
     float2 *val32 = nullptr;
-    // real parts of the complex64 copy for the block-flat complex64 kernel
-    // under HZ_SPMV_FLAT64P (built with val32 when the handle has the packed
-    // binary64 stream): c64_re[k] = Re(val32[k]); the entries fall in chunks
-    // of kC64Chunk consecutive positions, and c64_cplx[c] = 1 where a
-    // binary32 imaginary part of chunk c is not +0 (the kernel reads val32
-    // there), 0 where all are +0 (it reads c64_re alone)
-    int64_t c64_chunks = 0;
-    float *c64_re = nullptr;      // [nnz]
-    int32_t *c64_cplx = nullptr;  // [c64_chunks]
-    // whether the kernel reads them: at least 3/4 of the chunks real when
-    // the complex64 copy was created (the extra registers of that kernel
-    // cost more than the bytes saved on a mostly complex matrix)
-    bool c64_use_re = false;
     // double-float split of the values (hi_re, lo_re, hi_im, lo_im) and the
     // handle's x scratch for hz_zspmv on that path
     float4 *val_ff = nullptr;

@@ -127,83 +127,6 @@ static hz_status pk_refresh(hz_mat *A, cudaStream_t s) {
     return HZ_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Real parts of the complex64 copy and the chunk flags (hz_mat::c64_*),
-// built with the copy on creation and every value refresh: one CTA of
-// kC64Chunk threads per chunk writes val32, c64_re and the chunk's flag (1
-// if one of its binary32 imaginary parts is not +0)
-__global__ void __launch_bounds__(kC64Chunk) k_to_c64_re(int nnz, int nchunks, const double2 *__restrict__ in,
-                                                         float2 *__restrict__ out, float *__restrict__ re,
-                                                         int *__restrict__ cplx) {
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const int64_t k = (int64_t)c * kC64Chunk + threadIdx.x;
-        bool nz = false;
-        if (k < nnz) {
-            const float2 v = to_c64(in[k]);
-            out[k] = v;
-            re[k] = v.x;
-            nz = __float_as_uint(v.y) != 0u;
-        }
-        const int any = __syncthreads_or(nz);
-        if (threadIdx.x == 0) cplx[c] = any ? 1 : 0;
-    }
-}
-
-static hz_status c64_refresh(hz_mat *A, cudaStream_t s) {
-    if (!A->val32 || !A->nnz) return HZ_OK;
-    DevInfo d;
-    HZ_TRY(dev_info(&d));
-    if (A->c64_re) {
-        const int nc = (int)A->c64_chunks;
-        k_to_c64_re<<<std::max(1, std::min(nc, d.num_sms * 8)), kC64Chunk, 0, s>>>(A->nnz, nc, A->val, A->val32,
-                                                                                  A->c64_re, A->c64_cplx);
-    } else {
-        k_to_c64<<<stream_grid(d, A->nnz, 256, 8), 256, 0, s>>>(A->nnz, A->val, A->val32);
-    }
-    HZ_CUDA(cudaGetLastError());
-    return HZ_OK;
-}
-
-// whether the block-flat complex64 kernel reads the real parts: counted
-// from the chunk flags when the copy is created (synchronises s)
-static hz_status c64_choose(hz_mat *A, cudaStream_t s) {
-    A->c64_use_re = false;
-    if (!A->c64_re) return HZ_OK;
-    std::vector<int> f(A->c64_chunks);
-    HZ_CUDA(cudaMemcpyAsync(f.data(), A->c64_cplx, sizeof(int) * f.size(), cudaMemcpyDeviceToHost, s));
-    HZ_CUDA(cudaStreamSynchronize(s));
-    const int64_t cplx = std::count_if(f.begin(), f.end(), [](int v) { return v != 0; });
-    A->c64_use_re = 4 * (A->c64_chunks - cplx) >= 3 * A->c64_chunks;
-    return HZ_OK;
-}
-
-// the complex64 copy (and its SELL slots), and its real parts and chunk
-// flags when the handle has the packed binary64 stream; all or nothing,
-// false on an allocation failure
-static bool alloc_c64(hz_mat *A) {
-    bool ok = cudaMalloc(&A->val32, sizeof(float2) * std::max(A->nnz, 1)) == cudaSuccess &&
-              (!A->sell_val ||
-               cudaMalloc(&A->sell_val32, sizeof(float2) * std::max<int64_t>(A->sell_slots, 1)) == cudaSuccess);
-    if (ok && A->pk_re && A->nnz) {
-        A->c64_chunks = ((int64_t)A->nnz + kC64Chunk - 1) / kC64Chunk;
-        ok = cudaMalloc(&A->c64_re, sizeof(float) * A->nnz) == cudaSuccess &&
-             cudaMalloc(&A->c64_cplx, sizeof(int) * A->c64_chunks) == cudaSuccess;
-    }
-    if (!ok) {
-        cudaFree(A->val32);
-        cudaFree(A->sell_val32);
-        cudaFree(A->c64_re);
-        cudaFree(A->c64_cplx);
-        A->val32 = nullptr;
-        A->sell_val32 = nullptr;
-        A->c64_re = nullptr;
-        A->c64_cplx = nullptr;
-        A->c64_chunks = 0;
-        cudaGetLastError();   // clear the allocation error
-    }
-    return ok;
-}
-
 // smallest and largest binary exponent (IEEE field minus bias) over the
 // nonzero real and imaginary parts of the values: out[0] = min, out[1] = max
 // (out[0] = INT_MAX, out[1] = INT_MIN on entry); a non-finite part counts as
@@ -268,15 +191,6 @@ MatView<float2> mat_view<float2>(const hz_mat *A) {
     return v;
 }
 
-MatView<float2> c64_view(const hz_mat *A, int kind) {
-    MatView<float2> v = mat_view<float2>(A);
-    if (A->c64_use_re && d64_kind(A, kind) == HZ_SPMV_FLAT64P) {
-        v.c64_re = A->c64_re;
-        v.c64_cplx = A->c64_cplx;
-    }
-    return v;
-}
-
 int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap) {
     DevInfo d;
     if (dev_info(&d) != HZ_OK) return 1;
@@ -315,9 +229,14 @@ int spmv_grid(const hz_mat *A, int kind, int group, int blocks_per_sm_cap) {
     return stream_grid(d, threads, kSpmvBlock, blocks_per_sm_cap);
 }
 
-int c64_flat_grid(const hz_mat *A, int occ) {
+int c64_flat_grid(const hz_mat *A) {
     DevInfo d;
     if (dev_info(&d) != HZ_OK) return 1;
+    static int occ = 0;
+    if (occ == 0 &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_c64b<EpiStore<float2>>, kFlatThreads, 0) !=
+             cudaSuccess || occ < 1))
+        occ = 1;
     const int64_t g = std::min<int64_t>(A->nfblk, (int64_t)d.num_sms * occ);
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
 }
@@ -395,7 +314,10 @@ static hz_status build_sell(hz_mat *A, cudaStream_t s, const std::vector<int> &r
 static hz_status refresh(hz_mat *A, cudaStream_t s) {
     DevInfo d;
     HZ_TRY(dev_info(&d));
-    HZ_TRY(c64_refresh(A, s));
+    if (A->val32 && A->nnz) {
+        k_to_c64<<<stream_grid(d, A->nnz, 256, 8), 256, 0, s>>>(A->nnz, A->val, A->val32);
+        HZ_CUDA(cudaGetLastError());
+    }
     if (A->val_ff && A->nnz) {
         k_split_ff<<<stream_grid(d, A->nnz, 256, 8), 256, 0, s>>>(A->nnz, A->val, A->val_ff);
         HZ_CUDA(cudaGetLastError());
@@ -410,12 +332,9 @@ static hz_status refresh(hz_mat *A, cudaStream_t s) {
 
 hz_status ensure_c64(hz_mat *A, cudaStream_t s) {
     if (A->val32) return HZ_OK;
-    if (!alloc_c64(A)) {
-        set_error("hz_cspmv: allocation of the complex64 copy failed");
-        return HZ_ERR_ALLOC;
-    }
+    HZ_CUDA(cudaMalloc(&A->val32, sizeof(float2) * std::max(A->nnz, 1)));
+    if (A->sell_val) HZ_CUDA(cudaMalloc(&A->sell_val32, sizeof(float2) * std::max<int64_t>(A->sell_slots, 1)));
     HZ_TRY(refresh(A, s));
-    HZ_TRY(c64_choose(A, s));
     HZ_CUDA(cudaStreamSynchronize(s));
     return HZ_OK;
 }
@@ -633,7 +552,9 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
         A->spmv_kind = HZ_SPMV_SELL;
     }
     if (flags & HZ_FLAG_C64) {
-        if (!alloc_c64(A)) {
+        if (cudaMalloc(&A->val32, sizeof(float2) * std::max(nnz, 1)) != cudaSuccess ||
+            (A->sell_val && cudaMalloc(&A->sell_val32, sizeof(float2) * std::max<int64_t>(A->sell_slots, 1)) !=
+                                cudaSuccess)) {
             set_error("hz_csr_create: allocation failed");
             return fail(HZ_ERR_ALLOC);
         }
@@ -691,7 +612,6 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
         A->spmv_kind = in_range ? HZ_SPMV_FF_FLAT : A->pk_re ? HZ_SPMV_FLAT64P : HZ_SPMV_FLAT64;
     }
     if ((st = refresh(A, s)) != HZ_OK) return fail(st);
-    if ((st = c64_choose(A, s)) != HZ_OK) return fail(st);
     if (flags & HZ_FLAG_AUTOTUNE) {
         if ((st = autotune(A, s)) != HZ_OK) return fail(st);
     }
@@ -730,8 +650,6 @@ extern "C" HZ_API hz_status hz_mat_destroy(hz_mat *A) {
     cudaFree(A->fault);
     cudaFree(A->sell_val32);
     cudaFree(A->val32);
-    cudaFree(A->c64_re);
-    cudaFree(A->c64_cplx);
     cudaFree(A->val_ff);
     cudaFree(A->x_ff);
     cudaFree(A->diag_pos);
@@ -750,7 +668,7 @@ extern "C" HZ_API hz_status hz_mat_query(const hz_mat *A, hz_mat_props *p) {
     p->group = A->group;
     p->sell_slots = A->sell_slots;
     p->sell_sigma = A->sell_sigma;
-    p->has_c64 = A->c64_use_re ? 2 : A->val32 ? 1 : 0;
+    p->has_c64 = A->val32 != nullptr;
     return HZ_OK;
 }
 
@@ -808,11 +726,8 @@ extern "C" HZ_API hz_status hz_cspmv(hz_mat *A, const hz_c *d_x, hz_c *d_y, void
     if (A->fblk && is_flat64(d64_kind(A, A->spmv_kind))) {
         // the block-flat kinds: the block-flat complex64 kernel
         EpiStore<float2> epi{(float2 *)d_y};
-        const MatView<float2> V = c64_view(A, A->spmv_kind);
-        const bool re = V.c64_re != nullptr;
-        HZ_CUDA(launch_k(false, re ? k_spmv_c64b<EpiStore<float2>, true> : k_spmv_c64b<EpiStore<float2>, false>,
-                         c64_flat_grid(A, c64_flat_occupancy<EpiStore<float2>>(re)), kFlatThreads,
-                         (cudaStream_t)stream, V, (const float2 *)d_x, epi, RedScratch{}));
+        HZ_CUDA(launch_k(false, k_spmv_c64b<EpiStore<float2>>, c64_flat_grid(A), kFlatThreads, (cudaStream_t)stream,
+                         mat_view<float2>(A), (const float2 *)d_x, epi, RedScratch{}));
         return HZ_OK;
     }
     const int kind = (A->spmv_kind == HZ_SPMV_SELL || A->spmv_kind == HZ_SPMV_SELL_FF) ? HZ_SPMV_SELL

@@ -108,10 +108,6 @@ struct MatView {
     const int *pk_col;
     const double *pk_re;
     const double *pk_im;
-    // real parts and chunk flags of the complex64 copy (see hz_mat::c64_*);
-    // null unless the complex64 view of a HZ_SPMV_FLAT64P handle (c64_view)
-    const float *c64_re;
-    const int *c64_cplx;
 };
 
 // Epilogue interface (every fused SpMV epilogue provides):
@@ -1130,11 +1126,8 @@ __global__ void __launch_bounds__(kFlatThreads) k_spmv_fft(MatView<double2> A, c
 // double-float kernel with complex64 values (the mixed solver's inner
 // operator) and plain binary32 arithmetic: phase 1 forms a_k x_col(k) (four
 // FMA-pipe operations) into the warp's slab, phase 2 sums each row in
-// storage order.  RE: with the real parts (A.c64_re), a group whose chunks
-// are all real reads them alone (4 bytes per value instead of 8), any other
-// group the complex64 copy; a real chunk's imaginary parts are +0, so the
-// products are bit-identical either way.
-template <class Epi, int NV, bool RE>
+// storage order.
+template <class Epi, int NV>
 __device__ __forceinline__ void flat_rows_c64(const MatView<float2> &A, const float2 *__restrict__ x, const Epi &epi,
                                               typename Epi::Acc (&acc)[NV], float2 *slab) {
     const uint64_t pol = pol_evict_first();
@@ -1170,22 +1163,12 @@ __device__ __forceinline__ void flat_rows_c64(const MatView<float2> &A, const fl
         q.kend = min(m.ke, m.kb + kFlatCap);
         return q;
     };
-    // a group's 32 kFlatGroup consecutive entries span at most two chunks
-    static_assert(32 * kFlatGroup <= kC64Chunk, "a group must span at most two complex64 chunks");
-    // columns one group ahead
     auto load_cols = [&](const Group &q, int (&c)[kFlatGroup]) {
 #pragma unroll
         for (int u = 0; u < kFlatGroup; ++u) {
             const int k = q.kg + lane + 32 * u;
             c[u] = (q.b < A.nfblk && k < q.kend) ? ld_stream(A.col + k, pol) : -1;
         }
-    };
-    // with the real parts: whether every chunk the group touches (at most
-    // two) is real
-    auto real_group = [&](const Group &q) {
-        if constexpr (!RE) return false;
-        const int c0 = q.kg >> kC64ChunkLog, c1 = (min(q.kend, q.kg + 32 * kFlatGroup) - 1) >> kC64ChunkLog;
-        return (__ldg(A.c64_cplx + c0) | (c1 > c0 ? __ldg(A.c64_cplx + c1) : 0)) == 0;
     };
     const int b0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b0 >= A.nfblk) return;
@@ -1198,15 +1181,10 @@ __device__ __forceinline__ void flat_rows_c64(const MatView<float2> &A, const fl
         int c[kFlatGroup];
         float2 a[kFlatGroup], v[kFlatGroup];
 #pragma unroll
-        for (int u = 0; u < kFlatGroup; ++u) c[u] = cn[u];
-        if (real_group(cur)) {   // warp-uniform: the real parts alone
-#pragma unroll
-            for (int u = 0; u < kFlatGroup; ++u)
-                a[u] = make_float2(c[u] >= 0 ? ld_stream(A.c64_re + cur.kg + lane + 32 * u, pol) : 0.f, 0.f);
-        } else {   // the complex64 copy
-#pragma unroll
-            for (int u = 0; u < kFlatGroup; ++u)
-                a[u] = c[u] >= 0 ? ld_stream(A.val + cur.kg + lane + 32 * u) : make_float2(0.f, 0.f);
+        for (int u = 0; u < kFlatGroup; ++u) {
+            c[u] = cn[u];
+            const int k = cur.kg + lane + 32 * u;
+            a[u] = c[u] >= 0 ? ld_stream(A.val + k) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < kFlatGroup; ++u) v[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float2(0.f, 0.f);
@@ -1258,7 +1236,7 @@ __device__ __forceinline__ void flat_rows_c64(const MatView<float2> &A, const fl
     }
 }
 
-template <class Epi, bool RE = false>
+template <class Epi>
 __global__ void __launch_bounds__(kFlatThreads) k_spmv_c64b(MatView<float2> A, const float2 *__restrict__ x, Epi epi,
                                                             RedScratch red) {
     __shared__ float2 prod[(kFlatThreads / 32) * kFlatCap];   // one slab per warp
@@ -1272,28 +1250,12 @@ __global__ void __launch_bounds__(kFlatThreads) k_spmv_c64b(MatView<float2> A, c
     typename Epi::Acc acc[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) Epi::zero(acc[j]);
-    flat_rows_c64<Epi, NV, RE>(A, x, epi, acc, prod);
+    flat_rows_c64<Epi, NV>(A, x, epi, acc, prod);
     if constexpr (Epi::NV > 0) spmv_reduce<Epi, NV>(epi, acc, red);
 }
 
-// CTAs of k_spmv_c64b<Epi, RE> that fit on one SM (computed once)
-template <class Epi>
-int c64_flat_occupancy(bool re) {
-    static int occ[2] = {0, 0};
-    int &o = occ[re ? 1 : 0];
-    if (o == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                       &o, re ? k_spmv_c64b<Epi, true> : k_spmv_c64b<Epi, false>, kFlatThreads, 0) != cudaSuccess ||
-                   o < 1))
-        o = 1;
-    return o;
-}
-// grid of k_spmv_c64b for occ CTAs per SM: the CTAs that fit at once
-int c64_flat_grid(const hz_mat *A, int occ);
-// complex64 view of a handle for a kernel kind: mat_view<float2> plus the
-// real parts and chunk flags when the kind resolves to HZ_SPMV_FLAT64P and
-// the handle reads them (hz_mat::c64_use_re); the kernel is then
-// k_spmv_c64b<Epi, true>
-MatView<float2> c64_view(const hz_mat *A, int kind);
+// grid of k_spmv_c64b: the CTAs that fit at once
+int c64_flat_grid(const hz_mat *A);
 
 // binary64 -> double-float split of a vector (xff[i] = split_ff(x[i])), on stream s
 cudaError_t split_ff_vec(int n, const double2 *x, float4 *xff, cudaStream_t s);

@@ -313,30 +313,16 @@ def test_spmv_c3_full_size(hz, oracle):
         M.close()
 
 
-def expected_has_c64(A):
-    """hz_mat_props.has_c64 of a handle with the complex64 copy: 2 (the
-    kernel reads the real parts) where at least 3/4 of the chunks of 256
-    consecutive nonzeros have only +0 binary32 imaginary parts, else 1."""
-    im = A.val.astype(np.complex64).imag.view(np.uint32) != 0
-    nc = (A.nnz + 255) // 256
-    pad = np.zeros(nc * 256, dtype=bool)
-    pad[:A.nnz] = im
-    real = int((~pad.reshape(nc, 256).any(axis=1)).sum())
-    return 2 if 4 * real >= 3 * nc else 1
-
-
 @pytest.mark.parametrize("ff", [False, True])
 def test_cspmv_complex64(hz, oracle, ff):
     """Complex64 products, including rows longer than one 512-entry block:
     the block-flat kernel under the handle's default kind (plain or
-    double-float; it reads the real parts of the complex64 copy where most
-    chunks are real, as on the cylinder), under FLAT64 (never) and
-    CSR-vector.  The real parts are the same values, so the products equal
-    FLAT64's bit for bit."""
+    double-float) and under FLAT64, and CSR-vector.  Both block-flat kinds
+    run the same complex64 kernel on the same copy: equal bit for bit."""
     for A in (K.small_cylinder()[0], K.random_csr(3000, 6, max_row=12, long_rows=(2500, 1300))):
         x = K.vectors(A.n, 5)[0].astype(np.complex64)
         M = hz.Matrix.from_csr(A, c64=True, ff=ff)
-        assert M.props()["has_c64"] == expected_has_c64(A)
+        assert M.props()["has_c64"] == 1
         ref = oracle.cspmv(A, x)
         scale = K.row_abs_scale(A, x.astype(np.complex128))
         ys = {}
@@ -349,15 +335,14 @@ def test_cspmv_complex64(hz, oracle, ff):
         M.close()
 
 
-def test_cspmv_real_chunks_follow_value_refresh(hz, oracle):
-    """The block-flat complex64 kernel reads the real parts alone for a
-    group of entries whose chunks of 256 consecutive nonzeros have only +0
-    binary32 imaginary parts.  A real matrix with a band of complex rows,
-    one -0 imaginary part (its chunk is complex: the bits are not +0), one
-    of 1e-60 (+0 in binary32: the chunk stays real) and a ragged last chunk;
-    then a value refresh that swaps the band's rows and a long row between
-    real and complex.  Each product equals the FLAT64 kernel's (no real
-    parts) bit for bit and the oracle's within the binary32 bound."""
+def test_cspmv_complex64_copy_follows_value_refresh(hz, oracle):
+    """The complex64 copy is re-derived by hz_mat_refresh_values.  A real
+    matrix with a band of complex rows, one -0 imaginary part, one of 1e-60
+    (+0 in binary32) and a complex last entry, then a value refresh that
+    swaps the band's rows and a long row (900 entries: the long-row passes)
+    between real and complex.  Each block-flat complex64 product is within
+    the binary32 bound of the oracle's on the values of the moment, and
+    equal bit for bit under FLAT64P and FLAT64."""
     A = K.random_csr(5000, 93, max_row=20, long_rows=(900,))
     assert A.nnz % 256 != 0
     rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
@@ -366,14 +351,14 @@ def test_cspmv_real_chunks_follow_value_refresh(hz, oracle):
     v0[band] = A.val[band]
     v0[10] = complex(v0[10].real, -0.0)
     v0[3000] = complex(v0[3000].real, 1e-60)
-    v0[-1] = A.val[-1]                                        # complex entry in the ragged last chunk
+    v0[-1] = A.val[-1]                                        # complex last entry
     flip = band | (np.diff(A.rowptr)[rows] == 900)
     v1 = v0.copy()
     v1[flip] = np.where(band[flip], A.val[flip].real, A.val[flip])
     x = K.vectors(A.n, 94)[0].astype(np.complex64)
     vd = dev(v0)
     M = hz.Matrix(dev(A.rowptr), dev(A.col), vd, c64=True)
-    assert M.props()["spmv_kind"] == 7 and M.props()["has_c64"] == 2 == expected_has_c64(W.CSR(A.n, A.rowptr, A.col, v0))
+    assert M.props()["spmv_kind"] == 7 and M.props()["has_c64"] == 1
     for v in (v0, v1):
         if v is v1:
             vd.copy_(torch.as_tensor(v1))

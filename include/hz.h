@@ -166,9 +166,11 @@ typedef struct {
  * Synchronises `stream` once (row statistics are computed on the host).
  * d_val must be 16-byte aligned (any complex128 allocation is), d_col and
  * d_rowptr 4-byte aligned.
- * Errors: HZ_ERR_ARG for n < 0, nnz < 0, null pointers with nonzero sizes,
- * misaligned arrays, index_base not 0/1, or (with HZ_FLAG_VALIDATE) a
- * malformed CSR.
+ * Errors: HZ_ERR_ARG for n < 0, nnz < 0, n or nnz above 2^31 - 4097 (the
+ * kernels' int32 index arithmetic runs up to 4096 past them), null pointers
+ * with nonzero sizes, misaligned arrays, index_base not 0/1, or (with
+ * HZ_FLAG_VALIDATE) a malformed CSR; all but the last are detected before
+ * any array is read.
  */
 HZ_API hz_status hz_csr_create(hz_mat **A, int32_t n, int32_t nnz, const int32_t *d_rowptr,
                                const int32_t *d_col, const hz_z *d_val, int32_t index_base,

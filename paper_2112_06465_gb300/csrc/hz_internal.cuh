@@ -203,6 +203,10 @@ __device__ __forceinline__ double widen_d(float f) {
 constexpr int kFFMinExp = -100;
 constexpr int kFFMaxExp = 100;
 
+// largest n and nnz of a handle: the kernels form int32 indices up to a few
+// thousand past a row or entry count (a group, a row block, a lane step)
+constexpr int32_t kMaxCsrSize = 0x7fffffff - 4096;
+
 __device__ __forceinline__ float4 split_ff(double2 d) {
     float4 r;
     split_d(d.x, r.x, r.y);

@@ -411,6 +411,7 @@ extern "C" HZ_API hz_status hz_csr_create(hz_mat **out, int32_t n, int32_t nnz, 
     HZ_CHECK(out != nullptr, "hz_csr_create: null output handle");
     *out = nullptr;
     HZ_CHECK(n >= 0 && nnz >= 0, "hz_csr_create: negative size");
+    HZ_CHECK(n <= kMaxCsrSize && nnz <= kMaxCsrSize, "hz_csr_create: n and nnz must be at most 2^31 - 4097");
     HZ_CHECK(index_base == 0 || index_base == 1, "hz_csr_create: index_base must be 0 or 1");
     HZ_CHECK(d_rowptr != nullptr, "hz_csr_create: null rowptr");
     HZ_CHECK(nnz == 0 || (d_col != nullptr && d_val != nullptr), "hz_csr_create: null col/val");

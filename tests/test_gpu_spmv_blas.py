@@ -270,6 +270,20 @@ def test_spmv_bad_csr_rejected(hz):
         hz.Matrix(dev(rp), dev(A.col), dev(A.val), validate=True)
 
 
+def test_create_rejects_sizes_without_index_headroom(hz):
+    """n and nnz above 2^31 - 4097 leave the kernels' int32 index arithmetic
+    no headroom: hz_csr_create refuses them with HZ_ERR_ARG before reading
+    any array (here 8-entry buffers stand for the declared sizes)."""
+    import ctypes as C
+    from paper_2112_06465_gb300 import _lib
+    rp, cl, vl = dev(np.zeros(8, np.int32)), dev(np.zeros(8, np.int32)), dev(np.zeros(8, np.complex128))
+    for n, nnz in ((4, 2**31 - 4096), (2**31 - 4096, 4)):
+        h = C.c_void_p()
+        st = hz.hz._L.hz_csr_create(C.byref(h), n, nnz, C.c_void_p(rp.data_ptr()), C.c_void_p(cl.data_ptr()),
+                                     C.c_void_p(vl.data_ptr()), 0, 0, None)
+        assert st == _lib.HZ_ERR_ARG and not h.value, (n, nnz)
+
+
 def test_spmv_c2_full_size_sampled(hz, oracle):
     """C2 cylinder (~618k rows, ~9.2M nonzeros) in the launch configuration the
     benchmark times, checked entry by entry against the oracle."""

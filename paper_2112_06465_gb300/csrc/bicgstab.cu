@@ -669,7 +669,19 @@ static hz_status get_solver(hz_mat *A, uint32_t mode, cudaStream_t s, Solver **o
         S->group = A->group;
         S->grid_spmv = spmv_grid(A, S->kind, S->group);
         S->grid_spmv_cv = spmv_grid(A, d64_kind(A, S->kind), S->group);
-        S->grid_c64 = A->fblk ? c64_flat_grid(A) : 1;
+        if (A->fblk) {
+            // the CTAs of both complex64 products of the iteration that fit
+            // at once: a grid sized for another epilogue's instantiation
+            // would run a partial second wave if these held more registers
+            int o1 = 0, o2 = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_spmv_c64b<EpiSigma<float2>>, kFlatThreads, 0) !=
+                    cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_spmv_c64b<EpiOmega<float2>>, kFlatThreads, 0) !=
+                    cudaSuccess)
+                o1 = o2 = 1;
+            const int64_t g = std::min<int64_t>(A->nfblk, (int64_t)d.num_sms * std::max(1, std::min(o1, o2)));
+            S->grid_c64 = (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
+        }
         // HZ_PDL=1 (environment) captures F2..F5 as programmatic dependent
         // launches; measured no faster on a 24^3 box (41.5 vs 41.9 us per
         // iteration) and slower on a 64^3 box (99 vs 93 us) and on C2

@@ -509,3 +509,22 @@ def test_adjoint_oracle_gradient(oracle):
         fd = (loss_dense(S + eps * dA)[0] - loss_dense(S - eps * dA)[0]) / (2 * eps)
         an = float(np.real(np.vdot(grad_val, v)))
         assert abs(fd - an) <= 1e-5 * max(abs(fd), 1e-12)   # FD round-off ~ eps_mach L / eps
+
+
+def test_openmp_oracle_is_thread_count_invariant(oracle):
+    """The all-cores CPU baseline runs the oracle built with OpenMP.  Its
+    reductions sum fixed chunks of 8192 elements and add the chunk totals in
+    order, so any thread count gives the same iterates bit for bit.  Its
+    solution is the plain build's up to the rounding of the chunked sums:
+    both reach the tolerance, and the solutions agree to 1e-8 relative (the
+    two differ by at most about 2 cond(A) tol).  13,824 unknowns span two
+    chunks."""
+    A = W.fd_helmholtz_box(24, kh=0.5, damping=0.05)
+    b = K.vectors(A.n, 7)[0]
+    runs = [oracle.bicgstab_omp(A, b, tol=1e-10, maxit=2000, threads=t) for t in (1, 3, 4)]
+    for x, info in runs:
+        assert info.status == 0 and info.relres_true <= 1e-10
+        assert np.array_equal(x, runs[0][0]) and info.iters == runs[0][1].iters
+    xs, info_s = oracle.bicgstab(A, b, tol=1e-10, maxit=2000)[:2]
+    assert info_s.status == 0 and info_s.relres_true <= 1e-10
+    assert np.linalg.norm(xs - runs[0][0]) <= 1e-8 * np.linalg.norm(xs)
